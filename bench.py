@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Throughput of the hybrid LBM step (Renard et al., arXiv 2002.03644) on GB300.
+
+Workload: isentropic vortex convected at Ma 1.2 in a periodic 1024 x 1024
+box (vortex strength 0.2, radius 32 cells, gamma 1.4, Pr 0.71, sigma 0,
+seeded +-1e-6 density noise), FP32 storage and arithmetic.  One bench step is
+one time step of Algorithm 1 over the whole grid (one launch of the fused
+kernel).  The state (2 x 54.5 MB) fits in L2, so L2 is flushed between timed
+steps (a write of one buffer and a read of another, each larger than L2) and
+each step is timed alone with CUDA events on the library's stream.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.  Under torchrun every rank
+runs an independent replica on its own GPU (the method has no exchange step
+in this single-GPU build); value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {"fp32": 104, "fp64": 208}  # 13 state scalars read + written once
+METRIC, UNIT = "MLUPS", "MLUPS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--e2e-inner", type=int, default=100)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_2002_03644_gb300 import inputs
+    return inputs.vortex(n=n)
+
+
+def describe(case, precision):
+    return {
+        "workload": f"isentropic vortex {case.nx}x{case.ny} periodic, Ma 1.2, strength 0.2, radius 32, "
+                    f"gamma 1.4, Pr 0.71, sigma 0, mu 1.5e-6, +-1e-6 seeded rho noise",
+        "nx": case.nx, "ny": case.ny, "precision": precision,
+        "l2": "flushed between timed steps (state smaller than L2)",
+    }
+
+
+# ---- distributed plumbing ------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---- clocks ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        try:
+            self.f.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+            os.remove(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        mx = max(num(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        loaded = [s for s in sm if not math.isnan(s)]
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- roofline helpers ------------------------------------------------------------------
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("hlbm_device.cuh", "hlbm_api.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2002_03644_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(precision, n):
+    """dram bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "fused_step_vortex_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    e = d.get(f"{precision}_{n}")
+    if not e or e.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---- CPU oracle timing -----------------------------------------------------------------
+def oracle_mlups(case, seconds, rows=None):
+    """Time the FP64 oracle on the host (one thread).  With rows, a periodic
+    strip of that many rows of the workload is used as the sample."""
+    from oracle.oracle import Oracle
+    if rows:
+        sl = slice(case.ny // 2 - rows // 2, case.ny // 2 - rows // 2 + rows)
+        f = [np.ascontiguousarray(a[sl]) for a in case.fields()]
+        nx, ny = case.nx, rows
+    else:
+        f = list(case.fields())
+        nx, ny = case.nx, case.ny
+    o = Oracle(nx, ny, **case.params())
+    o.init(*f)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    k = max(1, int(seconds / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    return nx * ny * k / dt / 1e6, k, dt, nx, ny
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    case = workload(args.n)
+    rows = 16
+    from oracle.oracle import Oracle
+    sl = slice(case.ny // 2 - rows // 2, case.ny // 2 - rows // 2 + rows)
+    f = [np.ascontiguousarray(a[sl]) for a in case.fields()]
+    o = Oracle(case.nx, rows, **case.params())
+    o.init(*f)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    cells = case.nx * rows
+    v = cells * args.steps / dt / 1e6
+    sample = f"{rows}-row periodic strip ({case.nx}x{rows}) through the vortex centre, one time step per bench step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": describe(case, "fp64"),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---- the GPU arm ------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    if rank == 0 or ws == 1:
+        g.build()
+    barrier(ws)
+    from paper_2002_03644_gb300 import hlbm
+
+    prec = hlbm.HLBM_FP32 if args.precision == "fp32" else hlbm.HLBM_FP64
+    case = workload(args.n)
+    cells = case.nx * case.ny
+    stream = torch.cuda.current_stream()
+    s = hlbm.Solver(case.nx, case.ny, stream=stream.cuda_stream, precision=prec, **case.params())
+    s.init(*case.fields())
+
+    flush_w = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush_r = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_w.zero_()
+        flush_r.sum()
+
+    for _ in range(args.warmup):
+        flush()
+        s.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for a, b in ev:
+            flush()
+            a.record(stream)
+            s.step(1)
+            b.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    total_s = max_over_ranks(total_s, ws)
+    value = ws * cells * args.steps / total_s / 1e6
+    ms_per_step = total_s / args.steps * 1e3
+
+    # back-to-back steps (L2 warm), reported for context only
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s.step(args.steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    b2b = cells * args.steps / (a.elapsed_time(b) / 1e3) / 1e6
+
+    d = s.diagnostics()
+    if d[7] != 0:
+        raise RuntimeError("non-finite state after the timed steps")
+
+    # end to end through the C ABI with pinned host buffers: init from host,
+    # e2e_inner steps, read rho, u, theta back to host
+    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case.fields()]
+    outs = [torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    e2e_iters = 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_iters):
+        hlbm.hlbm_init_fields(s.h, *pin, n=cells)
+        s.step(args.e2e_inner)
+        hlbm.hlbm_get_macros(s.h, rho=outs[0], ux=outs[1], uy=outs[2], theta=outs[3], n=cells)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, ws)
+    e2e = {"value": ws * cells * args.e2e_inner * e2e_iters / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": 4 * 8 * cells, "d2h_bytes_per_step": 4 * 8 * cells,
+           "steps_per_call": args.e2e_inner,
+           "note": "one e2e step = hlbm_init_fields(host) + hlbm_step(e2e_inner) + hlbm_get_macros(host)"}
+    s.close()
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    bpc = BYTES_PER_CELL[args.precision]
+    mean_launch_s = statistics.mean(step_ms) / 1e3
+    achieved = bpc * cells / mean_launch_s / 1e9
+    if args.precision == "fp32":
+        peak = peaks["hbm_gbs"] if peaks else 6800.0
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(args.precision, args.n),
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                "kernel": "fused_step_kernel<float,32,16,256>",
+                "algorithmic_bytes_per_launch": bpc * cells}
+    else:
+        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "GB/s", "frac": None,
+                "traffic": profiled_traffic(args.precision, args.n),
+                "note": "FP64 build is bound by the FP64 ALU rate; bytes shown for reference",
+                "kernel": "fused_step_kernel<double,32,8,256>", "algorithmic_bytes_per_launch": bpc * cells}
+
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        v, k, dt, nx, ny = oracle_mlups(case, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 oracle, full {nx}x{ny} grid, {k} time steps after init ({dt:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic", "config": dict(describe(case, args.precision), parallelism=f"replicas{ws}",
+                                            back_to_back_mlups=b2b),
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+        "gpu_launches": args.steps,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

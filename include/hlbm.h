@@ -1,0 +1,163 @@
+/*
+ * hlbm.h -- C ABI of libhlbm, a GB300 (sm_103a) implementation of the hybrid
+ * lattice Boltzmann time step of Renard, Feng, Boussuge and Sagaut,
+ * "Improved compressible Hybrid Lattice Boltzmann Method on standard lattice
+ * for subsonic and supersonic flows" (arXiv 2002.03644).
+ *
+ * One call of hlbm_step advances Algorithm 1 (Sec. 3.5) by one or more time
+ * steps: D2Q9 pull-streaming and hybrid recursive regularised collision for
+ * mass and momentum (eq. streamalgo, eq. a1sigalgo, Sec. 3.3), with the
+ * upwind lattice-closure correction E1 and the polyatomic correction E2
+ * (eq. Psialgo, Sec. 3.2), coupled through temperature to an explicit finite
+ * volume update of the entropy equation (eq. sequaalgo, Sec. 3.4) with the
+ * regularised viscous heating of eq. (viscous heat discret).
+ *
+ * Conventions shared by every entry point
+ *  - Lattice units: dx = dt = 1, c_s^2 = 1/3, theta = T / T_r (Sec. 2.1).
+ *  - Field arrays are FP64, row-major [ny][nx] (x fastest), contiguous, for
+ *    every storage precision; the library converts.  a1 arrays hold three
+ *    such planes in the order xx, xy, yy.
+ *  - mem_kind says where caller arrays live: HLBM_MEM_HOST (pageable or
+ *    pinned host memory) or HLBM_MEM_DEVICE (device memory on the handle's
+ *    GPU).  Caller buffers are borrowed for the duration of the call only.
+ *  - The library allocates and owns all of its device state; nothing is
+ *    allocated by hlbm_step.
+ *  - Work is enqueued on the stream given to hlbm_create.  hlbm_step returns
+ *    without waiting for the GPU unless diag_every > 0; calls that return
+ *    data to the caller (get_*, diagnostics, state) synchronise the stream.
+ *  - Every function returns HLBM_OK (0) or a negative HLBM_ERR_* code; no
+ *    C++ exception crosses the ABI.  hlbm_strerror maps a code to text and
+ *    hlbm_last_error gives the detail of the last failure on a handle.
+ *  - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef HLBM_H
+#define HLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HLBM_ABI_VERSION 1
+
+/* storage and arithmetic precision of the state */
+enum { HLBM_FP64 = 0, HLBM_FP32 = 1 };
+
+/* boundary kind per side (Sec. 4-5 use periodic, zero-gradient and imposed
+ * states; the paper refers their exact form to an earlier work) */
+enum {
+    HLBM_BC_PERIODIC = 0,  /* wrap to the opposite side */
+    HLBM_BC_ZEROGRAD = 1,  /* every quantity copies the nearest interior cell */
+    HLBM_BC_DIRICHLET = 2  /* fixed (rho, ux, uy, theta), a1 = 0, f = f^eq */
+};
+
+enum { HLBM_MEM_HOST = 0, HLBM_MEM_DEVICE = 1 };
+
+enum {
+    HLBM_OK = 0,
+    HLBM_ERR_ARG = -1,         /* invalid argument (sizes, pointers, params) */
+    HLBM_ERR_CFL = -2,         /* initial state violates CFL < 1 (eq. CFL) */
+    HLBM_ERR_NONFINITE = -3,   /* NaN/Inf or non-positive rho or theta found */
+    HLBM_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    HLBM_ERR_STATE = -5,       /* call out of order or corrupt state blob */
+    HLBM_ERR_NOMEM = -6,       /* device or host allocation failed */
+    HLBM_ERR_UNSUPPORTED = -7  /* option not built into this library */
+};
+
+/* Side order of bc[] and bc_state[]: x-, x+, y-, y+.  bc_state[k] holds the
+ * imposed (rho, ux, uy, theta) of a Dirichlet side k.  At a corner cell a
+ * Dirichlet y side takes precedence, then a Dirichlet x side. */
+typedef struct {
+    int32_t nx, ny;        /* interior cells, >= 1 each */
+    int32_t precision;     /* HLBM_FP64 or HLBM_FP32 */
+    int32_t phi_mode;      /* 0: Phi = -(tau/tau_bar) a1 : grad u (eq. viscous
+                              heat discret, default); 1: finite-difference
+                              Phi of eq. (viscous heat) */
+    double gamma;          /* heat capacity ratio, > 1 */
+    double Pr;             /* Prandtl number, > 0 */
+    double mu;             /* dynamic viscosity (lattice units), >= 0, constant;
+                              tau = mu / p per cell (Sec. 2.4) */
+    double sigma;          /* HRR blend of a1^PR and a1^FD, in [0, 1] (eq. a1sigalgo) */
+    int32_t bc[4];
+    double bc_state[4][4];
+    int32_t diag_every;    /* > 0: hlbm_step checks the state every diag_every
+                              steps and returns HLBM_ERR_NONFINITE on a bad
+                              value (this synchronises); 0: never */
+    int32_t check_cfl;     /* != 0: hlbm_init_fields returns HLBM_ERR_CFL when
+                              max(|u| + sqrt(gamma theta / 3)) >= 1 */
+    int32_t reserved[6];   /* must be zero */
+} hlbm_params;
+
+typedef struct hlbm_handle hlbm_handle;
+
+/* Create a solver on the current CUDA device.  stream is a cudaStream_t (or
+ * NULL: the library creates and owns a non-blocking stream).  Allocates the
+ * ping-pong state (13 planes per copy: 9 post-collision populations, s and
+ * a1_xx, a1_xy, a1_yy) and FP64 staging buffers.  *out is NULL on failure. */
+int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out);
+
+/* Algorithm 1, input and initialisation (steps 1-4): from [rho, u, theta]^(0)
+ * build s = c_v ln(theta / rho^(gamma-1)), a1^(0) (= a1^FD of eq. a1FD when
+ * a1 is NULL, else the given three planes), psi^(0) and the post-collision
+ * populations of level 0.  Resets the step counter.  rho, ux, uy, theta are
+ * required; a1 may be NULL.  Synchronises before returning. */
+int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const double *uy,
+                     const double *theta, const double *a1, int mem_kind);
+
+/* Algorithm 1, steps 5-11, n times (n >= 0). */
+int hlbm_step(hlbm_handle *h, int64_t n);
+
+/* Fields of the current level: rho, ux, uy, theta, s (one plane each) and a1
+ * (three planes); any pointer may be NULL to skip that field.  rho and u are
+ * the moments of the post-collision populations (collision invariants,
+ * eqs. rhoalgo, ualgo); theta follows from s and rho (eq. Entropie
+ * expression).  Synchronises. */
+int hlbm_get_macros(hlbm_handle *h, double *rho, double *ux, double *uy, double *theta,
+                    double *s, double *a1, int mem_kind);
+
+/* The 9 post-collision populations of the current level (eq. streamalgo,
+ * before propagation), as 9 FP64 planes in D2Q9 order c_x = [0,1,0,-1,0,1,
+ * -1,-1,1], c_y = [0,0,1,0,-1,1,1,-1,-1].  Synchronises. */
+int hlbm_get_populations(hlbm_handle *h, double *F, int mem_kind);
+
+/* Diagnostics of the current level, FP64 sums over interior cells:
+ * out[0] = sum rho, out[1] = sum rho ux, out[2] = sum rho uy,
+ * out[3] = sum (rho c_v theta + rho |u|^2 / 2), out[4] = min rho,
+ * out[5] = min theta, out[6] = max (|u| + sqrt(gamma theta / 3)) (the local
+ * CFL number of eq. CFL), out[7] = number of cells with a non-finite or
+ * non-positive rho or theta.  out is a host array.  Synchronises. */
+int hlbm_diagnostics(hlbm_handle *h, double out[8]);
+
+/* Checkpoint: the size of the state blob, and a byte-exact copy of the state
+ * and step counter into / from host memory.  set_state checks sizes,
+ * precision and a header; it returns HLBM_ERR_STATE on any mismatch. */
+int hlbm_state_bytes(const hlbm_handle *h, size_t *bytes);
+int hlbm_get_state(hlbm_handle *h, void *buf, size_t bytes);
+int hlbm_set_state(hlbm_handle *h, const void *buf, size_t bytes);
+
+/* Time steps taken since hlbm_init_fields / hlbm_set_state (-1 on NULL). */
+int64_t hlbm_step_count(const hlbm_handle *h);
+
+/* Wait for all work of the handle's stream. */
+int hlbm_synchronize(hlbm_handle *h);
+
+/* Free all device and host resources of the handle (NULL is a no-op). */
+void hlbm_destroy(hlbm_handle *h);
+
+/* Static text for a status code. */
+const char *hlbm_strerror(int code);
+
+/* Detail of the last failure on this handle (CUDA error string or argument
+ * name); "" when none.  The pointer stays valid until the next call. */
+const char *hlbm_last_error(const hlbm_handle *h);
+
+/* HLBM_ABI_VERSION of the loaded library. */
+int hlbm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HLBM_H */

@@ -1,0 +1,312 @@
+"""Python binding of libhlbm (include/hlbm.h): the same entry points, argument
+marshalling only.  Every step of the method runs in the CUDA library; there
+is no fallback: if libhlbm.so is missing or a call fails, an exception is
+raised.
+
+Arrays may be numpy arrays (host memory) or torch tensors (a CUDA tensor is
+passed as device memory, a CPU tensor as host memory).  Field arrays are
+float64, contiguous, shape [ny, nx]; a1 arrays are [3, ny, nx].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+HLBM_FP64, HLBM_FP32 = 0, 1
+HLBM_BC_PERIODIC, HLBM_BC_ZEROGRAD, HLBM_BC_DIRICHLET = 0, 1, 2
+HLBM_MEM_HOST, HLBM_MEM_DEVICE = 0, 1
+HLBM_OK, HLBM_ERR_ARG, HLBM_ERR_CFL, HLBM_ERR_NONFINITE = 0, -1, -2, -3
+HLBM_ERR_CUDA, HLBM_ERR_STATE, HLBM_ERR_NOMEM, HLBM_ERR_UNSUPPORTED = -4, -5, -6, -7
+
+ENTRY_POINTS = (
+    "hlbm_create", "hlbm_init_fields", "hlbm_step", "hlbm_get_macros", "hlbm_get_populations",
+    "hlbm_diagnostics", "hlbm_state_bytes", "hlbm_get_state", "hlbm_set_state", "hlbm_step_count",
+    "hlbm_synchronize", "hlbm_destroy", "hlbm_strerror", "hlbm_last_error", "hlbm_abi_version",
+)
+
+
+class hlbm_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("phi_mode", ctypes.c_int32),
+        ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("mu", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("bc", ctypes.c_int32 * 4), ("bc_state", (ctypes.c_double * 4) * 4),
+        ("diag_every", ctypes.c_int32), ("check_cfl", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
+    ]
+
+
+def make_params(nx, ny, precision=HLBM_FP64, gamma=1.4, Pr=0.71, mu=1e-4, sigma=0.0,
+                bc=(HLBM_BC_PERIODIC,) * 4, bc_state=None, phi_mode=0, diag_every=0, check_cfl=0):
+    p = hlbm_params()
+    p.nx, p.ny, p.precision, p.phi_mode = int(nx), int(ny), int(precision), int(phi_mode)
+    p.gamma, p.Pr, p.mu, p.sigma = float(gamma), float(Pr), float(mu), float(sigma)
+    for k in range(4):
+        p.bc[k] = int(bc[k])
+    if bc_state is not None:
+        bs = np.asarray(bc_state, dtype=np.float64).reshape(4, 4)
+        for k in range(4):
+            for q in range(4):
+                p.bc_state[k][q] = float(bs[k, q])
+    p.diag_every, p.check_cfl = int(diag_every), int(check_cfl)
+    return p
+
+
+class HlbmError(RuntimeError):
+    def __init__(self, code, detail=""):
+        self.code = code
+        super().__init__(f"hlbm error {code}: {_strerror(code)}" + (f" ({detail})" if detail else ""))
+
+
+_lock = threading.Lock()
+_libh = None
+_P = ctypes.c_void_p
+_PD = ctypes.c_void_p  # pointers are passed as raw addresses
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _lib():
+    global _libh
+    with _lock:
+        if _libh is not None:
+            return _libh
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        lib.hlbm_create.restype = ctypes.c_int
+        lib.hlbm_create.argtypes = [ctypes.POINTER(hlbm_params), _P, ctypes.POINTER(_P)]
+        lib.hlbm_init_fields.restype = ctypes.c_int
+        lib.hlbm_init_fields.argtypes = [_P, _PD, _PD, _PD, _PD, _PD, ctypes.c_int]
+        lib.hlbm_step.restype = ctypes.c_int
+        lib.hlbm_step.argtypes = [_P, ctypes.c_int64]
+        lib.hlbm_get_macros.restype = ctypes.c_int
+        lib.hlbm_get_macros.argtypes = [_P, _PD, _PD, _PD, _PD, _PD, _PD, ctypes.c_int]
+        lib.hlbm_get_populations.restype = ctypes.c_int
+        lib.hlbm_get_populations.argtypes = [_P, _PD, ctypes.c_int]
+        lib.hlbm_diagnostics.restype = ctypes.c_int
+        lib.hlbm_diagnostics.argtypes = [_P, _PD]
+        lib.hlbm_state_bytes.restype = ctypes.c_int
+        lib.hlbm_state_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
+        lib.hlbm_get_state.restype = ctypes.c_int
+        lib.hlbm_get_state.argtypes = [_P, _PD, ctypes.c_size_t]
+        lib.hlbm_set_state.restype = ctypes.c_int
+        lib.hlbm_set_state.argtypes = [_P, _PD, ctypes.c_size_t]
+        lib.hlbm_step_count.restype = ctypes.c_int64
+        lib.hlbm_step_count.argtypes = [_P]
+        lib.hlbm_synchronize.restype = ctypes.c_int
+        lib.hlbm_synchronize.argtypes = [_P]
+        lib.hlbm_destroy.restype = None
+        lib.hlbm_destroy.argtypes = [_P]
+        lib.hlbm_strerror.restype = ctypes.c_char_p
+        lib.hlbm_strerror.argtypes = [ctypes.c_int]
+        lib.hlbm_last_error.restype = ctypes.c_char_p
+        lib.hlbm_last_error.argtypes = [_P]
+        lib.hlbm_abi_version.restype = ctypes.c_int
+        lib.hlbm_abi_version.argtypes = []
+        _libh = lib
+        return lib
+
+
+def _strerror(code):
+    try:
+        return _lib().hlbm_strerror(int(code)).decode()
+    except Exception:
+        return "?"
+
+
+def _check(code, h=None):
+    if code != HLBM_OK:
+        detail = ""
+        if h:
+            try:
+                detail = _lib().hlbm_last_error(h).decode()
+            except Exception:
+                pass
+        raise HlbmError(code, detail)
+
+
+def _addr(a, n, keep):
+    """(address, mem_kind) of an FP64 contiguous array with n elements."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != n:
+            raise ValueError("torch tensors must be float64, contiguous, with the field's size")
+        keep.append(a)
+        return a.data_ptr(), (HLBM_MEM_DEVICE if a.is_cuda else HLBM_MEM_HOST)
+    arr = np.asarray(a)
+    if arr.dtype != np.float64 or not arr.flags["C_CONTIGUOUS"] or arr.size != n:
+        raise ValueError("numpy arrays must be float64, C-contiguous, with the field's size")
+    keep.append(arr)
+    return arr.ctypes.data, HLBM_MEM_HOST
+
+
+def _one_kind(kinds):
+    ks = {k for k in kinds if k is not None}
+    if len(ks) > 1:
+        raise ValueError("all arrays of one call must live in the same memory (host or device)")
+    return ks.pop() if ks else HLBM_MEM_HOST
+
+
+# ---- the C entry points ---------------------------------------------------------
+
+def hlbm_abi_version():
+    return _lib().hlbm_abi_version()
+
+
+def hlbm_strerror(code):
+    return _strerror(code)
+
+
+def hlbm_last_error(h):
+    return _lib().hlbm_last_error(h).decode()
+
+
+def hlbm_create(params: hlbm_params, stream=None):
+    """Returns an opaque handle.  stream: a cudaStream_t as int (e.g.
+    torch.cuda.current_stream().cuda_stream) or None."""
+    h = _P()
+    _check(_lib().hlbm_create(ctypes.byref(params), stream or None, ctypes.byref(h)))
+    return h.value
+
+
+def hlbm_init_fields(h, rho, ux, uy, theta, a1=None, n=None):
+    keep = []
+    if n is None:
+        n = int(np.prod(np.shape(rho)))
+    ptrs, kinds = [], []
+    for a, m in ((rho, n), (ux, n), (uy, n), (theta, n), (a1, 3 * n)):
+        p, k = _addr(a, m, keep)
+        ptrs.append(p); kinds.append(k)
+    _check(_lib().hlbm_init_fields(h, *ptrs, _one_kind(kinds)), h)
+
+
+def hlbm_step(h, n):
+    _check(_lib().hlbm_step(h, int(n)), h)
+
+
+def hlbm_get_macros(h, rho=None, ux=None, uy=None, theta=None, s=None, a1=None, n=None):
+    keep = []
+    ref = next(a for a in (rho, ux, uy, theta, s, a1) if a is not None)
+    if n is None:
+        n = int(np.prod(np.shape(ref))) // (3 if ref is a1 else 1)
+    ptrs, kinds = [], []
+    for a, m in ((rho, n), (ux, n), (uy, n), (theta, n), (s, n), (a1, 3 * n)):
+        p, k = _addr(a, m, keep)
+        ptrs.append(p); kinds.append(k)
+    _check(_lib().hlbm_get_macros(h, *ptrs, _one_kind(kinds)), h)
+
+
+def hlbm_get_populations(h, F):
+    keep = []
+    p, k = _addr(F, int(np.prod(np.shape(F))), keep)
+    _check(_lib().hlbm_get_populations(h, p, k), h)
+
+
+def hlbm_diagnostics(h):
+    out = np.zeros(8)
+    _check(_lib().hlbm_diagnostics(h, out.ctypes.data), h)
+    return out
+
+
+def hlbm_state_bytes(h):
+    n = ctypes.c_size_t()
+    _check(_lib().hlbm_state_bytes(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def hlbm_get_state(h):
+    buf = np.zeros(hlbm_state_bytes(h), dtype=np.uint8)
+    _check(_lib().hlbm_get_state(h, buf.ctypes.data, buf.size), h)
+    return buf
+
+
+def hlbm_set_state(h, buf):
+    b = np.ascontiguousarray(np.asarray(buf, dtype=np.uint8))
+    _check(_lib().hlbm_set_state(h, b.ctypes.data, b.size), h)
+
+
+def hlbm_step_count(h):
+    return _lib().hlbm_step_count(h)
+
+
+def hlbm_synchronize(h):
+    _check(_lib().hlbm_synchronize(h), h)
+
+
+def hlbm_destroy(h):
+    if h:
+        _lib().hlbm_destroy(h)
+
+
+# ---- convenience wrapper ----------------------------------------------------------
+
+class Solver:
+    """Owns one handle.  Example:
+        s = Solver(nx, ny, precision=HLBM_FP32, mu=1e-4)
+        s.init(rho, ux, uy, theta); s.step(100); m = s.macros()
+    """
+
+    def __init__(self, nx, ny, stream=None, **params):
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = make_params(nx, ny, **params)
+        self.h = hlbm_create(self.params, stream)
+
+    def close(self):
+        if self.h:
+            hlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, rho, ux, uy, theta, a1=None):
+        hlbm_init_fields(self.h, rho, ux, uy, theta, a1, n=self.nx * self.ny)
+
+    def step(self, n=1):
+        hlbm_step(self.h, n)
+
+    def macros(self):
+        shp = (self.ny, self.nx)
+        out = {k: np.zeros(shp) for k in ("rho", "ux", "uy", "theta", "s")}
+        a1 = np.zeros((3,) + shp)
+        hlbm_get_macros(self.h, out["rho"], out["ux"], out["uy"], out["theta"], out["s"], a1,
+                        n=self.nx * self.ny)
+        out["a1"] = a1
+        return out
+
+    def populations(self):
+        F = np.zeros((9, self.ny, self.nx))
+        hlbm_get_populations(self.h, F)
+        return F
+
+    def diagnostics(self):
+        return hlbm_diagnostics(self.h)
+
+    def state(self):
+        return hlbm_get_state(self.h)
+
+    def set_state(self, buf):
+        hlbm_set_state(self.h, buf)
+
+    @property
+    def step_count(self):
+        return hlbm_step_count(self.h)
+
+    def synchronize(self):
+        hlbm_synchronize(self.h)

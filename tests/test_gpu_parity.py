@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
+the same seeded inputs, element by element.
+
+Tolerances (per field, max abs difference / field scale):
+  FP64 build: 1e-10, FP32 build: 1e-4.
+Field scales: rho -> max rho; u_x, u_y -> max |u| + max sound speed
+sqrt(gamma theta / 3); theta -> max theta; s -> max |s|; a1 -> max p
+(a1 is a stress; its PR part is a difference of O(p) moments, so its
+rounding error scales with p, not with |a1|).  Populations -> max rho / 9.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2002_03644_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-4}  # HLBM_FP64, HLBM_FP32
+
+
+@pytest.fixture(scope="module")
+def hl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2002_03644_gb300 import hlbm
+    torch.cuda.set_device(0)
+    return hlbm
+
+
+def scales(m, gamma):
+    c = np.sqrt(gamma * np.abs(m["theta"]) / 3.0).max()
+    umax = np.sqrt(m["ux"] ** 2 + m["uy"] ** 2).max()
+    p = (m["rho"] * m["theta"] / 3.0).max()
+    return {"rho": np.abs(m["rho"]).max(), "ux": umax + c, "uy": umax + c,
+            "theta": np.abs(m["theta"]).max(), "s": np.abs(m["s"]).max(), "a1": p}
+
+
+def compare(got, ref, gamma, tol, fields=("rho", "ux", "uy", "theta", "s", "a1")):
+    sc = scales(ref, gamma)
+    errs = {}
+    for k in fields:
+        assert np.isfinite(got[k]).all(), k
+        errs[k] = float(np.abs(got[k] - ref[k]).max() / sc[k])
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"parity failure {bad} (tol {tol})"
+    return errs
+
+
+def run_pair(hl, case, precision, steps, a1=None, device_inputs=False):
+    ora = Oracle(case.nx, case.ny, **case.params())
+    ora.init(*case.fields(), a1=a1)
+    ora.step(steps)
+    s = hl.Solver(case.nx, case.ny, precision=precision, **case.params())
+    if device_inputs:
+        import torch
+        f = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in case.fields()]
+        a = None if a1 is None else torch.from_numpy(np.ascontiguousarray(a1)).cuda()
+        s.init(*f, a1=a)
+    else:
+        s.init(*case.fields(), a1=a1)
+    s.step(steps)
+    got = s.macros()
+    return s, ora, got, ora.macros()
+
+
+SIZES = [(1, 1), (3, 5), (37, 23), (64, 48), (101, 67)]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("nx,ny", SIZES)
+@pytest.mark.parametrize("sigma", [0.0, 0.6, 1.0])
+def test_periodic_random_fields(hl, precision, nx, ny, sigma):
+    case = inputs.random_smooth(nx, ny, seed=100 + nx, amp=0.05, mu=2e-3, sigma=sigma)
+    s, _, got, ref = run_pair(hl, case, precision, 12)
+    compare(got, ref, case.gamma, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_phi_mode_fd_and_device_inputs(hl, precision):
+    case = inputs.random_smooth(45, 33, seed=9, amp=0.06, mu=4e-3, sigma=0.7)
+    case.phi_mode = 1
+    _, _, got, ref = run_pair(hl, case, precision, 15, device_inputs=True)
+    compare(got, ref, case.gamma, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_given_initial_a1(hl, precision):
+    case = inputs.random_smooth(30, 26, seed=4, amp=0.04, mu=3e-3, sigma=0.4)
+    rng = np.random.default_rng(3)
+    a1 = rng.normal(size=(3, case.ny, case.nx)) * 1e-4
+    _, _, got, ref = run_pair(hl, case, precision, 6, a1=a1)
+    compare(got, ref, case.gamma, TOL[precision])
+
+
+BCS = [
+    (1, 1, 1, 1),          # zero-gradient everywhere
+    (1, 1, 0, 0),          # zero-gradient x, periodic y
+    (0, 0, 1, 1),          # periodic x, zero-gradient y
+    (2, 1, 0, 0),          # inflow x-, outflow x+, periodic y
+    (2, 2, 2, 2),          # Dirichlet everywhere
+    (1, 2, 2, 1),          # mixed corners
+]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("bc", BCS)
+def test_boundaries(hl, precision, bc):
+    bs = np.array([[1.02, 0.08, 0.01, 0.21], [0.98, 0.05, -0.02, 0.19],
+                   [1.01, 0.06, 0.03, 0.2], [0.99, 0.07, 0.0, 0.205]])
+    case = inputs.random_smooth(53, 41, seed=21, amp=0.04, u0=(0.06, 0.01), theta0=0.2, mu=3e-3,
+                                sigma=0.5, bc=bc, bc_state=bs)
+    _, _, got, ref = run_pair(hl, case, precision, 20)
+    compare(got, ref, case.gamma, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_populations_match_post_collision_state(hl, precision):
+    case = inputs.random_smooth(33, 29, seed=12, amp=0.05, mu=2e-3, sigma=0.8,
+                                bc=(1, 1, 0, 0))
+    s, ora, _, ref = run_pair(hl, case, precision, 7)
+    F = s.populations()
+    Fo = ora.post_collision()
+    err = np.abs(F - Fo).max() / (ref["rho"].max() / 9.0)
+    assert err < TOL[precision], err
+
+
+def test_sod_shock_tube_fp64_full_run(hl):
+    """The shock-tube case at its full length (zero-gradient x ends,
+    periodic y, discontinuous initial data)."""
+    case = inputs.sod(C0=3.875, mu=3e-6, sigma=0.0)
+    _, _, got, ref = run_pair(hl, case, 0, case.steps)
+    compare(got, ref, case.gamma, TOL[0])
+
+
+def test_vortex_1024_fp32_bench_configuration(hl):
+    """The benchmark's workload (isentropic vortex, 1024^2, Ma 1.2, FP32) in
+    the launch configuration bench.py times, all cells compared after a few
+    steps (the oracle takes about a second per step at this size)."""
+    case = inputs.vortex(n=1024)
+    _, _, got, ref = run_pair(hl, case, 1, 3)
+    compare(got, ref, case.gamma, TOL[1])
+
+
+def test_vortex_fp64_long_run(hl):
+    case = inputs.vortex(n=96, R=6.0)
+    _, _, got, ref = run_pair(hl, case, 0, 250)
+    compare(got, ref, case.gamma, TOL[0])
+
+
+def test_fp32_long_run_error_stays_bounded(hl):
+    """FP32 storage and arithmetic over a full pass of the vortex through a
+    128^2 box: the error against the FP64 oracle stays within 1e-4."""
+    case = inputs.vortex(n=128, R=8.0)
+    _, _, got, ref = run_pair(hl, case, 1, 347)
+    compare(got, ref, case.gamma, TOL[1], fields=("rho", "ux", "uy", "theta", "s"))
+
+
+def test_conservation_on_gpu_fp64(hl):
+    case = inputs.random_smooth(96, 80, seed=5, amp=0.08, mu=1e-3, sigma=0.3)
+    s = hl.Solver(case.nx, case.ny, precision=0, **case.params())
+    s.init(*case.fields())
+    d0 = s.diagnostics()
+    s.step(200)
+    d1 = s.diagnostics()
+    assert abs(d1[0] - d0[0]) < 1e-12 * d0[0]
+    assert abs(d1[1] - d0[1]) < 1e-12 * d0[0] and abs(d1[2] - d0[2]) < 1e-12 * d0[0]
+    assert d1[7] == 0
+
+
+def test_diagnostics_match_fields(hl):
+    case = inputs.random_smooth(70, 50, seed=8, amp=0.05, mu=1e-3, sigma=0.5)
+    s = hl.Solver(case.nx, case.ny, precision=0, **case.params())
+    s.init(*case.fields())
+    s.step(5)
+    d = s.diagnostics()
+    m = s.macros()
+    cv = (1.0 / 3.0) / (case.gamma - 1.0)
+    assert abs(d[0] - m["rho"].sum()) < 1e-12 * d[0]
+    assert abs(d[1] - (m["rho"] * m["ux"]).sum()) < 1e-12 * d[0]
+    assert abs(d[2] - (m["rho"] * m["uy"]).sum()) < 1e-12 * d[0]
+    e = (m["rho"] * cv * m["theta"] + 0.5 * m["rho"] * (m["ux"] ** 2 + m["uy"] ** 2)).sum()
+    assert abs(d[3] - e) < 1e-12 * e
+    assert d[4] == pytest.approx(m["rho"].min(), rel=1e-14)
+    assert d[5] == pytest.approx(m["theta"].min(), rel=1e-14)
+    cfl = (np.sqrt(m["ux"] ** 2 + m["uy"] ** 2) + np.sqrt(case.gamma * m["theta"] / 3.0)).max()
+    assert d[6] == pytest.approx(cfl, rel=1e-13)
+    assert d[7] == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_roundtrip_is_bitwise(hl, precision):
+    case = inputs.random_smooth(40, 30, seed=2, amp=0.05, mu=2e-3, sigma=0.5)
+    a = hl.Solver(case.nx, case.ny, precision=precision, **case.params())
+    a.init(*case.fields())
+    a.step(10)
+    blob = a.state()
+    a.step(10)
+    b = hl.Solver(case.nx, case.ny, precision=precision, **case.params())
+    b.set_state(blob)
+    assert b.step_count == 10
+    b.step(10)
+    assert np.array_equal(a.populations(), b.populations())
+    ma, mb = a.macros(), b.macros()
+    for k in ma:
+        assert np.array_equal(ma[k], mb[k]), k
+    # a corrupted header is refused
+    bad = blob.copy()
+    bad[0] ^= 0xFF
+    with pytest.raises(hl.HlbmError) as e:
+        b.set_state(bad)
+    assert e.value.code == hl.HLBM_ERR_STATE
+
+
+def test_error_paths(hl):
+    case = inputs.random_smooth(16, 16, seed=1)
+    s = hl.Solver(16, 16, precision=1, **case.params())
+    with pytest.raises(hl.HlbmError) as e:
+        s.step(1)
+    assert e.value.code == hl.HLBM_ERR_STATE
+    # CFL check on the initial state
+    fast = hl.Solver(16, 16, precision=1, check_cfl=1, **{k: v for k, v in case.params().items()})
+    ux = np.full((16, 16), 0.9)
+    with pytest.raises(hl.HlbmError) as e:
+        fast.init(case.rho, ux, case.uy, case.theta)
+    assert e.value.code == hl.HLBM_ERR_CFL
+    # a NaN planted in the host input is caught by the periodic check
+    chk = hl.Solver(16, 16, precision=1, diag_every=2, **case.params())
+    rho = case.rho.copy()
+    rho[3, 4] = np.nan
+    chk.init(rho, case.ux, case.uy, case.theta)
+    with pytest.raises(hl.HlbmError) as e:
+        chk.step(4)
+    assert e.value.code == hl.HLBM_ERR_NONFINITE
