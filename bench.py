@@ -38,7 +38,7 @@ METRIC, UNIT = "MLUPS", "MLUPS"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -103,7 +103,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -254,7 +254,11 @@ def run_ours(args):
     prec = hlbm.HLBM_FP32 if args.precision == "fp32" else hlbm.HLBM_FP64
     case = workload(args.n)
     cells = case.nx * case.ny
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: torch's default stream has handle 0, which the C ABI
+    # reads as "create your own stream"; events and flushes must share the
+    # library's stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     s = hlbm.Solver(case.nx, case.ny, stream=stream.cuda_stream, precision=prec, **case.params())
     s.init(*case.fields())
 
