@@ -156,6 +156,37 @@ const char *hlbm_last_error(const hlbm_handle *h);
 /* HLBM_ABI_VERSION of the loaded library. */
 int hlbm_abi_version(void);
 
+/* Largest grid (nx * ny cells) that hlbm_diagnostics_noalloc accepts. */
+#define HLBM_NOALLOC_MAX_CELLS 16777216
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory -- code that must live inside a device
+ * memory budget it does not own, or that runs while another component is
+ * building a CUDA graph -- and still need the checks of hlbm_diagnostics.
+ *
+ * Same results, in the same order, as hlbm_diagnostics, for a state that
+ * the caller holds: `state` points to device memory with 13 planes of
+ * [ny][pitch] elements (FP64 or FP32 per `precision`: 9 post-collision
+ * populations, s, a1_xx, a1_xy, a1_yy), the layout hlbm_get_state copies
+ * after its header.  gamma is the heat capacity ratio of the case.  out is
+ * a host array of 8 doubles; the call waits for `stream` (a cudaStream_t,
+ * NULL for the legacy default stream) before returning.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * is one file-scope device array of (1024 * 8 + 8) doubles (65.6 KB), which
+ * every GPU that loads the library holds until the process exits.  Grids
+ * above HLBM_NOALLOC_MAX_CELLS cells are rejected with HLBM_ERR_ARG, as are
+ * nx, ny < 1, pitch < nx, gamma <= 1 and NULL pointers.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array and each overwrites what it reads, so
+ * results never depend on earlier calls; calls that overlap on the GPU
+ * (other streams or threads) race on it and must be serialised by the
+ * caller. */
+int hlbm_diagnostics_noalloc(const void *state, int precision, int nx, int ny, int pitch, double gamma,
+                             double out[8], void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,9 @@ ENTRY_POINTS = (
     "hlbm_create", "hlbm_init_fields", "hlbm_step", "hlbm_get_macros", "hlbm_get_populations",
     "hlbm_diagnostics", "hlbm_state_bytes", "hlbm_get_state", "hlbm_set_state", "hlbm_step_count",
     "hlbm_synchronize", "hlbm_destroy", "hlbm_strerror", "hlbm_last_error", "hlbm_abi_version",
+    "hlbm_diagnostics_noalloc",
 )
+HLBM_NOALLOC_MAX_CELLS = 16777216
 
 
 class hlbm_params(ctypes.Structure):
@@ -114,6 +116,9 @@ def _lib():
         lib.hlbm_last_error.argtypes = [_P]
         lib.hlbm_abi_version.restype = ctypes.c_int
         lib.hlbm_abi_version.argtypes = []
+        lib.hlbm_diagnostics_noalloc.restype = ctypes.c_int
+        lib.hlbm_diagnostics_noalloc.argtypes = [_PD, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_double, _PD, _P]
         _libh = lib
         return lib
 
@@ -249,6 +254,21 @@ def hlbm_synchronize(h):
 def hlbm_destroy(h):
     if h:
         _lib().hlbm_destroy(h)
+
+
+def hlbm_diagnostics_noalloc(state_ptr, precision, nx, ny, pitch, gamma, stream=None):
+    """Diagnostics of a caller-held device state without any allocation by
+    the library (for callers that may not allocate device memory).
+    state_ptr: device address of 13 planes [ny][pitch].  Grids above
+    HLBM_NOALLOC_MAX_CELLS cells are refused."""
+    out = np.zeros(8)
+    code = _lib().hlbm_diagnostics_noalloc(state_ptr, int(precision), int(nx), int(ny), int(pitch),
+                                           float(gamma), out.ctypes.data, stream or None)
+    if code != HLBM_OK and int(nx) * int(ny) > HLBM_NOALLOC_MAX_CELLS:
+        raise HlbmError(code, f"{int(nx) * int(ny)} cells exceed the static scratch capacity of "
+                              f"{HLBM_NOALLOC_MAX_CELLS} cells")
+    _check(code)
+    return out
 
 
 # ---- convenience wrapper ----------------------------------------------------------
