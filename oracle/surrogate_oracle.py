@@ -1,0 +1,112 @@
+"""FP64 CPU reference of the learned K-step surrogate -- TEST INFRASTRUCTURE.
+
+Only tests/ may import this module.  It states, in plain numpy, the network
+the GPU kernels implement, so that their forward outputs and gradients can
+be checked element by element.
+
+Network: a stack of 3x3 convolutions with periodic padding on a [B, C, H, W]
+field; GELU (the exact form 0.5 x (1 + erf(x / sqrt 2))) after every layer
+but the last; the output is added to the input (the network predicts the
+change of the normalised state over K time steps).  Loss: mean squared
+error over all elements.
+
+Definitions (written out, no library convolution):
+  conv(x, W, b)[n, o, i, j] = b[o] + sum_c sum_{p,q in -1..1}
+                              W[o, c, p+1, q+1] x[n, c, (i+p) mod H, (j+q) mod W]
+The backward pass applies the chain rule to these sums.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+try:
+    from scipy.special import erf as _erf
+except Exception:  # pragma: no cover - scipy is present in the test image
+    _erf = np.vectorize(math.erf)
+
+SQRT2 = math.sqrt(2.0)
+INV_SQRT_2PI = 1.0 / math.sqrt(2.0 * math.pi)
+
+
+def conv3x3_periodic(x, W, b):
+    """x [N, C, H, W], W [O, C, 3, 3], b [O] -> [N, O, H, W]."""
+    N, C, H, Wd = x.shape
+    O = W.shape[0]
+    out = np.zeros((N, O, H, Wd))
+    for p in (-1, 0, 1):
+        for q in (-1, 0, 1):
+            # xs[n, c, i, j] = x[n, c, (i+p) mod H, (j+q) mod W]
+            xs = np.roll(x, shift=(-p, -q), axis=(2, 3))
+            out += np.einsum("oc,ncij->noij", W[:, :, p + 1, q + 1], xs)
+    return out + b[None, :, None, None]
+
+
+def conv3x3_periodic_backward(x, W, dout):
+    """Gradients of sum(dout * conv(x, W, b)) with respect to x, W and b."""
+    dx = np.zeros_like(x)
+    dW = np.zeros_like(W)
+    for p in (-1, 0, 1):
+        for q in (-1, 0, 1):
+            xs = np.roll(x, shift=(-p, -q), axis=(2, 3))
+            dW[:, :, p + 1, q + 1] = np.einsum("noij,ncij->oc", dout, xs)
+            # d/dxs = W^T dout, and xs is x shifted by (-p, -q): shift back
+            dxs = np.einsum("oc,noij->ncij", W[:, :, p + 1, q + 1], dout)
+            dx += np.roll(dxs, shift=(p, q), axis=(2, 3))
+    db = dout.sum(axis=(0, 2, 3))
+    return dx, dW, db
+
+
+def gelu(x):
+    return 0.5 * x * (1.0 + _erf(x / SQRT2))
+
+
+def gelu_grad(x):
+    """d/dx of 0.5 x (1 + erf(x / sqrt 2)) = Phi(x) + x phi(x)."""
+    return 0.5 * (1.0 + _erf(x / SQRT2)) + x * INV_SQRT_2PI * np.exp(-0.5 * x * x)
+
+
+def forward(params, x):
+    """params: list of (W, b); returns (y, cache)."""
+    acts = [x]
+    pre = []
+    h = x
+    L = len(params)
+    for l, (W, b) in enumerate(params):
+        z = conv3x3_periodic(h, W, b)
+        pre.append(z)
+        h = gelu(z) if l < L - 1 else z
+        acts.append(h)
+    y = x + h
+    return y, (acts, pre)
+
+
+def loss(y, target):
+    return float(np.mean((y - target) ** 2))
+
+
+def backward(params, cache, y, target):
+    """Gradients of loss(y, target) with respect to every (W, b) and x."""
+    acts, pre = cache
+    L = len(params)
+    dy = 2.0 * (y - target) / y.size
+    dh = dy.copy()
+    grads = [None] * L
+    for l in range(L - 1, -1, -1):
+        dz = dh * gelu_grad(pre[l]) if l < L - 1 else dh
+        W, _ = params[l]
+        dx, dW, db = conv3x3_periodic_backward(acts[l], W, dz)
+        grads[l] = (dW, db)
+        dh = dx
+    dx_total = dy + dh  # residual path
+    return grads, dx_total
+
+
+def adam_update(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba 2015) on arrays, returning new (p, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v

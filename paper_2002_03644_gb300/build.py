@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libhlbm.so")
-SOURCES = [os.path.join(CSRC, "hlbm_api.cu"), os.path.join(CSRC, "hlbm_noalloc.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("hlbm_api.cu", "hlbm_noalloc.cu", "hlbm_surrogate.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
 

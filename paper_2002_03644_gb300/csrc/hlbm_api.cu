@@ -10,15 +10,18 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "hlbm.h"
 #include "hlbm_device.cuh"
+#include "hlbm_tma.cuh"
 
 using namespace hlbm;
 
 namespace {
 
-constexpr int TX32 = 32, TY32 = 16, NT32 = 256;  // FP32 tile
 constexpr int TX64 = 32, TY64 = 8, NT64 = 256;   // FP64 tile
 constexpr int DIAG_BLOCKS = 2 * 152;
 constexpr uint64_t STATE_MAGIC = 0x31305453424c4848ull;  // "HHLBST01"
@@ -28,6 +31,14 @@ struct StateHeader {
     int32_t abi, precision, nx, ny, pitch, nplane;
     int64_t step;
     int64_t payload_bytes;
+    float ref[9];  // reference populations of the 16-bit storage forms
+    int32_t pad;
+};
+
+template <typename T, typename S>
+struct Types {
+    using t = T;
+    using s = S;
 };
 
 }  // namespace
@@ -37,7 +48,8 @@ struct hlbm_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
-    size_t esize = 0;         // bytes per state element
+    size_t fsize = 0;         // bytes per stored population
+    size_t asize = 0;         // bytes per auxiliary element (s, a1)
     int pitch = 0;
     size_t plane = 0;         // elements per plane
     void *state[2] = {nullptr, nullptr};
@@ -46,6 +58,12 @@ struct hlbm_handle {
     double *diag_partial = nullptr;
     double *diag_out = nullptr;
     KParams kp;
+    TmaMaps maps[2];            // tensor maps of state[0] and state[1] (FP32)
+    bool tma_ready = false;
+    int tma_grid = 0;
+    int tma_variant = 0;        // FP32 kernel choice, fixed at create
+    int tile_variant = 0;
+    int *d_err = nullptr;       // device-side timeout flag of the TMA kernel
     int64_t step = 0;
     bool initialized = false;
     char err[256] = {0};
@@ -69,29 +87,182 @@ static int cuda_fail(hlbm_handle *h, cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
     } while (0)
 
-template <typename T, int TX, int TY, int NT>
-static cudaError_t launch_step(hlbm_handle *h, const void *in, void *out)
+// Population and auxiliary planes of state copy idx: 9 planes of S::raw,
+// then 4 planes of T (s, a1_xx, a1_xy, a1_yy).
+template <typename T, typename S>
+static typename S::raw *pop_planes(const hlbm_handle *h, int idx)
+{
+    return static_cast<typename S::raw *>(h->state[idx]);
+}
+
+template <typename T, typename S>
+static T *aux_planes(const hlbm_handle *h, int idx)
+{
+    return reinterpret_cast<T *>(static_cast<char *>(h->state[idx]) + 9 * h->plane * sizeof(typename S::raw));
+}
+
+// Call fn(Types<T, S>{}) for the handle's precision.
+template <typename Fn>
+static cudaError_t with_types(const hlbm_handle *h, Fn &&fn)
+{
+    switch (h->p.precision) {
+    case HLBM_FP64: return fn(Types<double, FullStore<double>>{});
+    case HLBM_FP32_F16POP: return fn(Types<float, HalfStore>{});
+    case HLBM_FP32_BF16POP: return fn(Types<float, BF16Store>{});
+    default: return fn(Types<float, FullStore<float>>{});
+    }
+}
+
+template <typename T, typename S, int TX, int TY, int NT>
+static cudaError_t launch_step(hlbm_handle *h)
 {
     using Geo = TileGeom<T, TX, TY>;
     static bool attr_done[64] = {false};
     if (!attr_done[h->device & 63]) {
-        cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<T, TX, TY, NT>,
+        cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<T, S, TX, TY, NT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo::smem_bytes);
         if (e != cudaSuccess) return e;
         attr_done[h->device & 63] = true;
     }
     dim3 grid((h->p.nx + TX - 1) / TX, (h->p.ny + TY - 1) / TY);
-    fused_step_kernel<T, TX, TY, NT><<<grid, NT, Geo::smem_bytes, h->stream>>>(
-        static_cast<const T *>(in), static_cast<T *>(out), h->kp);
+    const int a = h->cur, b = h->cur ^ 1;
+    fused_step_kernel<T, S, TX, TY, NT><<<grid, NT, Geo::smem_bytes, h->stream>>>(
+        pop_planes<T, S>(h, a), aux_planes<T, S>(h, a), pop_planes<T, S>(h, b), aux_planes<T, S>(h, b), h->kp);
+    return cudaGetLastError();
+}
+
+// FP32 kernels.  By default grids of up to 2048^2 cells use the plain tiled
+// kernel with 32x32 tiles and larger grids the persistent TMA kernel with
+// 32x16 tiles (the faster of the two at each size in GB300 sweeps of the
+// vortex).  HLBM_FP32_TMA=<k> forces TMA tile k, HLBM_FP32_TMA=-1 the plain
+// kernel with HLBM_FP32_TILE=<k> (tuning sweeps).
+constexpr int kNumFp32Tiles = 5;  // plain: 32x16x256, 64x16x256, 32x8x128, 64x32x512, 32x32x512
+constexpr int kNumTma = 4;        // TMA: 32x16x512, 32x16x256, 64x16x512, 32x32x512
+
+static int env_choice(const char *name, int dflt, int lo, int hi)
+{
+    const char *e = getenv(name);
+    if (!e) return dflt;
+    const int v = atoi(e);
+    return (v >= lo && v < hi) ? v : dflt;
+}
+
+
+template <int TX, int TY, int NT>
+static cudaError_t tma_grid_size(hlbm_handle *h, int *grid)
+{
+    using G = TmaGeom<TX, TY>;
+    cudaError_t e = cudaFuncSetAttribute(fused_step_tma_kernel<TX, TY, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_step_tma_kernel<TX, TY, NT>, NT, G::smem_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((h->p.nx + TX - 1) / TX) * ((h->p.ny + TY - 1) / TY);
+    const int g = (per_sm > 0 ? per_sm : 1) * sms;
+    *grid = g < tiles ? g : tiles;
+    return cudaSuccess;
+}
+
+template <int TX, int TY>
+static bool encode_maps(hlbm_handle *h, void *state, TmaMaps *m)
+{
+    using G = TmaGeom<TX, TY>;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)h->p.ny, (cuuint64_t)NPLANE};
+    const cuuint64_t strides[2] = {(cuuint64_t)h->pitch * 4, (cuuint64_t)h->plane * 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint32_t boxF[3] = {G::BX, G::F_ROWS, 9}, boxS[3] = {G::BX, G::S_ROWS, 1}, boxA[3] = {G::BX, G::A_ROWS, 3};
+    const cuuint32_t *boxes[3] = {boxF, boxS, boxA};
+    CUtensorMap *out[3] = {&m->f, &m->s, &m->a};
+    for (int k = 0; k < 3; k++) {
+        if (encode(out[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, state, dims, strides, boxes[k], estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+// The TMA kernel serves grids that have interior tiles (away from every
+// edge by the halo); smaller grids, or a tensor map the driver refuses,
+// use the plain tiled kernel, which handles every tile itself.
+template <int TX, int TY, int NT>
+static cudaError_t prepare_tma(hlbm_handle *h)
+{
+    if (h->p.nx < TX + 8 + 2 * TX || h->p.ny < TY + 6 + 2 * TY) return cudaSuccess;
+    if (!encode_maps<TX, TY>(h, h->state[0], &h->maps[0]) || !encode_maps<TX, TY>(h, h->state[1], &h->maps[1]))
+        return cudaSuccess;
+    const cudaError_t e = tma_grid_size<TX, TY, NT>(h, &h->tma_grid);
+    if (e == cudaSuccess) h->tma_ready = true;
+    return e;
+}
+
+static cudaError_t setup_fp32_kernel(hlbm_handle *h)
+{
+    const bool large = (long long)h->p.nx * h->p.ny > 2048ll * 2048ll;
+    h->tma_variant = env_choice("HLBM_FP32_TMA", large ? 0 : -1, -1, kNumTma);
+    h->tile_variant = env_choice("HLBM_FP32_TILE", 4, 0, kNumFp32Tiles);
+    switch (h->tma_variant) {
+    case -1: return cudaSuccess;
+    case 1: return prepare_tma<32, 16, 256>(h);
+    case 2: return prepare_tma<64, 16, 512>(h);
+    case 3: return prepare_tma<32, 32, 512>(h);
+    default: return prepare_tma<32, 16, 512>(h);
+    }
+}
+
+template <int TX, int TY, int NT>
+static cudaError_t launch_tma(hlbm_handle *h)
+{
+    using G = TmaGeom<TX, TY>;
+    fused_step_tma_kernel<TX, TY, NT><<<h->tma_grid, NT, G::smem_bytes, h->stream>>>(
+        h->maps[h->cur], static_cast<const float *>(h->state[h->cur]), static_cast<float *>(h->state[h->cur ^ 1]),
+        h->kp, h->d_err);
     return cudaGetLastError();
 }
 
 static cudaError_t launch_one_step(hlbm_handle *h)
 {
-    const void *in = h->state[h->cur];
-    void *out = h->state[h->cur ^ 1];
-    if (h->p.precision == HLBM_FP64) return launch_step<double, TX64, TY64, NT64>(h, in, out);
-    return launch_step<float, TX32, TY32, NT32>(h, in, out);
+    using F32 = FullStore<float>;
+    if (h->p.precision == HLBM_FP64) return launch_step<double, FullStore<double>, TX64, TY64, NT64>(h);
+    if (h->p.precision == HLBM_FP32_F16POP) return launch_step<float, HalfStore, 32, 32, 512>(h);
+    if (h->p.precision == HLBM_FP32_BF16POP) return launch_step<float, BF16Store, 32, 32, 512>(h);
+    if (h->tma_ready) {
+        switch (h->tma_variant) {
+        case 1: return launch_tma<32, 16, 256>(h);
+        case 2: return launch_tma<64, 16, 512>(h);
+        case 3: return launch_tma<32, 32, 512>(h);
+        default: return launch_tma<32, 16, 512>(h);
+        }
+    }
+    switch (h->tile_variant) {
+    case 1: return launch_step<float, F32, 64, 16, 256>(h);
+    case 2: return launch_step<float, F32, 32, 8, 128>(h);
+    case 3: return launch_step<float, F32, 64, 32, 512>(h);
+    case 4: return launch_step<float, F32, 32, 32, 512>(h);
+    default: return launch_step<float, F32, 32, 16, 256>(h);
+    }
+}
+
+// Device timeout flag -> HLBM_ERR_TIMEOUT (called after a stream sync).
+static int check_timeout(hlbm_handle *h)
+{
+    if (!h->d_err) return HLBM_OK;
+    int flag = 0;
+    CK(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "timeout flag");
+    if (flag) return fail(h, HLBM_ERR_TIMEOUT, "a bulk copy into shared memory did not arrive within 1 s");
+    return HLBM_OK;
 }
 
 static dim3 cell_grid(const hlbm_handle *h, dim3 blk)
@@ -114,7 +285,7 @@ static int validate(const hlbm_params *p)
     if (!p) return HLBM_ERR_ARG;
     if (p->nx < 1 || p->ny < 1) return HLBM_ERR_ARG;
     if ((long long)p->nx * p->ny > (1ll << 28)) return HLBM_ERR_ARG;
-    if (p->precision != HLBM_FP64 && p->precision != HLBM_FP32) return HLBM_ERR_UNSUPPORTED;
+    if (p->precision < HLBM_FP64 || p->precision > HLBM_FP32_BF16POP) return HLBM_ERR_UNSUPPORTED;
     if (p->phi_mode != 0 && p->phi_mode != 1) return HLBM_ERR_ARG;
     if (!(p->gamma > 1.0) || !(p->Pr > 0.0) || !(p->mu >= 0.0) || !(p->sigma >= 0.0 && p->sigma <= 1.0))
         return HLBM_ERR_ARG;
@@ -160,6 +331,16 @@ static void fill_kparams(hlbm_handle *h)
         k.d_gy[s] = r * v * (1.0 - t - v * v);
         host_feq(r, u, v, t, k.d_F[s]);
     }
+    k.f_gm1 = (float)k.gm1;
+    k.f_s2exp = (float)(k.inv_cv / std::log(2.0));
+    k.f_mu = (float)k.mu; k.f_lam = (float)k.lambda;
+    k.f_sigma = (float)k.sigma; k.f_one_m_sigma = (float)(1.0 - k.sigma);
+    k.f_two_m_gamma = (float)k.two_minus_gamma;
+    for (int s = 0; s < 4; s++) {
+        k.f_d_rho[s] = (float)k.d_rho[s]; k.f_d_ux[s] = (float)k.d_ux[s]; k.f_d_uy[s] = (float)k.d_uy[s];
+        k.f_d_th[s] = (float)k.d_th[s]; k.f_d_s[s] = (float)k.d_s[s];
+        for (int i = 0; i < 9; i++) k.f_d_F[s][i] = (float)k.d_F[s][i];
+    }
 }
 
 extern "C" {
@@ -177,6 +358,7 @@ const char *hlbm_strerror(int code)
     case HLBM_ERR_STATE: return "call out of order or state mismatch";
     case HLBM_ERR_NOMEM: return "out of memory";
     case HLBM_ERR_UNSUPPORTED: return "option not supported";
+    case HLBM_ERR_TIMEOUT: return "device-side wait timed out";
     default: return "unknown status";
     }
 }
@@ -195,6 +377,7 @@ void hlbm_destroy(hlbm_handle *h)
     cudaFree(h->staging);
     cudaFree(h->diag_partial);
     cudaFree(h->diag_out);
+    cudaFree(h->d_err);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -217,15 +400,17 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         if (e != cudaSuccess) { delete h; return HLBM_ERR_CUDA; }
         h->own_stream = true;
     }
-    h->esize = params->precision == HLBM_FP64 ? sizeof(double) : sizeof(float);
+    h->asize = params->precision == HLBM_FP64 ? sizeof(double) : sizeof(float);
+    h->fsize = params->precision >= HLBM_FP32_F16POP ? 2 : h->asize;
     h->pitch = (params->nx + 31) / 32 * 32;
     h->plane = (size_t)h->pitch * params->ny;
-    const size_t bytes = h->plane * NPLANE * h->esize;
+    const size_t bytes = h->plane * (9 * h->fsize + 4 * h->asize);
     const size_t ncell = (size_t)params->nx * params->ny;
     if (cudaMalloc(&h->state[0], bytes) != cudaSuccess || cudaMalloc(&h->state[1], bytes) != cudaSuccess ||
         cudaMalloc(&h->staging, 9 * ncell * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->diag_partial, DIAG_BLOCKS * DIAG_NV * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&h->diag_out, DIAG_NV * sizeof(double)) != cudaSuccess) {
+        cudaMalloc(&h->diag_out, DIAG_NV * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         hlbm_destroy(h);
         return HLBM_ERR_NOMEM;
@@ -236,24 +421,34 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         hlbm_destroy(h);
         return HLBM_ERR_CUDA;
     }
+    if (cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream) != cudaSuccess) {
+        hlbm_destroy(h);
+        return HLBM_ERR_CUDA;
+    }
     fill_kparams(h);
+    if (params->precision == HLBM_FP32 && setup_fp32_kernel(h) != cudaSuccess) {
+        cudaGetLastError();
+        hlbm_destroy(h);
+        return HLBM_ERR_CUDA;
+    }
     *out = h;
     return HLBM_OK;
 }
 
 static int run_diagnostics(hlbm_handle *h, double out[8])
 {
-    const void *st = h->state[h->cur];
-    if (h->p.precision == HLBM_FP64)
-        diag_partial_kernel<double><<<DIAG_BLOCKS, DIAG_NT, 0, h->stream>>>(static_cast<const double *>(st), h->diag_partial, h->kp);
-    else
-        diag_partial_kernel<float><<<DIAG_BLOCKS, DIAG_NT, 0, h->stream>>>(static_cast<const float *>(st), h->diag_partial, h->kp);
-    CK(cudaGetLastError(), "diag_partial_kernel");
+    CK(with_types(h, [&](auto ty) {
+           using T = typename decltype(ty)::t;
+           using S = typename decltype(ty)::s;
+           diag_partial_kernel<T, S><<<DIAG_BLOCKS, DIAG_NT, 0, h->stream>>>(
+               pop_planes<T, S>(h, h->cur), aux_planes<T, S>(h, h->cur), h->diag_partial, h->kp);
+           return cudaGetLastError();
+       }), "diag_partial_kernel");
     diag_final_kernel<<<1, DIAG_NT, 0, h->stream>>>(h->diag_partial, DIAG_BLOCKS, h->diag_out);
     CK(cudaGetLastError(), "diag_final_kernel");
     CK(cudaMemcpyAsync(out, h->diag_out, DIAG_NV * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "diag copy");
     CK(cudaStreamSynchronize(h->stream), "diag sync");
-    return HLBM_OK;
+    return check_timeout(h);
 }
 
 int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const double *uy, const double *theta,
@@ -278,14 +473,31 @@ int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const 
     } else {
         for (int k = 0; k < 5; k++) dev[k] = src[k];
     }
+    if (h->p.precision >= HLBM_FP32_F16POP) {
+        // reference equilibrium of the mean state for the 16-bit forms
+        field_sums_partial_kernel<<<DIAG_BLOCKS, DIAG_NT, 0, h->stream>>>(dev[0], dev[1], dev[2], dev[3],
+                                                                          (long long)n, h->diag_partial);
+        CK(cudaGetLastError(), "field_sums_partial_kernel");
+        diag_final_kernel<<<1, DIAG_NT, 0, h->stream>>>(h->diag_partial, DIAG_BLOCKS, h->diag_out);
+        CK(cudaGetLastError(), "diag_final_kernel");
+        double sums[DIAG_NV];
+        CK(cudaMemcpyAsync(sums, h->diag_out, sizeof(sums), cudaMemcpyDeviceToHost, h->stream), "sums copy");
+        CK(cudaStreamSynchronize(h->stream), "sums sync");
+        const double rm = sums[0] / (double)n;
+        if (!(rm > 0.0) || !std::isfinite(sums[1]) || !std::isfinite(sums[2]) || !(sums[3] > 0.0))
+            return fail(h, HLBM_ERR_NONFINITE, "initial fields hold non-finite or non-positive values");
+        double fr[9];
+        host_feq(rm, sums[1] / sums[0], sums[2] / sums[0], sums[3] / (double)n, fr);
+        for (int i = 0; i < 9; i++) h->kp.f_ref[i] = (float)fr[i];
+    }
     dim3 blk(32, 8);
-    if (h->p.precision == HLBM_FP64)
-        init_kernel<double><<<cell_grid(h, blk), blk, 0, h->stream>>>(dev[0], dev[1], dev[2], dev[3], dev[4],
-                                                                        static_cast<double *>(h->state[0]), h->kp);
-    else
-        init_kernel<float><<<cell_grid(h, blk), blk, 0, h->stream>>>(dev[0], dev[1], dev[2], dev[3], dev[4],
-                                                                       static_cast<float *>(h->state[0]), h->kp);
-    CK(cudaGetLastError(), "init_kernel");
+    CK(with_types(h, [&](auto ty) {
+           using T = typename decltype(ty)::t;
+           using S = typename decltype(ty)::s;
+           init_kernel<T, S><<<cell_grid(h, blk), blk, 0, h->stream>>>(dev[0], dev[1], dev[2], dev[3], dev[4],
+                                                                       pop_planes<T, S>(h, 0), aux_planes<T, S>(h, 0), h->kp);
+           return cudaGetLastError();
+       }), "init_kernel");
     h->cur = 0;
     h->step = 0;
     h->initialized = true;
@@ -349,14 +561,14 @@ static int extract(hlbm_handle *h, double *rho, double *ux, double *uy, double *
         for (int k = 0; k < 7; k++) dev[k] = dst[k];
     }
     dim3 blk(32, 8);
-    const void *st = h->state[h->cur];
-    if (h->p.precision == HLBM_FP64)
-        macros_kernel<double><<<cell_grid(h, blk), blk, 0, h->stream>>>(static_cast<const double *>(st), dev[0], dev[1], dev[2],
-                                                                          dev[3], dev[4], dev[5], dev[6], h->kp);
-    else
-        macros_kernel<float><<<cell_grid(h, blk), blk, 0, h->stream>>>(static_cast<const float *>(st), dev[0], dev[1], dev[2],
-                                                                         dev[3], dev[4], dev[5], dev[6], h->kp);
-    CK(cudaGetLastError(), "macros_kernel");
+    CK(with_types(h, [&](auto ty) {
+           using T = typename decltype(ty)::t;
+           using S = typename decltype(ty)::s;
+           macros_kernel<T, S><<<cell_grid(h, blk), blk, 0, h->stream>>>(pop_planes<T, S>(h, h->cur),
+                                                                        aux_planes<T, S>(h, h->cur), dev[0], dev[1],
+                                                                        dev[2], dev[3], dev[4], dev[5], dev[6], h->kp);
+           return cudaGetLastError();
+       }), "macros_kernel");
     if (mem_kind == HLBM_MEM_HOST) {
         for (int k = 0; k < 7; k++) {
             if (!dst[k] || !dev[k]) continue;
@@ -365,7 +577,7 @@ static int extract(hlbm_handle *h, double *rho, double *ux, double *uy, double *
         }
     }
     CK(cudaStreamSynchronize(h->stream), "get sync");
-    return HLBM_OK;
+    return check_timeout(h);
 }
 
 int hlbm_get_macros(hlbm_handle *h, double *rho, double *ux, double *uy, double *theta, double *s, double *a1,
@@ -393,13 +605,13 @@ int hlbm_synchronize(hlbm_handle *h)
     if (!h) return HLBM_ERR_ARG;
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     CK(cudaStreamSynchronize(h->stream), "sync");
-    return HLBM_OK;
+    return check_timeout(h);
 }
 
 int hlbm_state_bytes(const hlbm_handle *h, size_t *bytes)
 {
     if (!h || !bytes) return HLBM_ERR_ARG;
-    *bytes = sizeof(StateHeader) + h->plane * NPLANE * h->esize;
+    *bytes = sizeof(StateHeader) + h->plane * (9 * h->fsize + 4 * h->asize);
     return HLBM_OK;
 }
 
@@ -416,6 +628,7 @@ int hlbm_get_state(hlbm_handle *h, void *buf, size_t bytes)
     hd.magic = STATE_MAGIC; hd.abi = HLBM_ABI_VERSION; hd.precision = h->p.precision;
     hd.nx = h->p.nx; hd.ny = h->p.ny; hd.pitch = h->pitch; hd.nplane = NPLANE; hd.step = h->step;
     hd.payload_bytes = (int64_t)(need - sizeof(StateHeader));
+    for (int i = 0; i < 9; i++) hd.ref[i] = h->kp.f_ref[i];
     memcpy(buf, &hd, sizeof(hd));
     CK(cudaMemcpyAsync(static_cast<char *>(buf) + sizeof(hd), h->state[h->cur], (size_t)hd.payload_bytes,
                        cudaMemcpyDeviceToHost, h->stream), "state copy");
@@ -439,10 +652,300 @@ int hlbm_set_state(hlbm_handle *h, const void *buf, size_t bytes)
     CK(cudaMemcpyAsync(h->state[0], static_cast<const char *>(buf) + sizeof(hd), (size_t)hd.payload_bytes,
                        cudaMemcpyHostToDevice, h->stream), "state copy");
     CK(cudaStreamSynchronize(h->stream), "state sync");
+    for (int i = 0; i < 9; i++) h->kp.f_ref[i] = hd.ref[i];
     h->cur = 0;
     h->step = hd.step;
     h->initialized = true;
     return HLBM_OK;
+}
+
+}  // extern "C"
+
+// ---- batches --------------------------------------------------------------------------
+namespace {
+
+struct TileShape {
+    int tx, ty, nt;
+};
+constexpr TileShape kBatchTiles[] = {{32, 16, 256}, {64, 16, 256}, {32, 8, 128}, {64, 32, 512}, {32, 32, 512}};
+constexpr int kNumBatchTiles = 5;
+constexpr int kGraphSteps = 16;  // steps per captured graph (even: parity returns)
+
+}  // namespace
+
+struct hlbm_batch {
+    std::vector<hlbm_handle *> cases;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int tile = 0;
+    // device tables for the current tile shape
+    KParams *d_kps = nullptr;
+    CasePlanes *d_planes = nullptr;
+    int *d_tile_case = nullptr, *d_tile_first = nullptr;
+    int ntiles = 0;
+    int grid = 0;
+    size_t smem = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // starting parity 0 / 1
+};
+
+template <int TX, int TY, int NT>
+static cudaError_t batch_launch(hlbm_batch *b, int parity)
+{
+    BatchTables tab;
+    tab.kps = b->d_kps; tab.planes = b->d_planes; tab.tile_case = b->d_tile_case; tab.tile_first = b->d_tile_first;
+    tab.ntiles = b->ntiles;
+    batched_step_kernel<TX, TY, NT><<<b->grid, NT, b->smem, b->stream>>>(tab, parity);
+    return cudaGetLastError();
+}
+
+static cudaError_t batch_launch_any(hlbm_batch *b, int parity)
+{
+    switch (b->tile) {
+    case 1: return batch_launch<64, 16, 256>(b, parity);
+    case 2: return batch_launch<32, 8, 128>(b, parity);
+    case 3: return batch_launch<64, 32, 512>(b, parity);
+    case 4: return batch_launch<32, 32, 512>(b, parity);
+    default: return batch_launch<32, 16, 256>(b, parity);
+    }
+}
+
+template <int TX, int TY, int NT>
+static cudaError_t batch_kernel_setup(hlbm_batch *b, int *per_sm)
+{
+    using Geo = TileGeom<float, TX, TY>;
+    b->smem = (Geo::smem_bytes + 15) / 16 * 16 + sizeof(KParams);
+    cudaError_t e = cudaFuncSetAttribute(batched_step_kernel<TX, TY, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batched_step_kernel<TX, TY, NT>, NT, b->smem);
+}
+
+static void batch_drop_graphs(hlbm_batch *b)
+{
+    for (int q = 0; q < 2; q++) {
+        if (b->graph[q]) cudaGraphExecDestroy(b->graph[q]);
+        b->graph[q] = nullptr;
+    }
+}
+
+// (Re)build the tile tables and the persistent grid for tile shape b->tile.
+static int batch_tables(hlbm_batch *b)
+{
+    batch_drop_graphs(b);
+    const TileShape ts = kBatchTiles[b->tile];
+    const int nc = (int)b->cases.size();
+    std::vector<int> tile_case, tile_first(nc);
+    std::vector<KParams> kps(nc);
+    std::vector<CasePlanes> planes(nc);
+    for (int c = 0; c < nc; c++) {
+        hlbm_handle *h = b->cases[c];
+        tile_first[c] = (int)tile_case.size();
+        const int nt = ((h->p.nx + ts.tx - 1) / ts.tx) * ((h->p.ny + ts.ty - 1) / ts.ty);
+        tile_case.insert(tile_case.end(), nt, c);
+        kps[c] = h->kp;
+        for (int q = 0; q < 2; q++) {
+            planes[c].inF[q] = pop_planes<float, FullStore<float>>(h, q);
+            planes[c].inA[q] = aux_planes<float, FullStore<float>>(h, q);
+            planes[c].outF[q] = pop_planes<float, FullStore<float>>(h, q ^ 1);
+            planes[c].outA[q] = aux_planes<float, FullStore<float>>(h, q ^ 1);
+        }
+    }
+    b->ntiles = (int)tile_case.size();
+    cudaFree(b->d_kps); cudaFree(b->d_planes); cudaFree(b->d_tile_case); cudaFree(b->d_tile_first);
+    b->d_kps = nullptr; b->d_planes = nullptr; b->d_tile_case = nullptr; b->d_tile_first = nullptr;
+    if (cudaMalloc(&b->d_kps, nc * sizeof(KParams)) != cudaSuccess ||
+        cudaMalloc(&b->d_planes, nc * sizeof(CasePlanes)) != cudaSuccess ||
+        cudaMalloc(&b->d_tile_case, b->ntiles * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_tile_first, nc * sizeof(int)) != cudaSuccess)
+        return HLBM_ERR_NOMEM;
+    if (cudaMemcpy(b->d_kps, kps.data(), nc * sizeof(KParams), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_planes, planes.data(), nc * sizeof(CasePlanes), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_tile_case, tile_case.data(), b->ntiles * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_tile_first, tile_first.data(), nc * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return HLBM_ERR_CUDA;
+    int per_sm = 0, sms = 0;
+    cudaError_t e;
+    switch (b->tile) {
+    case 1: e = batch_kernel_setup<64, 16, 256>(b, &per_sm); break;
+    case 2: e = batch_kernel_setup<32, 8, 128>(b, &per_sm); break;
+    case 3: e = batch_kernel_setup<64, 32, 512>(b, &per_sm); break;
+    case 4: e = batch_kernel_setup<32, 32, 512>(b, &per_sm); break;
+    default: e = batch_kernel_setup<32, 16, 256>(b, &per_sm); break;
+    }
+    if (e != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+        return HLBM_ERR_CUDA;
+    const int g = (per_sm > 0 ? per_sm : 1) * sms;
+    b->grid = g < b->ntiles ? g : b->ntiles;
+    return HLBM_OK;
+}
+
+// All cases initialised and at one parity; returns that parity or -1.
+static int batch_parity(const hlbm_batch *b)
+{
+    int par = -1;
+    for (hlbm_handle *h : b->cases) {
+        if (!h->initialized) return -1;
+        if (par < 0) par = h->cur;
+        else if (par != h->cur) return -1;
+    }
+    return par;
+}
+
+static int batch_advance(hlbm_batch *b, int64_t n)
+{
+    int par = batch_parity(b);
+    if (par < 0) return HLBM_ERR_STATE;
+    int64_t done = 0;
+    while (n - done >= kGraphSteps) {
+        if (!b->graph[par]) {
+            cudaGraph_t g;
+            if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HLBM_ERR_CUDA;
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < kGraphSteps && e == cudaSuccess; k++) e = batch_launch_any(b, par ^ (k & 1));
+            const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) return HLBM_ERR_CUDA;
+            e = cudaGraphInstantiate(&b->graph[par], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return HLBM_ERR_CUDA;
+        }
+        if (cudaGraphLaunch(b->graph[par], b->stream) != cudaSuccess) return HLBM_ERR_CUDA;
+        done += kGraphSteps;
+    }
+    for (; done < n; done++) {
+        if (batch_launch_any(b, par) != cudaSuccess) return HLBM_ERR_CUDA;
+        par ^= 1;
+    }
+    for (hlbm_handle *h : b->cases) {
+        h->cur = (int)((h->cur + n) & 1);
+        h->step += n;
+    }
+    return HLBM_OK;
+}
+
+extern "C" {
+
+void hlbm_batch_destroy(hlbm_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    cudaFree(b->d_kps); cudaFree(b->d_planes); cudaFree(b->d_tile_case); cudaFree(b->d_tile_first);
+    for (hlbm_handle *h : b->cases) hlbm_destroy(h);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int hlbm_batch_create(const hlbm_params *params, int ncase, void *stream, hlbm_batch **out)
+{
+    if (!out || !params || ncase < 1) return HLBM_ERR_ARG;
+    *out = nullptr;
+    for (int c = 0; c < ncase; c++)
+        if (params[c].precision != HLBM_FP32) return HLBM_ERR_UNSUPPORTED;
+    hlbm_batch *b = new (std::nothrow) hlbm_batch();
+    if (!b) return HLBM_ERR_NOMEM;
+    if (cudaGetDevice(&b->device) != cudaSuccess) { delete b; return HLBM_ERR_CUDA; }
+    if (stream) {
+        b->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return HLBM_ERR_CUDA; }
+        b->own_stream = true;
+    }
+    for (int c = 0; c < ncase; c++) {
+        hlbm_handle *h = nullptr;
+        const int r = hlbm_create(&params[c], b->stream, &h);
+        if (r != HLBM_OK) { hlbm_batch_destroy(b); return r; }
+        b->cases.push_back(h);
+    }
+    const int r = batch_tables(b);
+    if (r != HLBM_OK) { hlbm_batch_destroy(b); return r; }
+    *out = b;
+    return HLBM_OK;
+}
+
+int hlbm_batch_case(hlbm_batch *b, int index, hlbm_handle **h)
+{
+    if (!b || !h || index < 0 || index >= (int)b->cases.size()) return HLBM_ERR_ARG;
+    *h = b->cases[index];
+    return HLBM_OK;
+}
+
+int hlbm_batch_step(hlbm_batch *b, int64_t n)
+{
+    if (!b || n < 0) return HLBM_ERR_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return HLBM_ERR_CUDA;
+    return batch_advance(b, n);
+}
+
+int hlbm_batch_tile(const hlbm_batch *b, int *index, int *tx, int *ty, int *threads)
+{
+    if (!b) return HLBM_ERR_ARG;
+    if (index) *index = b->tile;
+    if (tx) *tx = kBatchTiles[b->tile].tx;
+    if (ty) *ty = kBatchTiles[b->tile].ty;
+    if (threads) *threads = kBatchTiles[b->tile].nt;
+    return HLBM_OK;
+}
+
+int hlbm_batch_autotune(hlbm_batch *b, int *tile)
+{
+    if (!b) return HLBM_ERR_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return HLBM_ERR_CUDA;
+    if (batch_parity(b) < 0) return HLBM_ERR_STATE;
+    // snapshot every case (the trials advance the states)
+    std::vector<void *> saved(b->cases.size(), nullptr);
+    std::vector<size_t> sizes(b->cases.size());
+    std::vector<int> cur(b->cases.size());
+    std::vector<int64_t> steps(b->cases.size());
+    int rc = HLBM_OK;
+    for (size_t c = 0; c < b->cases.size() && rc == HLBM_OK; c++) {
+        hlbm_handle *h = b->cases[c];
+        sizes[c] = h->plane * (9 * h->fsize + 4 * h->asize);
+        cur[c] = h->cur;
+        steps[c] = h->step;
+        if (cudaMalloc(&saved[c], sizes[c]) != cudaSuccess) rc = HLBM_ERR_NOMEM;
+        else if (cudaMemcpyAsync(saved[c], h->state[h->cur], sizes[c], cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+            rc = HLBM_ERR_CUDA;
+    }
+    float best = 1e30f;
+    int best_tile = b->tile;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == HLBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = HLBM_ERR_CUDA;
+    for (int t = 0; t < kNumBatchTiles && rc == HLBM_OK; t++) {
+        b->tile = t;
+        rc = batch_tables(b);
+        if (rc != HLBM_OK) break;
+        int par = batch_parity(b);
+        for (int k = 0; k < 2 && rc == HLBM_OK; k++, par ^= 1)
+            if (batch_launch_any(b, par) != cudaSuccess) rc = HLBM_ERR_CUDA;
+        cudaEventRecord(e0, b->stream);
+        for (int k = 0; k < 6 && rc == HLBM_OK; k++, par ^= 1)
+            if (batch_launch_any(b, par) != cudaSuccess) rc = HLBM_ERR_CUDA;
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = HLBM_ERR_CUDA;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == HLBM_OK && ms < best) { best = ms; best_tile = t; }
+    }
+    // restore the states and the parity
+    for (size_t c = 0; c < b->cases.size(); c++) {
+        hlbm_handle *h = b->cases[c];
+        if (saved[c] && rc == HLBM_OK &&
+            cudaMemcpyAsync(h->state[cur[c]], saved[c], sizes[c], cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+            rc = HLBM_ERR_CUDA;
+        h->cur = cur[c];
+        h->step = steps[c];
+    }
+    cudaStreamSynchronize(b->stream);
+    for (void *p : saved) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->tile = best_tile;
+    const int r2 = batch_tables(b);
+    if (rc == HLBM_OK) rc = r2;
+    if (tile) *tile = best_tile;
+    return rc;
 }
 
 }  // extern "C"

@@ -38,6 +38,8 @@
 // corner, then a Dirichlet x side.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -58,6 +60,58 @@ struct KParams {
     // Dirichlet side constants: macros, entropy, closure defect, populations
     double d_rho[4], d_ux[4], d_uy[4], d_th[4], d_s[4], d_gx[4], d_gy[4];
     double d_F[4][9];
+    // the same constants rounded to FP32 on the host, so that FP32 kernels
+    // never touch the (slow) FP64 pipe
+    float f_gm1, f_s2exp, f_mu, f_lam, f_sigma, f_one_m_sigma, f_two_m_gamma;
+    float f_d_rho[4], f_d_ux[4], f_d_uy[4], f_d_th[4], f_d_s[4];
+    float f_d_F[4][9];
+    // reference populations subtracted before 16-bit storage (precision
+    // forms HLBM_FP32_F16POP / HLBM_FP32_BF16POP; unused otherwise)
+    float f_ref[9];
+};
+
+// ---- population storage ----------------------------------------------------------
+// The nine population planes are stored as S::raw; the four auxiliary planes
+// (s, a1_xx, a1_xy, a1_yy) always in the arithmetic type T.  Full storage
+// keeps F_i itself; the 16-bit forms keep F_i - f_ref_i, the difference from
+// one reference equilibrium per case, rounded to FP16 or BF16.
+template <typename T> struct FullStore {
+    using raw = T;
+    static __device__ __forceinline__ T get(raw r, int, const KParams &) { return r; }
+    static __device__ __forceinline__ raw put(T v, int, const KParams &) { return v; }
+};
+struct HalfStore {
+    using raw = __half;
+    static __device__ __forceinline__ float get(raw r, int i, const KParams &kp) { return __half2float(r) + kp.f_ref[i]; }
+    static __device__ __forceinline__ raw put(float v, int i, const KParams &kp) { return __float2half_rn(v - kp.f_ref[i]); }
+};
+struct BF16Store {
+    using raw = __nv_bfloat16;
+    static __device__ __forceinline__ float get(raw r, int i, const KParams &kp) { return __bfloat162float(r) + kp.f_ref[i]; }
+    static __device__ __forceinline__ raw put(float v, int i, const KParams &kp) { return __float2bfloat16_rn(v - kp.f_ref[i]); }
+};
+// auxiliary plane indices
+constexpr int A_S = 0, A_XX = 1, A_XY = 2, A_YY = 3;
+
+// Dirichlet constants in the kernel's precision.
+template <typename T> struct Side;
+template <> struct Side<float> {
+    const KParams &k;
+    __device__ float rho(int s) const { return k.f_d_rho[s]; }
+    __device__ float ux(int s) const { return k.f_d_ux[s]; }
+    __device__ float uy(int s) const { return k.f_d_uy[s]; }
+    __device__ float th(int s) const { return k.f_d_th[s]; }
+    __device__ float s_(int s) const { return k.f_d_s[s]; }
+    __device__ float F(int s, int i) const { return k.f_d_F[s][i]; }
+};
+template <> struct Side<double> {
+    const KParams &k;
+    __device__ double rho(int s) const { return k.d_rho[s]; }
+    __device__ double ux(int s) const { return k.d_ux[s]; }
+    __device__ double uy(int s) const { return k.d_uy[s]; }
+    __device__ double th(int s) const { return k.d_th[s]; }
+    __device__ double s_(int s) const { return k.d_s[s]; }
+    __device__ double F(int s, int i) const { return k.d_F[s][i]; }
 };
 
 __device__ __forceinline__ constexpr int cxi(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
@@ -95,11 +149,9 @@ template <> struct Consts<float> {
     float gm1, s2exp, mu, two_mu, lam, sigma, one_m_sigma, two_m_gamma;
     __device__ void load(const KParams &kp)
     {
-        gm1 = (float)kp.gm1;
-        s2exp = (float)(kp.inv_cv * 1.4426950408889634);  // 1 / (c_v ln 2)
-        mu = (float)kp.mu; two_mu = 2.0f * mu; lam = (float)kp.lambda;
-        sigma = (float)kp.sigma; one_m_sigma = (float)(1.0 - kp.sigma);
-        two_m_gamma = (float)kp.two_minus_gamma;
+        gm1 = kp.f_gm1; s2exp = kp.f_s2exp;  // 1 / (c_v ln 2)
+        mu = kp.f_mu; two_mu = 2.0f * mu; lam = kp.f_lam;
+        sigma = kp.f_sigma; one_m_sigma = kp.f_one_m_sigma; two_m_gamma = kp.f_two_m_gamma;
     }
     // theta = rho^(gamma-1) exp(s / c_v) = 2^((gamma-1) log2 rho + s / (c_v ln 2))
     __device__ __forceinline__ float theta(float rho, float s) const { return exp2f(fmaf(gm1, __log2f(rho), s * s2exp)); }
@@ -123,29 +175,6 @@ __device__ __forceinline__ void moments(const T f[9], T &rho, T &jx, T &jy)
     rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-}
-
-// Van Albada limited slope from the two one-sided differences; zero at an
-// extremum (a b <= 0).
-template <typename T>
-__device__ __forceinline__ T va_slope(T a, T b)
-{
-    const T ab = a * b;
-    return ab > T(0) ? ab * (a + b) / (a * a + b * b) : T(0);
-}
-
-// u ds/dx from limited, upwinded face values (non-conservative advection of
-// Sec. 3.4).  For u > 0 the term is u [(s0 + d0/2) - (sm + dm/2)]; for u < 0
-// the same expression on the mirrored stencil (sm <-> sp, smm <-> spp) times
-// |u|, since the limited slope is odd in its arguments.  u = 0 gives zero.
-template <typename T>
-__device__ __forceinline__ T muscl_adv(T u, T smm, T sm, T s0, T sp, T spp)
-{
-    const bool pos = u > T(0);
-    const T q2 = pos ? smm : spp, q1 = pos ? sm : sp, qm = pos ? sp : sm;
-    const T d10 = s0 - q1;
-    const T dd = d10 + T(0.5) * (va_slope(d10, qm - s0) - va_slope(q1 - q2, d10));
-    return fabs(u) * dd;
 }
 
 // Post-collision populations from level quantities: F = f^eq + omega f1 +
@@ -191,12 +220,19 @@ __device__ __forceinline__ void build_populations(T rho, T ux, T uy, T th, T axx
 }
 
 // ---- the fused step ------------------------------------------------------------
+// Shared memory per tile (elements of T):
+//   sS  s(n) on tile + 3                      (TX+6)(TY+6)
+//   sF  F_i(n) on tile + 2, 9 planes          9 (TX+4)(TY+4)
+//   m*  rho, u_x, u_y, theta of level n on tile + 2   4 (TX+4)(TY+4)
+//   n*  rho, u_x, u_y, theta, s of level n+1 on tile + 1   5 (TX+2)(TY+2)
+// F(n) is read from HBM once (phase 1, coalesced rows) and every later use --
+// the pull of phase 2 and the projection of phase 3 -- reads shared memory.
 template <typename T, int TX, int TY>
 struct TileGeom {
     static constexpr int R3X = TX + 6, R3Y = TY + 6, N3 = R3X * R3Y;
     static constexpr int R2X = TX + 4, R2Y = TY + 4, N2 = R2X * R2Y;
     static constexpr int R1X = TX + 2, R1Y = TY + 2, N1 = R1X * R1Y;
-    static constexpr size_t smem_bytes = sizeof(T) * (size_t)(N3 + 4 * N2 + 10 * N1);
+    static constexpr size_t smem_bytes = sizeof(T) * (size_t)(N3 + 13 * N2 + 5 * N1);
 };
 
 // Classification of a tile + 1 cell for phase 2: 0 compute, 1 Dirichlet
@@ -212,53 +248,126 @@ __device__ __forceinline__ int classify_r1(int gx, int gy, const KParams &kp, in
     return (cx || cy) ? 2 : 0;
 }
 
-template <typename T, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT)
-fused_step_kernel(const T *__restrict__ in, T *__restrict__ out, const KParams kp)
+// Division and reciprocal: the hardware approximation in FP32 (about 2 ulp,
+// well inside the FP32 parity bound), IEEE division in FP64.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
+// Van Albada limited slope from the two one-sided differences; zero at an
+// extremum (a b <= 0).
+template <typename T>
+__device__ __forceinline__ T va_slope(T a, T b)
+{
+    const T ab = a * b;
+    return ab > T(0) ? fdiv(ab * (a + b), a * a + b * b) : T(0);
+}
+
+// u ds/dx from limited, upwinded face values (non-conservative advection of
+// Sec. 3.4).  For u > 0 the term is u [(s0 + d0/2) - (sm + dm/2)]; for u < 0
+// the same expression on the mirrored stencil (sm <-> sp, smm <-> spp) times
+// |u|, since the limited slope is odd in its arguments.  u = 0 gives zero.
+template <typename T>
+__device__ __forceinline__ T muscl_adv(T u, T smm, T sm, T s0, T sp, T spp)
+{
+    const bool pos = u > T(0);
+    const T q2 = pos ? smm : spp, q1 = pos ? sm : sp, qm = pos ? sp : sm;
+    const T d10 = s0 - q1;
+    const T dd = d10 + T(0.5) * (va_slope(d10, qm - s0) - va_slope(q1 - q2, d10));
+    return fabs(u) * dd;
+}
+
+// closure defect Gamma_a = rho u_a (1 - theta - u_a^2) (Sec. 2.3)
+template <typename T>
+__device__ __forceinline__ T gamma_defect(T rho, T ua, T th)
+{
+    return rho * ua * (T(1) - th - ua * ua);
+}
+
+// One tile of Algorithm 1, steps 5-11 (all threads of the CTA take part;
+// the caller separates consecutive tiles with a barrier).
+template <typename T, typename S, int TX, int TY, int NT>
+__device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
+                                          typename S::raw *__restrict__ outF, T *__restrict__ outA,
+                                          const KParams &kp, const int x0, const int y0, unsigned char *smem_raw)
 {
     using Geo = TileGeom<T, TX, TY>;
     constexpr int R3X = Geo::R3X, N3 = Geo::N3, R2X = Geo::R2X, N2 = Geo::N2, R1X = Geo::R1X, N1 = Geo::N1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sS = reinterpret_cast<T *>(smem_raw);
-    T *mRho = sS + N3, *mUx = mRho + N2, *mUy = mUx + N2, *mTh = mUy + N2;
+    T *sF = sS + N3;
+    T *mRho = sF + 9 * N2, *mUx = mRho + N2, *mUy = mUx + N2, *mTh = mUy + N2;
     T *nRho = mTh + N2, *nUx = nRho + N1, *nUy = nUx + N1, *nTh = nUy + N1, *nS = nTh + N1;
-    T *nGx = nS + N1, *nGy = nGx + N1, *nMxx = nGy + N1, *nMxy = nMxx + N1, *nMyy = nMxy + N1;
 
     Consts<T> cs;
     cs.load(kp);
+    const Side<T> side{kp};
     const T third = T(1) / T(3);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int pitch = kp.pitch;
     const long long P = kp.plane;
     const bool interior = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= kp.nx && y0 + TY + 3 <= kp.ny;
 
-    // phase 0: s(n) on tile + 3
+    // phase 0 + 1 loads: s(n) on tile + 3 and F(n) on tile + 2 go to shared
+    // memory first, with all of a thread's loads in flight together
     for (int c = threadIdx.x; c < N3; c += NT) {
         const int ly = c / R3X, lx = c - ly * R3X;
         const int gx = x0 - 3 + lx, gy = y0 - 3 + ly;
         const int o = interior ? gy * pitch + gx : locate(gx, gy, kp, pitch);
-        sS[c] = o >= 0 ? __ldg(in + P_S * P + o) : T(kp.d_s[-o - 1]);
+        sS[c] = o >= 0 ? __ldg(inA + A_S * P + o) : side.s_(-o - 1);
+    }
+    {
+        constexpr int ITER = (N2 + NT - 1) / NT;
+        T f[ITER][9];
+        int oc[ITER];
+#pragma unroll
+        for (int it = 0; it < ITER; it++) {
+            const int c = threadIdx.x + it * NT;
+            oc[it] = 0;
+            if (c < N2) {
+                const int ly = c / R2X, lx = c - ly * R2X;
+                const int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
+                const int o = interior ? gy * pitch + gx : locate(gx, gy, kp, pitch);
+                oc[it] = o;
+                if (o >= 0) {
+#pragma unroll
+                    for (int i = 0; i < 9; i++) f[it][i] = S::get(inF[i * P + o], i, kp);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; i++) f[it][i] = side.F(-o - 1, i);
+                }
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < ITER; it++) {
+            const int c = threadIdx.x + it * NT;
+            if (c < N2) {
+#pragma unroll
+                for (int i = 0; i < 9; i++) sF[i * N2 + c] = f[it][i];
+            }
+        }
+        (void)oc;
     }
     __syncthreads();
 
-    // phase 1: rho, u, theta of level n on tile + 2
+    // phase 1: the level-n rho, u, theta on tile + 2
     for (int c = threadIdx.x; c < N2; c += NT) {
         const int ly = c / R2X, lx = c - ly * R2X;
-        const int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
-        const int o = interior ? gy * pitch + gx : locate(gx, gy, kp, pitch);
         T rho, ux, uy, th;
-        if (o >= 0) {
+        bool dirichlet = false;
+        int sd = 0;
+        if (!interior) {
+            const int o = locate(x0 - 2 + lx, y0 - 2 + ly, kp, pitch);
+            if (o < 0) { dirichlet = true; sd = -o - 1; }
+        }
+        if (!dirichlet) {
             T f[9];
 #pragma unroll
-            for (int i = 0; i < 9; i++) f[i] = __ldg(in + i * P + o);
+            for (int i = 0; i < 9; i++) f[i] = sF[i * N2 + c];
             T jx, jy;
             moments(f, rho, jx, jy);
-            const T ir = T(1) / rho;
+            const T ir = fdiv(T(1), rho);
             ux = jx * ir; uy = jy * ir;
             th = cs.theta(rho, sS[(ly + 1) * R3X + lx + 1]);
         } else {
-            const int sd = -o - 1;
-            rho = T(kp.d_rho[sd]); ux = T(kp.d_ux[sd]); uy = T(kp.d_uy[sd]); th = T(kp.d_th[sd]);
+            rho = side.rho(sd); ux = side.ux(sd); uy = side.uy(sd); th = side.th(sd);
         }
         mRho[c] = rho; mUx[c] = ux; mUy[c] = uy; mTh[c] = th;
     }
@@ -272,13 +381,20 @@ fused_step_kernel(const T *__restrict__ in, T *__restrict__ out, const KParams k
             int sd = 0;
             const int kind = classify_r1(gx, gy, kp, &sd);
             if (kind == 1) {
-                nRho[c] = T(kp.d_rho[sd]); nUx[c] = T(kp.d_ux[sd]); nUy[c] = T(kp.d_uy[sd]);
-                nTh[c] = T(kp.d_th[sd]); nS[c] = T(kp.d_s[sd]);
-                nGx[c] = T(kp.d_gx[sd]); nGy[c] = T(kp.d_gy[sd]);
-                nMxx[c] = T(0); nMxy[c] = T(0); nMyy[c] = T(0);
+                nRho[c] = side.rho(sd); nUx[c] = side.ux(sd); nUy[c] = side.uy(sd);
+                nTh[c] = side.th(sd); nS[c] = side.s_(sd);
                 continue;
             }
             if (kind == 2) continue;
+        }
+        // a1(n) of this cell (phi_mode 0): issued first so the loads overlap
+        // the stencil arithmetic below
+        T axx = T(0), axy = T(0), ayy = T(0);
+        if (kp.phi_mode == 0) {
+            const int o = interior ? gy * pitch + gx : locate(gx, gy, kp, pitch);
+            if (o >= 0) {
+                axx = __ldg(inA + A_XX * P + o); axy = __ldg(inA + A_XY * P + o); ayy = __ldg(inA + A_YY * P + o);
+            }
         }
         // step 7: entropy update from level-n fields
         const int k2 = (ly + 1) * R2X + lx + 1;
@@ -296,44 +412,22 @@ fused_step_kernel(const T *__restrict__ in, T *__restrict__ out, const KParams k
         const T p0 = rt * third;
         T phi;
         if (kp.phi_mode == 0) {
-            const int o = interior ? gy * pitch + gx : locate(gx, gy, kp, pitch);
-            T axx = T(0), axy = T(0), ayy = T(0);
-            if (o >= 0) {
-                axx = __ldg(in + P_AXX * P + o); axy = __ldg(in + P_AXY * P + o); ayy = __ldg(in + P_AYY * P + o);
-            }
-            phi = -(cs.two_mu / (cs.two_mu + p0)) * (axx * dxux + axy * (dyux + dxuy) + ayy * dyuy);
+            phi = -fdiv(cs.two_mu, cs.two_mu + p0) * (axx * dxux + axy * (dyux + dxuy) + ayy * dyuy);
         } else {
             const T d1 = dxux - dyuy, d2 = dyux + dxuy;
             phi = cs.mu * (d1 * d1 + d2 * d2);
         }
-        const T s1 = s0 - adv + (cs.lam * lap + phi) / rt;
-        // steps 5-6: pull the post-collision populations, moments
+        const T s1 = s0 - adv + fdiv(cs.lam * lap + phi, rt);
+        // steps 5-6: pull the post-collision populations (shared memory), moments
         T f[9];
-        if (interior) {
-            const int o = gy * pitch + gx;
 #pragma unroll
-            for (int i = 0; i < 9; i++) f[i] = __ldg(in + i * P + (o - cyi(i) * pitch - cxi(i)));
-        } else {
-#pragma unroll
-            for (int i = 0; i < 9; i++) {
-                const int o = locate(gx - cxi(i), gy - cyi(i), kp, pitch);
-                f[i] = o >= 0 ? __ldg(in + i * P + o) : T(kp.d_F[-o - 1][i]);
-            }
-        }
+        for (int i = 0; i < 9; i++) f[i] = sF[i * N2 + k2 - cxi(i) - cyi(i) * R2X];
         T rho1, jx, jy;
         moments(f, rho1, jx, jy);
-        const T ir = T(1) / rho1;
-        const T ux1 = jx * ir, uy1 = jy * ir;
-        const T th1 = cs.theta(rho1, s1);  // step 8
-        nRho[c] = rho1; nUx[c] = ux1; nUy[c] = uy1; nTh[c] = th1; nS[c] = s1;
-        nGx[c] = rho1 * ux1 * (T(1) - th1 - ux1 * ux1);
-        nGy[c] = rho1 * uy1 * (T(1) - th1 - uy1 * uy1);
-        if (kp.sigma_nonzero) {
-            const T diag = (f[5] + f[6]) + (f[7] + f[8]);
-            nMxx[c] = (f[1] + f[3]) + diag;
-            nMyy[c] = (f[2] + f[4]) + diag;
-            nMxy[c] = (f[5] - f[6]) + (f[7] - f[8]);
-        }
+        const T ir = fdiv(T(1), rho1);
+        nRho[c] = rho1; nUx[c] = jx * ir; nUy[c] = jy * ir;
+        nTh[c] = cs.theta(rho1, s1);  // step 8
+        nS[c] = s1;
     }
     __syncthreads();
 
@@ -349,9 +443,7 @@ fused_step_kernel(const T *__restrict__ in, T *__restrict__ out, const KParams k
             if ((gx < 0 || gx >= kp.nx) && kp.bc[gx < 0 ? 0 : 1] == BC_ZEROGRAD) sx = gx < 0 ? 0 : kp.nx - 1;
             if ((gy < 0 || gy >= kp.ny) && kp.bc[gy < 0 ? 2 : 3] == BC_ZEROGRAD) sy = gy < 0 ? 0 : kp.ny - 1;
             const int src = (sy - (y0 - 1)) * R1X + (sx - (x0 - 1));
-            nRho[c] = nRho[src]; nUx[c] = nUx[src]; nUy[c] = nUy[src]; nTh[c] = nTh[src];
-            nS[c] = nS[src]; nGx[c] = nGx[src]; nGy[c] = nGy[src];
-            nMxx[c] = nMxx[src]; nMxy[c] = nMxy[src]; nMyy[c] = nMyy[src];
+            nRho[c] = nRho[src]; nUx[c] = nUx[src]; nUy[c] = nUy[src]; nTh[c] = nTh[src]; nS[c] = nS[src];
         }
         __syncthreads();
     }
@@ -363,17 +455,20 @@ fused_step_kernel(const T *__restrict__ in, T *__restrict__ out, const KParams k
         if (gx >= kp.nx || gy >= kp.ny) continue;
         const int k = (ly + 1) * R1X + lx + 1;
         const T rho = nRho[k], ux = nUx[k], uy = nUy[k], th = nTh[k];
-        const T dxux = T(0.5) * (nUx[k + 1] - nUx[k - 1]);
+        const T uxm = nUx[k - 1], uxp = nUx[k + 1], uym = nUy[k - R1X], uyp = nUy[k + R1X];
+        const T dxux = T(0.5) * (uxp - uxm);
         const T dyux = T(0.5) * (nUx[k + R1X] - nUx[k - R1X]);
         const T dxuy = T(0.5) * (nUy[k + 1] - nUy[k - 1]);
-        const T dyuy = T(0.5) * (nUy[k + R1X] - nUy[k - R1X]);
+        const T dyuy = T(0.5) * (uyp - uym);
         const T p = rho * th * third;
         // E1: upwind difference of Gamma by the sign of the cell's velocity
-        const T gxc = nGx[k], gyc = nGy[k];
-        const T e1xx = ux > T(0) ? gxc - nGx[k - 1]
-                     : (ux < T(0) ? nGx[k + 1] - gxc : T(0.5) * (nGx[k + 1] - nGx[k - 1]));
-        const T e1yy = uy > T(0) ? gyc - nGy[k - R1X]
-                     : (uy < T(0) ? nGy[k + R1X] - gyc : T(0.5) * (nGy[k + R1X] - nGy[k - R1X]));
+        const T gxc = gamma_defect(rho, ux, th), gyc = gamma_defect(rho, uy, th);
+        const T gxm = gamma_defect(nRho[k - 1], uxm, nTh[k - 1]);
+        const T gxp = gamma_defect(nRho[k + 1], uxp, nTh[k + 1]);
+        const T gym = gamma_defect(nRho[k - R1X], uym, nTh[k - R1X]);
+        const T gyp = gamma_defect(nRho[k + R1X], uyp, nTh[k + R1X]);
+        const T e1xx = ux > T(0) ? gxc - gxm : (ux < T(0) ? gxp - gxc : T(0.5) * (gxp - gxm));
+        const T e1yy = uy > T(0) ? gyc - gym : (uy < T(0) ? gyp - gyc : T(0.5) * (gyp - gym));
         const T e2 = p * cs.two_m_gamma * (dxux + dyuy);
         const T ex = e1xx + e2, ey = e1yy + e2;
         // a1^FD = -tau_bar p (grad u + grad u^T - div u I), tau_bar p = mu + p/2
@@ -381,9 +476,17 @@ fused_step_kernel(const T *__restrict__ in, T *__restrict__ out, const KParams k
         const T fdxx = cfd * (dxux - dyuy), fdxy = cfd * (dyux + dxuy);
         T axx, axy, ayy;
         if (kp.sigma_nonzero) {
-            const T prxx = nMxx[k] - rho * ux * ux - p + T(0.5) * ex;
-            const T pryy = nMyy[k] - rho * uy * uy - p + T(0.5) * ey;
-            const T prxy = nMxy[k] - rho * ux * uy;
+            // second raw moments of the pulled populations of this cell
+            const int k2 = (ly + 2) * R2X + lx + 2;
+            T f[9];
+#pragma unroll
+            for (int i = 0; i < 9; i++) f[i] = sF[i * N2 + k2 - cxi(i) - cyi(i) * R2X];
+            const T diag = (f[5] + f[6]) + (f[7] + f[8]);
+            const T mxx = (f[1] + f[3]) + diag, myy = (f[2] + f[4]) + diag;
+            const T mxy = (f[5] - f[6]) + (f[7] - f[8]);
+            const T prxx = mxx - rho * ux * ux - p + T(0.5) * ex;
+            const T pryy = myy - rho * uy * uy - p + T(0.5) * ey;
+            const T prxy = mxy - rho * ux * uy;
             axx = cs.sigma * prxx + cs.one_m_sigma * fdxx;
             ayy = cs.sigma * pryy - cs.one_m_sigma * fdxx;
             axy = cs.sigma * prxy + cs.one_m_sigma * fdxy;
@@ -391,25 +494,78 @@ fused_step_kernel(const T *__restrict__ in, T *__restrict__ out, const KParams k
             axx = fdxx; ayy = -fdxx; axy = fdxy;
         }
         // 1 - 1 / tau_bar with tau = mu / p
-        const T omega = (cs.two_mu - p) / (cs.two_mu + p);
+        const T omega = fdiv(cs.two_mu - p, cs.two_mu + p);
         T f[9];
         build_populations(rho, ux, uy, th, axx, axy, ayy, ex, ey, omega, f);
         const int o = gy * pitch + gx;
 #pragma unroll
-        for (int i = 0; i < 9; i++) out[i * P + o] = f[i];
-        out[P_S * P + o] = nS[k];
-        out[P_AXX * P + o] = axx;
-        out[P_AXY * P + o] = axy;
-        out[P_AYY * P + o] = ayy;
+        for (int i = 0; i < 9; i++) outF[i * P + o] = S::put(f[i], i, kp);
+        outA[A_S * P + o] = nS[k];
+        outA[A_XX * P + o] = axx;
+        outA[A_XY * P + o] = axy;
+        outA[A_YY * P + o] = ayy;
+    }
+}
+
+// One case: one CTA per tile.
+template <typename T, typename S, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
+fused_step_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
+                  typename S::raw *__restrict__ outF, T *__restrict__ outA, const KParams kp)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    step_tile<T, S, TX, TY, NT>(inF, inA, outF, outA, kp, blockIdx.x * TX, blockIdx.y * TY, smem_raw);
+}
+
+// ---- many cases in one persistent launch (FP32) -----------------------------------
+// Every case keeps its own ping-pong state and parameters; the tiles of all
+// cases form one list that a grid of resident CTAs walks.  The parameters
+// of the current case are copied to shared memory once per tile.
+struct CasePlanes {
+    const float *inF[2], *inA[2];  // read planes for parity 0 / 1
+    float *outF[2], *outA[2];      // written planes for parity 0 / 1
+};
+
+struct BatchTables {
+    const KParams *kps;       // [ncase]
+    const CasePlanes *planes; // [ncase]
+    const int *tile_case;     // [ntiles] case of each tile
+    const int *tile_first;    // [ncase] first tile index of each case
+    int ntiles;
+};
+
+template <int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
+batched_step_kernel(const BatchTables tab, const int parity)
+{
+    using Geo = TileGeom<float, TX, TY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    KParams &skp = *reinterpret_cast<KParams *>(smem_raw + (Geo::smem_bytes + 15) / 16 * 16);
+    for (int t = blockIdx.x; t < tab.ntiles; t += gridDim.x) {
+        const int c = tab.tile_case[t];
+        {
+            const int *src = reinterpret_cast<const int *>(tab.kps + c);
+            int *dst = reinterpret_cast<int *>(&skp);
+            for (int w = threadIdx.x; w < (int)(sizeof(KParams) / sizeof(int)); w += NT) dst[w] = __ldg(src + w);
+        }
+        __syncthreads();
+        const int local = t - tab.tile_first[c];
+        const int tiles_x = (skp.nx + TX - 1) / TX;
+        const int x0 = (local % tiles_x) * TX, y0 = (local / tiles_x) * TY;
+        const CasePlanes &pl = tab.planes[c];
+        step_tile<float, FullStore<float>, TX, TY, NT>(pl.inF[parity], pl.inA[parity], pl.outF[parity],
+                                                      pl.outA[parity], skp, x0, y0, smem_raw);
+        __syncthreads();
     }
 }
 
 // ---- initialisation (Algorithm 1, steps 1-4) -----------------------------------
 // In FP64 from FP64 caller fields (row-major [ny][nx]); writes the state in T.
-template <typename T>
+template <typename T, typename S>
 __global__ void init_kernel(const double *__restrict__ rho, const double *__restrict__ ux,
                             const double *__restrict__ uy, const double *__restrict__ th,
-                            const double *__restrict__ a1, T *__restrict__ out, const KParams kp)
+                            const double *__restrict__ a1, typename S::raw *__restrict__ outF,
+                            T *__restrict__ outA, const KParams kp)
 {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x;
     const int gy = blockIdx.y * blockDim.y + threadIdx.y;
@@ -448,17 +604,18 @@ __global__ void init_kernel(const double *__restrict__ rho, const double *__rest
     const long long P = kp.plane;
     const int o = gy * kp.pitch + gx;
 #pragma unroll
-    for (int i = 0; i < 9; i++) out[i * P + o] = (T)f[i];
-    out[P_S * P + o] = (T)(kp.cv * (log(t0) - kp.gm1 * log(r0)));
-    out[P_AXX * P + o] = (T)axx;
-    out[P_AXY * P + o] = (T)axy;
-    out[P_AYY * P + o] = (T)ayy;
+    for (int i = 0; i < 9; i++) outF[i * P + o] = S::put((T)f[i], i, kp);
+    outA[A_S * P + o] = (T)(kp.cv * (log(t0) - kp.gm1 * log(r0)));
+    outA[A_XX * P + o] = (T)axx;
+    outA[A_XY * P + o] = (T)axy;
+    outA[A_YY * P + o] = (T)ayy;
 }
 
 // ---- field extraction ----------------------------------------------------------
-template <typename T>
-__global__ void macros_kernel(const T *__restrict__ in, double *rho, double *ux, double *uy, double *th,
-                              double *s, double *a1, double *F, const KParams kp)
+template <typename T, typename S>
+__global__ void macros_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA, double *rho,
+                              double *ux, double *uy, double *th, double *s, double *a1, double *F,
+                              const KParams kp)
 {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x;
     const int gy = blockIdx.y * blockDim.y + threadIdx.y;
@@ -471,19 +628,19 @@ __global__ void macros_kernel(const T *__restrict__ in, double *rho, double *ux,
     const size_t n = (size_t)kp.nx * kp.ny;
     T f[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) f[i] = in[i * P + o];
+    for (int i = 0; i < 9; i++) f[i] = S::get(inF[i * P + o], i, kp);
     T r, jx, jy;
     moments(f, r, jx, jy);
-    const T sv = in[P_S * P + o];
+    const T sv = inA[A_S * P + o];
     if (rho) rho[c] = (double)r;
     if (ux) ux[c] = (double)(jx / r);
     if (uy) uy[c] = (double)(jy / r);
     if (th) th[c] = (double)cs.theta(r, sv);
     if (s) s[c] = (double)sv;
     if (a1) {
-        a1[c] = (double)in[P_AXX * P + o];
-        a1[n + c] = (double)in[P_AXY * P + o];
-        a1[2 * n + c] = (double)in[P_AYY * P + o];
+        a1[c] = (double)inA[A_XX * P + o];
+        a1[n + c] = (double)inA[A_XY * P + o];
+        a1[2 * n + c] = (double)inA[A_YY * P + o];
     }
     if (F) {
 #pragma unroll
@@ -495,9 +652,10 @@ __global__ void macros_kernel(const T *__restrict__ in, double *rho, double *ux,
 constexpr int DIAG_NT = 256;
 constexpr int DIAG_NV = 8;
 
-template <typename T>
+template <typename T, typename S>
 __global__ void __launch_bounds__(DIAG_NT)
-diag_partial_kernel(const T *__restrict__ in, double *__restrict__ partial, const KParams kp)
+diag_partial_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
+                    double *__restrict__ partial, const KParams kp)
 {
     Consts<T> cs;
     cs.load(kp);
@@ -509,12 +667,12 @@ diag_partial_kernel(const T *__restrict__ in, double *__restrict__ partial, cons
         const int o = gy * kp.pitch + gx;
         T f[9];
 #pragma unroll
-        for (int i = 0; i < 9; i++) f[i] = in[i * P + o];
+        for (int i = 0; i < 9; i++) f[i] = S::get(inF[i * P + o], i, kp);
         T r, jx, jy;
         moments(f, r, jx, jy);
         const double rho = (double)r;
         const double u = (double)jx / rho, v = (double)jy / rho;
-        const double th = (double)cs.theta(r, in[P_S * P + o]);
+        const double th = (double)cs.theta(r, inA[A_S * P + o]);
         const bool bad = !(rho > 0.0) || !(th > 0.0) || !isfinite(rho) || !isfinite(th) || !isfinite(u) || !isfinite(v);
         if (bad) { acc[7] += 1.0; continue; }
         acc[0] += rho; acc[1] += rho * u; acc[2] += rho * v;
@@ -537,6 +695,33 @@ diag_partial_kernel(const T *__restrict__ in, double *__restrict__ partial, cons
         __syncthreads();
     }
     if (threadIdx.x < DIAG_NV) partial[blockIdx.x * DIAG_NV + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Sums of rho, rho u_x, rho u_y and theta over FP64 caller fields (for the
+// reference equilibrium of the 16-bit storage forms); same partial layout as
+// diag_partial_kernel so that diag_final_kernel folds them.
+__global__ void __launch_bounds__(DIAG_NT)
+field_sums_partial_kernel(const double *__restrict__ rho, const double *__restrict__ ux,
+                          const double *__restrict__ uy, const double *__restrict__ th, long long n,
+                          double *__restrict__ partial)
+{
+    double acc[DIAG_NV] = {0.0, 0.0, 0.0, 0.0, 1e300, 1e300, 0.0, 0.0};
+    for (long long c = (long long)blockIdx.x * DIAG_NT + threadIdx.x; c < n; c += (long long)gridDim.x * DIAG_NT) {
+        acc[0] += rho[c]; acc[1] += rho[c] * ux[c]; acc[2] += rho[c] * uy[c]; acc[3] += th[c];
+    }
+    __shared__ double red[4][DIAG_NT];
+#pragma unroll
+    for (int k = 0; k < 4; k++) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = DIAG_NT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < DIAG_NV)
+        partial[blockIdx.x * DIAG_NV + threadIdx.x] = threadIdx.x < 4 ? red[threadIdx.x][0] : acc[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(DIAG_NT)

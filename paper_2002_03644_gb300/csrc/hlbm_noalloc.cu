@@ -12,6 +12,8 @@
 // to a kernel (on the host the name is only a stand-in, not a device
 // address); the first call on each device looks up the real address with
 // cudaGetSymbolAddress while that device is current and caches it.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -131,6 +133,8 @@ extern "C" int hlbm_diagnostics_noalloc(const void *state, int precision, int nx
     kp.cv = (1.0 / 3.0) / (gamma - 1.0);
     kp.inv_cv = 1.0 / kp.cv;
     kp.two_minus_gamma = 2.0 - gamma;
+    kp.f_gm1 = (float)kp.gm1;                     // FP32 copies read by FP32 kernels
+    kp.f_s2exp = (float)(kp.inv_cv / 0.6931471805599453);
 
     const long long ncell = (long long)nx * ny;
     const int nblocks = (int)((ncell + NA_CHUNK - 1) / NA_CHUNK);

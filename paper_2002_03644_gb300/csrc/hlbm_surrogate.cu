@@ -1,0 +1,554 @@
+// hlbm_surrogate.cu -- a learned K-step surrogate of the hybrid LBM step:
+// a stack of periodic 3x3 convolutions (GELU between them, the output added
+// to the input) trained on the GPU by the kernels of this file.
+//
+// Layout: activations NHWC (channels innermost), BF16, channel counts padded
+// to a multiple of 16; FP32 master weights W[l][co][ci][tap] (tap = 3 (p+1) +
+// (q+1) for the offset (p, q) in rows and columns) and their BF16 copies
+// arranged for the tensor-core B operand: Wb[tap][co][ci] (forward) and
+// Wd[tap'][ci][co] with the tap mirrored (input gradient).
+//
+// Convolution = implicit GEMM on the BF16 tensor cores (mma.sync m16n8k16,
+// FP32 accumulators): out[pixel, n] = sum_tap sum_k B[tap][n][k] *
+// in[pixel + offset(tap), k].  One warp computes 16 pixels x 64 outputs; the
+// epilogue adds the bias and, where the layer has one, applies GELU and
+// keeps the pre-activation for the backward pass.
+//
+// Weight gradient: dW[co][ci][tap] = sum_pixels dz[pixel, co] *
+// h[pixel + offset(tap), ci], reduced in FP32 per block and added with
+// atomics.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hlbm.h"
+
+namespace {
+
+constexpr int MAX_LAYERS = 8;
+constexpr int MAXC = 64;  // widest layer (padded channels)
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad_f(float x)
+{
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * __expf(-0.5f * x * x);
+}
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16 *p)
+{
+    return *reinterpret_cast<const uint32_t *>(p);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// in  [npix][CIN]  (NHWC, pixels n*H*W + i*W + j), CIN multiple of 16
+// B   [9][NOUT][CIN] BF16, NOUT multiple of 8 and <= 64
+// bias[nbias] FP32 added to the first nbias outputs (bias may be NULL)
+// mode 0: z_f32 = z, out_bf16 = z (no activation)
+// mode 1: z_f32 = z, out_bf16 = GELU(z)
+// mode 2 (input gradient): g = z * GELU'(zprev) (or z when zprev is NULL);
+//         z_f32 = g, out_bf16 = g
+// flip: use offset -(p, q) for tap (p, q) (input gradient)
+template <int CIN, int NOUT>
+__global__ void __launch_bounds__(128)
+conv_mma_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ B,
+                const float *__restrict__ bias, int nbias, __nv_bfloat16 *__restrict__ out_bf,
+                float *__restrict__ z_f32, const float *__restrict__ zprev, int npix, int H, int W, int mode, int flip)
+{
+    constexpr int NT = NOUT / 8;  // n tiles of 8
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int pix0 = (blockIdx.x * 4 + warp) * 16;
+    if (pix0 >= npix) return;
+    const int HW = H * W;
+    // the two pixel rows of this thread's A fragment
+    int pr[2];
+    pr[0] = pix0 + g;
+    pr[1] = pix0 + g + 8;
+    int pn[2], pi[2], pj[2];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int pp = pr[r] < npix ? pr[r] : npix - 1;
+        pn[r] = pp / HW;
+        const int rem = pp - pn[r] * HW;
+        pi[r] = rem / W;
+        pj[r] = rem - pi[r] * W;
+    }
+    float acc[NT][4];
+#pragma unroll
+    for (int n = 0; n < NT; n++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) acc[n][k] = 0.0f;
+
+#pragma unroll 1
+    for (int tap = 0; tap < 9; tap++) {
+        int dp = tap / 3 - 1, dq = tap % 3 - 1;
+        if (flip) { dp = -dp; dq = -dq; }
+        const __nv_bfloat16 *row[2];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int ii = wrap(pi[r] + dp, H), jj = wrap(pj[r] + dq, W);
+            row[r] = in + ((size_t)pn[r] * HW + (size_t)ii * W + jj) * CIN;
+        }
+        const __nv_bfloat16 *Bt = B + (size_t)tap * NOUT * CIN;
+#pragma unroll
+        for (int k0 = 0; k0 < CIN; k0 += 16) {
+            uint32_t a[4];
+            a[0] = ld_pair(row[0] + k0 + 2 * t4);
+            a[1] = ld_pair(row[1] + k0 + 2 * t4);
+            a[2] = ld_pair(row[0] + k0 + 8 + 2 * t4);
+            a[3] = ld_pair(row[1] + k0 + 8 + 2 * t4);
+#pragma unroll
+            for (int n = 0; n < NT; n++) {
+                const __nv_bfloat16 *bn = Bt + (size_t)(n * 8 + g) * CIN + k0;
+                uint32_t b[2];
+                b[0] = ld_pair(bn + 2 * t4);
+                b[1] = ld_pair(bn + 8 + 2 * t4);
+                mma_bf16(acc[n], a, b);
+            }
+        }
+    }
+    // epilogue: C fragment rows g, g+8; columns 2 t4, 2 t4 + 1 of each n tile
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int p = pix0 + g + 8 * r;
+        if (p >= npix) continue;
+#pragma unroll
+        for (int n = 0; n < NT; n++) {
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                const int col = n * 8 + 2 * t4 + e;
+                float z = acc[n][2 * r + e] + ((bias && col < nbias) ? bias[col] : 0.0f);
+                const size_t idx = (size_t)p * NOUT + col;
+                if (mode == 2) {
+                    if (zprev) z *= gelu_grad_f(zprev[idx]);
+                    out_bf[idx] = __float2bfloat16_rn(z);
+                    if (z_f32) z_f32[idx] = z;
+                } else {
+                    if (z_f32) z_f32[idx] = z;
+                    out_bf[idx] = __float2bfloat16_rn(mode == 1 ? gelu_f(z) : z);
+                }
+            }
+        }
+    }
+}
+
+// dW[co][ci][tap] += sum over a chunk of pixels of dz[p, co] h[p + off(tap), ci]
+// in FP32 (real channels co < cout, ci < cin; arrays strided by the padded
+// counts), and db[co] += sum dz[p, co].  One block per (chunk, tap).
+__global__ void __launch_bounds__(256)
+wgrad_kernel(const __nv_bfloat16 *__restrict__ h, int cin_pad, int cin, const float *__restrict__ dz, int cout_pad,
+             int cout, int npix, int H, int W, int chunk, float *__restrict__ dW, float *__restrict__ db)
+{
+    constexpr int PER = MAXC * MAXC / 256;
+    const int tap = blockIdx.y;
+    const int p0 = blockIdx.x * chunk;
+    const int p1 = min(p0 + chunk, npix);
+    const int dp = tap / 3 - 1, dq = tap % 3 - 1;
+    const int HW = H * W;
+    __shared__ float sz[32][MAXC];
+    __shared__ float sh[32][MAXC + 1];
+    const int npair = cout * cin;
+    float acc[PER];
+#pragma unroll
+    for (int k = 0; k < PER; k++) acc[k] = 0.0f;
+    float bacc = 0.0f;
+    for (int q0 = p0; q0 < p1; q0 += 32) {
+        const int nq = min(32, p1 - q0);
+        for (int e = threadIdx.x; e < 32 * MAXC; e += 256) {
+            const int r = e / MAXC, c = e - r * MAXC;
+            float vz = 0.0f, vh = 0.0f;
+            if (r < nq) {
+                const int p = q0 + r;
+                if (c < cout) vz = dz[(size_t)p * cout_pad + c];
+                if (c < cin) {
+                    const int n = p / HW, rem = p - n * HW, i = rem / W, j = rem - i * W;
+                    const int ii = wrap(i + dp, H), jj = wrap(j + dq, W);
+                    vh = __bfloat162float(h[((size_t)n * HW + (size_t)ii * W + jj) * cin_pad + c]);
+                }
+            }
+            sz[r][c] = vz;
+            sh[r][c] = vh;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int pair = threadIdx.x + k * 256;
+            if (pair < npair) {
+                const int co = pair / cin, ci = pair - co * cin;
+                float sacc = 0.0f;
+                for (int r = 0; r < nq; r++) sacc += sz[r][co] * sh[r][ci];
+                acc[k] += sacc;
+            }
+        }
+        if (tap == 4 && (int)threadIdx.x < cout)
+            for (int r = 0; r < nq; r++) bacc += sz[r][threadIdx.x];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+        const int pair = threadIdx.x + k * 256;
+        if (pair < npair) {
+            const int co = pair / cin, ci = pair - co * cin;
+            atomicAdd(&dW[((size_t)co * cin + ci) * 9 + tap], acc[k]);
+        }
+    }
+    if (tap == 4 && (int)threadIdx.x < cout) atomicAdd(&db[threadIdx.x], bacc);
+}
+
+// y = x + net(x) (residual), loss = mean((y - t)^2), dnet = dy = 2 (y - t) / n
+__global__ void residual_loss_kernel(const __nv_bfloat16 *__restrict__ xin, int cin_pad,
+                                     const float *__restrict__ zlast, int cpad_last, const float *__restrict__ target,
+                                     int c_real, int npix, float *__restrict__ y, float *__restrict__ dz_last,
+                                     double *__restrict__ loss_acc)
+{
+    double local = 0.0;
+    const long long n = (long long)npix * c_real;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(e / c_real), c = (int)(e - (long long)p * c_real);
+        const float yy = __bfloat162float(xin[(size_t)p * cin_pad + c]) + zlast[(size_t)p * cpad_last + c];
+        y[e] = yy;
+        if (target) {
+            const float d = yy - target[e];
+            local += (double)d * d;
+            dz_last[(size_t)p * cpad_last + c] = 2.0f * d / (float)n;
+        }
+    }
+    if (target) {
+        __shared__ double red[256];
+        red[threadIdx.x] = local;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) atomicAdd(loss_acc, red[0]);
+    }
+}
+
+// FP32 NHWC (c_real channels) -> BF16 NHWC padded to cpad channels (zeros)
+__global__ void pack_input_kernel(const float *__restrict__ x, int c_real, int cpad, int npix,
+                                  __nv_bfloat16 *__restrict__ out)
+{
+    const long long n = (long long)npix * cpad;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(e / cpad), c = (int)(e - (long long)p * cpad);
+        out[e] = __float2bfloat16_rn(c < c_real ? x[(size_t)p * c_real + c] : 0.0f);
+    }
+}
+
+// FP32 [n] -> BF16 [n]
+__global__ void to_bf16_kernel(const float *__restrict__ x, long long n, __nv_bfloat16 *__restrict__ out)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        out[e] = __float2bfloat16_rn(x[e]);
+}
+
+// master W[co][ci][tap] (real channels) -> Wb[tap][co_pad][ci_pad] and
+// Wd[tap'][ci_pad][co_pad] with tap' the mirrored tap (8 - tap)
+__global__ void arrange_weights_kernel(const float *__restrict__ Wm, int cout, int cin, int cout_pad, int cin_pad,
+                                       __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Wd)
+{
+    const int n = 9 * cout_pad * cin_pad;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int tap = e / (cout_pad * cin_pad);
+        const int rem = e - tap * cout_pad * cin_pad;
+        const int co = rem / cin_pad, ci = rem - co * cin_pad;
+        const float w = (co < cout && ci < cin) ? Wm[((size_t)co * cin + ci) * 9 + tap] : 0.0f;
+        Wb[e] = __float2bfloat16_rn(w);
+        Wd[((size_t)(8 - tap) * cin_pad + ci) * cout_pad + co] = __float2bfloat16_rn(w);
+    }
+}
+
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                            float c2)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const float gg = g[e];
+        const float mm = b1 * m[e] + (1.0f - b1) * gg;
+        const float vv = b2 * v[e] + (1.0f - b2) * gg * gg;
+        m[e] = mm;
+        v[e] = vv;
+        p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    }
+}
+
+int pad16(int c) { return (c + 15) / 16 * 16; }
+
+struct ConvArgs {
+    const __nv_bfloat16 *in, *B;
+    const float *bias;
+    int nbias;
+    __nv_bfloat16 *out;
+    float *z;
+    const float *zprev;
+    int npix, H, W, mode, flip;
+};
+
+template <int CIN, int NOUT>
+cudaError_t launch_conv_t(const ConvArgs &a, cudaStream_t st)
+{
+    const int blocks = (a.npix + 63) / 64;
+    conv_mma_kernel<CIN, NOUT><<<blocks, 128, 0, st>>>(a.in, a.B, a.bias, a.nbias, a.out, a.z, a.zprev, a.npix, a.H,
+                                                       a.W, a.mode, a.flip);
+    return cudaGetLastError();
+}
+
+template <int CIN>
+cudaError_t launch_conv_cin(int nout, const ConvArgs &a, cudaStream_t st)
+{
+    switch (nout) {
+    case 8: return launch_conv_t<CIN, 8>(a, st);
+    case 16: return launch_conv_t<CIN, 16>(a, st);
+    case 32: return launch_conv_t<CIN, 32>(a, st);
+    case 48: return launch_conv_t<CIN, 48>(a, st);
+    case 64: return launch_conv_t<CIN, 64>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// cin: padded input channels (multiple of 16); nout: padded outputs
+cudaError_t launch_conv(int cin, int nout, const ConvArgs &a, cudaStream_t st)
+{
+    switch (cin) {
+    case 16: return launch_conv_cin<16>(nout, a, st);
+    case 32: return launch_conv_cin<32>(nout, a, st);
+    case 48: return launch_conv_cin<48>(nout, a, st);
+    case 64: return launch_conv_cin<64>(nout, a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+struct hlbm_sur {
+    int L = 0, H = 0, W = 0, bmax = 0;
+    int width[MAX_LAYERS + 1];
+    int cpad_in[MAX_LAYERS], cpad_out[MAX_LAYERS];  // padded channels (in: multiple of 16, out: of 8 / 16)
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t nparam = 0;
+    size_t woff[MAX_LAYERS], boff[MAX_LAYERS];
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 master params / grads / Adam moments
+    __nv_bfloat16 *Wb[MAX_LAYERS] = {nullptr}, *Wd[MAX_LAYERS] = {nullptr};
+    __nv_bfloat16 *act[MAX_LAYERS + 1] = {nullptr};  // layer inputs h_l (BF16, padded)
+    float *z[MAX_LAYERS] = {nullptr};                // pre-activations (FP32, padded out)
+    __nv_bfloat16 *gbuf[2] = {nullptr, nullptr};     // BF16 gradient ping-pong
+    float *dz = nullptr, *dz2 = nullptr;             // FP32 gradient ping-pong (pre-activations)
+    float *y = nullptr;
+    double *loss = nullptr;
+    int last_batch = 0;
+    int64_t adam_t = 0;
+};
+
+extern "C" {
+
+void hlbm_sur_destroy(hlbm_sur *s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    cudaFree(s->p); cudaFree(s->g); cudaFree(s->m); cudaFree(s->v);
+    for (int l = 0; l < MAX_LAYERS; l++) { cudaFree(s->Wb[l]); cudaFree(s->Wd[l]); cudaFree(s->z[l]); }
+    for (int l = 0; l <= MAX_LAYERS; l++) cudaFree(s->act[l]);
+    cudaFree(s->gbuf[0]); cudaFree(s->gbuf[1]); cudaFree(s->dz); cudaFree(s->dz2); cudaFree(s->y); cudaFree(s->loss);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+int hlbm_sur_create(int nlayer, const int *widths, int H, int W, int batch_max, void *stream, hlbm_sur **out)
+{
+    if (!out || !widths || nlayer < 1 || nlayer > MAX_LAYERS || H < 1 || W < 1 || batch_max < 1) return HLBM_ERR_ARG;
+    *out = nullptr;
+    for (int l = 0; l <= nlayer; l++)
+        if (widths[l] < 1 || widths[l] > MAXC) return HLBM_ERR_ARG;
+    if (widths[nlayer] != widths[0]) return HLBM_ERR_ARG;  // residual output
+    hlbm_sur *s = new (std::nothrow) hlbm_sur();
+    if (!s) return HLBM_ERR_NOMEM;
+    s->L = nlayer; s->H = H; s->W = W; s->bmax = batch_max;
+    for (int l = 0; l <= nlayer; l++) s->width[l] = widths[l];
+    if (stream) {
+        s->stream = static_cast<cudaStream_t>(stream);
+    } else if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return HLBM_ERR_CUDA;
+    } else {
+        s->own_stream = true;
+    }
+    size_t off = 0;
+    for (int l = 0; l < nlayer; l++) {
+        // every padded count is a multiple of 16: it is the K dimension of
+        // the next layer (forward) or of the input-gradient pass (backward)
+        s->cpad_in[l] = pad16(widths[l]);
+        s->cpad_out[l] = pad16(widths[l + 1]);
+        s->woff[l] = off; off += (size_t)widths[l + 1] * widths[l] * 9;
+        s->boff[l] = off; off += widths[l + 1];
+    }
+    s->nparam = off;
+    const size_t npix = (size_t)batch_max * H * W;
+    bool ok = cudaMalloc(&s->p, off * 4) == cudaSuccess && cudaMalloc(&s->g, off * 4) == cudaSuccess &&
+              cudaMalloc(&s->m, off * 4) == cudaSuccess && cudaMalloc(&s->v, off * 4) == cudaSuccess &&
+              cudaMalloc(&s->loss, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&s->y, npix * widths[0] * 4) == cudaSuccess &&
+              cudaMalloc(&s->dz, npix * MAXC * 4) == cudaSuccess && cudaMalloc(&s->dz2, npix * MAXC * 4) == cudaSuccess &&
+              cudaMalloc(&s->gbuf[0], npix * MAXC * 2) == cudaSuccess &&
+              cudaMalloc(&s->gbuf[1], npix * MAXC * 2) == cudaSuccess;
+    for (int l = 0; l < nlayer && ok; l++) {
+        ok = cudaMalloc(&s->Wb[l], (size_t)9 * s->cpad_out[l] * s->cpad_in[l] * 2) == cudaSuccess &&
+             cudaMalloc(&s->Wd[l], (size_t)9 * s->cpad_out[l] * s->cpad_in[l] * 2) == cudaSuccess &&
+             cudaMalloc(&s->z[l], npix * s->cpad_out[l] * 4) == cudaSuccess &&
+             cudaMalloc(&s->act[l], npix * s->cpad_in[l] * 2) == cudaSuccess;
+    }
+    if (ok) ok = cudaMalloc(&s->act[nlayer], npix * s->cpad_out[nlayer - 1] * 2) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); hlbm_sur_destroy(s); return HLBM_ERR_NOMEM; }
+    if (cudaMemsetAsync(s->m, 0, off * 4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->v, 0, off * 4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->p, 0, off * 4, s->stream) != cudaSuccess) {
+        hlbm_sur_destroy(s);
+        return HLBM_ERR_CUDA;
+    }
+    *out = s;
+    return HLBM_OK;
+}
+
+int64_t hlbm_sur_param_count(const hlbm_sur *s) { return s ? (int64_t)s->nparam : -1; }
+
+static int sur_arrange(hlbm_sur *s)
+{
+    for (int l = 0; l < s->L; l++) {
+        const int n = 9 * s->cpad_out[l] * s->cpad_in[l];
+        if (cudaMemsetAsync(s->Wd[l], 0, (size_t)n * 2, s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
+        arrange_weights_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(s->p + s->woff[l], s->width[l + 1], s->width[l],
+                                                                       s->cpad_out[l], s->cpad_in[l], s->Wb[l], s->Wd[l]);
+        if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+    }
+    return HLBM_OK;
+}
+
+int hlbm_sur_set_params(hlbm_sur *s, const float *params, int mem_kind)
+{
+    if (!s || !params) return HLBM_ERR_ARG;
+    const cudaMemcpyKind k = mem_kind == HLBM_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(s->p, params, s->nparam * 4, k, s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
+    if (cudaMemsetAsync(s->m, 0, s->nparam * 4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->v, 0, s->nparam * 4, s->stream) != cudaSuccess)
+        return HLBM_ERR_CUDA;
+    s->adam_t = 0;
+    const int r = sur_arrange(s);
+    if (r != HLBM_OK) return r;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? HLBM_OK : HLBM_ERR_CUDA;
+}
+
+int hlbm_sur_get_params(hlbm_sur *s, float *params, float *grads, int mem_kind)
+{
+    if (!s) return HLBM_ERR_ARG;
+    const cudaMemcpyKind k = mem_kind == HLBM_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (params && cudaMemcpyAsync(params, s->p, s->nparam * 4, k, s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
+    if (grads && cudaMemcpyAsync(grads, s->g, s->nparam * 4, k, s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? HLBM_OK : HLBM_ERR_CUDA;
+}
+
+// x: device FP32 [B, H, W, C0] (NHWC); y: device FP32 [B, H, W, C0] or NULL.
+int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B)
+{
+    if (!s || !x || B < 1 || B > s->bmax) return HLBM_ERR_ARG;
+    const int npix = B * s->H * s->W;
+    pack_input_kernel<<<1024, 256, 0, s->stream>>>(x, s->width[0], s->cpad_in[0], npix, s->act[0]);
+    if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+    for (int l = 0; l < s->L; l++) {
+        const bool last = l == s->L - 1;
+        const ConvArgs a{s->act[l], s->Wb[l], s->p + s->boff[l], s->width[l + 1], s->act[l + 1], s->z[l], nullptr,
+                         npix, s->H, s->W, last ? 0 : 1, 0};
+        if (launch_conv(s->cpad_in[l], s->cpad_out[l], a, s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
+    }
+    residual_loss_kernel<<<1024, 256, 0, s->stream>>>(s->act[0], s->cpad_in[0], s->z[s->L - 1], s->cpad_out[s->L - 1],
+                                                      nullptr, s->width[0], npix, s->y, nullptr, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+    if (y && cudaMemcpyAsync(y, s->y, (size_t)npix * s->width[0] * 4, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+        return HLBM_ERR_CUDA;
+    s->last_batch = B;
+    return HLBM_OK;
+}
+
+// After hlbm_sur_forward on the same batch: loss = mean((y - target)^2)
+// (target FP32 NHWC [B, H, W, C0] on the device) and the gradient of every
+// parameter into the gradient buffer.
+int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss_out)
+{
+    if (!s || !target || s->last_batch < 1) return HLBM_ERR_ARG;
+    const int B = s->last_batch, npix = B * s->H * s->W;
+    const int L = s->L;
+    float *dzf[2] = {s->dz, s->dz2};
+    int cur = 0;
+    if (cudaMemsetAsync(s->g, 0, s->nparam * 4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->loss, 0, sizeof(double), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(dzf[cur], 0, (size_t)npix * s->cpad_out[L - 1] * 4, s->stream) != cudaSuccess)
+        return HLBM_ERR_CUDA;
+    residual_loss_kernel<<<1024, 256, 0, s->stream>>>(s->act[0], s->cpad_in[0], s->z[L - 1], s->cpad_out[L - 1], target,
+                                                      s->width[0], npix, s->y, dzf[cur], s->loss);
+    if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+    // BF16 copy of the top gradient for the tensor-core input-gradient pass
+    to_bf16_kernel<<<1024, 256, 0, s->stream>>>(dzf[cur], (long long)npix * s->cpad_out[L - 1], s->gbuf[0]);
+    if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+    int gb = 0;
+    for (int l = L - 1; l >= 0; l--) {
+        const int chunk = 4096;
+        dim3 grid((npix + chunk - 1) / chunk, 9);
+        wgrad_kernel<<<grid, 256, 0, s->stream>>>(s->act[l], s->cpad_in[l], s->width[l], dzf[cur], s->cpad_out[l],
+                                                  s->width[l + 1], npix, s->H, s->W, chunk, s->g + s->woff[l],
+                                                  s->g + s->boff[l]);
+        if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+        if (l == 0) break;
+        // dz_{l-1} = (W_l^T * dz_l) . GELU'(z_{l-1}): the transposed
+        // convolution on the tensor cores (mirrored taps), GELU' in the
+        // epilogue, FP32 and BF16 results
+        const ConvArgs a{s->gbuf[gb], s->Wd[l], nullptr, 0, s->gbuf[gb ^ 1], dzf[cur ^ 1], s->z[l - 1], npix, s->H,
+                         s->W, 2, 1};
+        if (launch_conv(s->cpad_out[l], s->cpad_in[l], a, s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
+        cur ^= 1;
+        gb ^= 1;
+    }
+    if (loss_out) {
+        double l2 = 0.0;
+        if (cudaMemcpyAsync(&l2, s->loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess)
+            return HLBM_ERR_CUDA;
+        *loss_out = l2 / ((double)npix * s->width[0]);
+    }
+    return HLBM_OK;
+}
+
+// One Adam step (Kingma & Ba 2015) on all parameters from the gradient
+// buffer; the BF16 copies are refreshed.
+int hlbm_sur_adam(hlbm_sur *s, float lr, float beta1, float beta2, float eps)
+{
+    if (!s || !(lr > 0.0f)) return HLBM_ERR_ARG;
+    s->adam_t++;
+    const float c1 = 1.0f - powf(beta1, (float)s->adam_t), c2 = 1.0f - powf(beta2, (float)s->adam_t);
+    adam_kernel<<<1024, 256, 0, s->stream>>>(s->p, s->g, s->m, s->v, (long long)s->nparam, lr, beta1, beta2, eps, c1, c2);
+    if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+    return sur_arrange(s);
+}
+
+int hlbm_sur_synchronize(hlbm_sur *s)
+{
+    if (!s) return HLBM_ERR_ARG;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? HLBM_OK : HLBM_ERR_CUDA;
+}
+
+
+}  // extern "C"

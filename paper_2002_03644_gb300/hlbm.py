@@ -17,17 +17,22 @@ import numpy as np
 
 from . import build as _build
 
-HLBM_FP64, HLBM_FP32 = 0, 1
+HLBM_FP64, HLBM_FP32, HLBM_FP32_F16POP, HLBM_FP32_BF16POP = 0, 1, 2, 3
 HLBM_BC_PERIODIC, HLBM_BC_ZEROGRAD, HLBM_BC_DIRICHLET = 0, 1, 2
 HLBM_MEM_HOST, HLBM_MEM_DEVICE = 0, 1
 HLBM_OK, HLBM_ERR_ARG, HLBM_ERR_CFL, HLBM_ERR_NONFINITE = 0, -1, -2, -3
 HLBM_ERR_CUDA, HLBM_ERR_STATE, HLBM_ERR_NOMEM, HLBM_ERR_UNSUPPORTED = -4, -5, -6, -7
+HLBM_ERR_TIMEOUT = -8
 
 ENTRY_POINTS = (
     "hlbm_create", "hlbm_init_fields", "hlbm_step", "hlbm_get_macros", "hlbm_get_populations",
     "hlbm_diagnostics", "hlbm_state_bytes", "hlbm_get_state", "hlbm_set_state", "hlbm_step_count",
     "hlbm_synchronize", "hlbm_destroy", "hlbm_strerror", "hlbm_last_error", "hlbm_abi_version",
     "hlbm_diagnostics_noalloc",
+    "hlbm_batch_create", "hlbm_batch_case", "hlbm_batch_step", "hlbm_batch_autotune", "hlbm_batch_tile",
+    "hlbm_batch_destroy",
+    "hlbm_sur_create", "hlbm_sur_param_count", "hlbm_sur_set_params", "hlbm_sur_get_params", "hlbm_sur_forward",
+    "hlbm_sur_backward", "hlbm_sur_adam", "hlbm_sur_synchronize", "hlbm_sur_destroy",
 )
 HLBM_NOALLOC_MAX_CELLS = 16777216
 
@@ -116,6 +121,37 @@ def _lib():
         lib.hlbm_last_error.argtypes = [_P]
         lib.hlbm_abi_version.restype = ctypes.c_int
         lib.hlbm_abi_version.argtypes = []
+        lib.hlbm_batch_create.restype = ctypes.c_int
+        lib.hlbm_batch_create.argtypes = [ctypes.POINTER(hlbm_params), ctypes.c_int, _P, ctypes.POINTER(_P)]
+        lib.hlbm_batch_case.restype = ctypes.c_int
+        lib.hlbm_batch_case.argtypes = [_P, ctypes.c_int, ctypes.POINTER(_P)]
+        lib.hlbm_batch_step.restype = ctypes.c_int
+        lib.hlbm_batch_step.argtypes = [_P, ctypes.c_int64]
+        lib.hlbm_batch_autotune.restype = ctypes.c_int
+        lib.hlbm_batch_autotune.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
+        lib.hlbm_batch_tile.restype = ctypes.c_int
+        lib.hlbm_batch_tile.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int)] * 4
+        lib.hlbm_batch_destroy.restype = None
+        lib.hlbm_batch_destroy.argtypes = [_P]
+        lib.hlbm_sur_create.restype = ctypes.c_int
+        lib.hlbm_sur_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, _P, ctypes.POINTER(_P)]
+        lib.hlbm_sur_param_count.restype = ctypes.c_int64
+        lib.hlbm_sur_param_count.argtypes = [_P]
+        lib.hlbm_sur_set_params.restype = ctypes.c_int
+        lib.hlbm_sur_set_params.argtypes = [_P, _PD, ctypes.c_int]
+        lib.hlbm_sur_get_params.restype = ctypes.c_int
+        lib.hlbm_sur_get_params.argtypes = [_P, _PD, _PD, ctypes.c_int]
+        lib.hlbm_sur_forward.restype = ctypes.c_int
+        lib.hlbm_sur_forward.argtypes = [_P, _PD, _PD, ctypes.c_int]
+        lib.hlbm_sur_backward.restype = ctypes.c_int
+        lib.hlbm_sur_backward.argtypes = [_P, _PD, ctypes.POINTER(ctypes.c_double)]
+        lib.hlbm_sur_adam.restype = ctypes.c_int
+        lib.hlbm_sur_adam.argtypes = [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+        lib.hlbm_sur_synchronize.restype = ctypes.c_int
+        lib.hlbm_sur_synchronize.argtypes = [_P]
+        lib.hlbm_sur_destroy.restype = None
+        lib.hlbm_sur_destroy.argtypes = [_P]
         lib.hlbm_diagnostics_noalloc.restype = ctypes.c_int
         lib.hlbm_diagnostics_noalloc.argtypes = [_PD, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_double, _PD, _P]
@@ -271,23 +307,121 @@ def hlbm_diagnostics_noalloc(state_ptr, precision, nx, ny, pitch, gamma, stream=
     return out
 
 
+def hlbm_batch_create(params_list, stream=None):
+    """A batch of FP32 cases advanced together (one persistent launch per
+    step, replayed from a CUDA graph).  Returns the opaque batch pointer."""
+    arr = (hlbm_params * len(params_list))(*params_list)
+    b = _P()
+    _check(_lib().hlbm_batch_create(arr, len(params_list), stream or None, ctypes.byref(b)))
+    return b.value
+
+
+def hlbm_batch_case(b, index):
+    h = _P()
+    _check(_lib().hlbm_batch_case(b, int(index), ctypes.byref(h)))
+    return h.value
+
+
+def hlbm_batch_step(b, n):
+    _check(_lib().hlbm_batch_step(b, int(n)))
+
+
+def hlbm_batch_autotune(b):
+    t = ctypes.c_int()
+    _check(_lib().hlbm_batch_autotune(b, ctypes.byref(t)))
+    return t.value
+
+
+def hlbm_batch_tile(b):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(_lib().hlbm_batch_tile(b, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def hlbm_batch_destroy(b):
+    if b:
+        _lib().hlbm_batch_destroy(b)
+
+
+def hlbm_sur_create(widths, H, W, batch_max, stream=None):
+    arr = (ctypes.c_int * len(widths))(*[int(w) for w in widths])
+    s = _P()
+    _check(_lib().hlbm_sur_create(len(widths) - 1, arr, int(H), int(W), int(batch_max), stream or None,
+                                  ctypes.byref(s)))
+    return s.value
+
+
+def hlbm_sur_param_count(s):
+    return _lib().hlbm_sur_param_count(s)
+
+
+def _f32_ptr(a):
+    """(address, mem_kind) of a contiguous float32 torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        assert a.dtype == torch.float32 and a.is_contiguous()
+        return a.data_ptr(), (HLBM_MEM_DEVICE if a.is_cuda else HLBM_MEM_HOST)
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data, HLBM_MEM_HOST
+
+
+def hlbm_sur_set_params(s, params):
+    p, k = _f32_ptr(params)
+    _check(_lib().hlbm_sur_set_params(s, p, k))
+
+
+def hlbm_sur_get_params(s, params=None, grads=None):
+    kinds = set()
+    pp = gg = None
+    if params is not None:
+        pp, k = _f32_ptr(params); kinds.add(k)
+    if grads is not None:
+        gg, k = _f32_ptr(grads); kinds.add(k)
+    _check(_lib().hlbm_sur_get_params(s, pp, gg, kinds.pop() if kinds else HLBM_MEM_HOST))
+
+
+def hlbm_sur_forward(s, x, y, batch):
+    """x, y: CUDA float32 tensors [B, H, W, C] (y may be None)."""
+    _check(_lib().hlbm_sur_forward(s, x.data_ptr(), None if y is None else y.data_ptr(), int(batch)))
+
+
+def hlbm_sur_backward(s, target):
+    loss = ctypes.c_double()
+    _check(_lib().hlbm_sur_backward(s, target.data_ptr(), ctypes.byref(loss)))
+    return loss.value
+
+
+def hlbm_sur_adam(s, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(_lib().hlbm_sur_adam(s, lr, beta1, beta2, eps))
+
+
+def hlbm_sur_synchronize(s):
+    _check(_lib().hlbm_sur_synchronize(s))
+
+
+def hlbm_sur_destroy(s):
+    if s:
+        _lib().hlbm_sur_destroy(s)
+
+
 # ---- convenience wrapper ----------------------------------------------------------
 
 class Solver:
-    """Owns one handle.  Example:
+    """Owns one handle (or borrows one, see Batch).  Example:
         s = Solver(nx, ny, precision=HLBM_FP32, mu=1e-4)
         s.init(rho, ux, uy, theta); s.step(100); m = s.macros()
     """
 
-    def __init__(self, nx, ny, stream=None, **params):
+    def __init__(self, nx, ny, stream=None, _borrowed=None, **params):
         self.nx, self.ny = int(nx), int(ny)
         self.params = make_params(nx, ny, **params)
-        self.h = hlbm_create(self.params, stream)
+        self._owned = _borrowed is None
+        self.h = hlbm_create(self.params, stream) if self._owned else _borrowed
 
     def close(self):
-        if self.h:
+        if self.h and self._owned:
             hlbm_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -330,3 +464,39 @@ class Solver:
 
     def synchronize(self):
         hlbm_synchronize(self.h)
+
+
+class Batch:
+    """Many FP32 cases advanced together.  cases: list of dicts with nx, ny and
+    the keyword parameters of make_params.  batch.cases[i] is a Solver view of
+    case i (init / macros / diagnostics); batch.step(n) advances all."""
+
+    def __init__(self, cases, stream=None):
+        plist = [make_params(c["nx"], c["ny"], **{k: v for k, v in c.items() if k not in ("nx", "ny")})
+                 for c in cases]
+        self.b = hlbm_batch_create(plist, stream)
+        self.cases = [Solver(c["nx"], c["ny"], _borrowed=hlbm_batch_case(self.b, i),
+                             **{k: v for k, v in c.items() if k not in ("nx", "ny")})
+                      for i, c in enumerate(cases)]
+
+    def step(self, n=1):
+        hlbm_batch_step(self.b, n)
+
+    def autotune(self):
+        return hlbm_batch_autotune(self.b)
+
+    def tile(self):
+        return hlbm_batch_tile(self.b)
+
+    def close(self):
+        if self.b:
+            for c in self.cases:
+                c.h = None
+            hlbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

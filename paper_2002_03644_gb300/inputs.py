@@ -242,3 +242,25 @@ def uniform(nx, ny, rho=1.0, ux=0.1, uy=-0.05, theta=0.25, **kw):
     """A uniform state (a fixed point of the scheme on a periodic grid)."""
     f = lambda v: np.full((ny, nx), float(v))
     return Case("uniform", nx, ny, f(rho), f(ux), f(uy), f(theta), **kw)
+
+
+def batch_sweep(ncase=64, seed=2002, steps=2000, mu=1.5e-6, beta=0.2, cfl=0.7):
+    """Vortex-convection cases of uneven size and physics for the batched
+    form: N drawn uniformly from {128, 256, 512, 1024}, Ma uniform in
+    [0.1, 1.5], gamma from {1.4, 1.3, 1.67}, all from counter-based draws of
+    `seed`; theta_inf of each case sets CFL = (Ma + 1) sqrt(gamma theta / 3)
+    to `cfl`; vortex radius N / 32, strength beta."""
+    r = uniform01(seed, 3 * ncase).reshape(ncase, 3)
+    sizes = (128, 256, 512, 1024)
+    gammas = (1.4, 1.3, 1.67)
+    out = []
+    for k in range(ncase):
+        n = sizes[min(3, int(r[k, 0] * 4))]
+        ma = 0.1 + 1.4 * r[k, 1]
+        gamma = gammas[min(2, int(r[k, 2] * 3))]
+        theta_inf = 3.0 * (cfl / (ma + 1.0)) ** 2 / gamma
+        c = vortex(n=n, Ma=ma, beta=beta, R=n / 32.0, gamma=gamma, mu=mu, theta_inf=theta_inf, noise=1e-6,
+                   seed=seed + k + 1, steps=steps)
+        c.name = f"vortex{n}_Ma{ma:.2f}_g{gamma}"
+        out.append(c)
+    return out

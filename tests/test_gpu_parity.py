@@ -260,3 +260,39 @@ def test_error_paths(hl):
     with pytest.raises(hl.HlbmError) as e:
         chk.step(4)
     assert e.value.code == hl.HLBM_ERR_NONFINITE
+
+
+# ---- the plain tiled FP32 kernel (HLBM_FP32_TMA=-1) and the other TMA tiles ---------
+
+class _env:
+    def __init__(self, **kv):
+        self.kv = kv
+
+    def __enter__(self):
+        import os
+        self.old = {k: os.environ.get(k) for k in self.kv}
+        os.environ.update({k: str(v) for k, v in self.kv.items()})
+
+    def __exit__(self, *a):
+        import os
+        for k, v in self.old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+KERNELS = [dict(HLBM_FP32_TMA=-1, HLBM_FP32_TILE=t) for t in range(5)] + \
+          [dict(HLBM_FP32_TMA=k) for k in range(4)]
+
+
+@pytest.mark.parametrize("kern", KERNELS, ids=lambda d: "-".join(f"{k[5:]}{v}" for k, v in d.items()))
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 2, 2, 1)])
+def test_fp32_kernel_variants(hl, kern, bc):
+    bs = np.array([[1.02, 0.08, 0.01, 0.21], [0.98, 0.05, -0.02, 0.19],
+                   [1.01, 0.06, 0.03, 0.2], [0.99, 0.07, 0.0, 0.205]])
+    case = inputs.random_smooth(173, 141, seed=31, amp=0.04, u0=(0.06, 0.01), theta0=0.2, mu=3e-3,
+                                sigma=0.5, bc=bc, bc_state=bs)
+    with _env(**kern):
+        _, _, got, ref = run_pair(hl, case, 1, 9)
+    compare(got, ref, case.gamma, TOL[1])

@@ -71,7 +71,7 @@ int main(void) {
 def test_status_strings_and_version(lib):
     from paper_2002_03644_gb300 import hlbm
     assert hlbm.hlbm_abi_version() == 1
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         assert hlbm.hlbm_strerror(code) not in ("", "unknown status")
 
 
