@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--e2e-inner", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="train the K=16 conv surrogate on HLBM rollouts and compare it with the HLBM step")
+    ap.add_argument("--sur-samples", type=int, default=2000)
+    ap.add_argument("--sur-epochs", type=int, default=20)
     ap.add_argument("--batched", action="store_true",
                     help="the 64-case batched vortex sweep (one persistent launch per step) "
                          "against the same cases run one after another")
@@ -453,10 +457,98 @@ def run_batched(args):
     return 0
 
 
+def run_surrogate(args):
+    """Learned K = 16 surrogate: 6 periodic 3x3 conv layers (4 -> 64 x 5 -> 4,
+    GELU), BF16 operands with FP32 accumulation, trained by the library's own
+    kernels on HLBM snapshot pairs of 256^2 random-Fourier fields (8 lowest
+    modes, amplitude 0.05, Mach 0.3-1.2).  Reports training throughput, the
+    held-out error, and the time of one surrogate call against 16 HLBM
+    steps on the same grid."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2002_03644_gb300 import hlbm, inputs, surrogate
+    n, K, batch = 256, 16, 16
+    # one dedicated stream for the solver, the surrogate and the events
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sh = stream.cuda_stream
+    t0 = time.perf_counter()
+    X, Y = surrogate.make_dataset_device(args.sur_samples, n=n, K=K, pairs_per_run=4, seed=2002, stream=sh)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    ntrain = int(0.9 * X.shape[0]) // batch * batch
+    norm = surrogate.DeviceNormaliser(X[:ntrain])
+    Xn, Yn = norm.fwd(X).contiguous(), norm.fwd(Y).contiguous()
+    del X, Y
+    widths = (4, 64, 64, 64, 64, 64, 4)
+    sur = surrogate.Surrogate(widths, n, n, batch_max=batch, seed=0, stream=sh)
+    # FLOPs per sample of one forward pass (multiply-add = 2)
+    fwd_flops = sum(2 * 9 * a * b * n * n for a, b in zip(widths[:-1], widths[1:]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = sur.fit(Xn[:ntrain], Yn[:ntrain], epochs=args.sur_epochs, batch=batch, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    samples = args.sur_epochs * ntrain
+    # held-out error (normalised fields) of the surrogate and of y = x
+    errs, errs_id, mse, mse_id = [], [], [], []
+    for b0 in range(ntrain, Xn.shape[0] - batch + 1, batch):
+        pred = sur.forward(Xn[b0:b0 + batch].contiguous())
+        d, d0 = pred - Yn[b0:b0 + batch], Xn[b0:b0 + batch] - Yn[b0:b0 + batch]
+        errs.append(float(d.abs().max())); errs_id.append(float(d0.abs().max()))
+        mse.append(float((d * d).mean())); mse_id.append(float((d0 * d0).mean()))
+    # inference time per sample (batch of 16) vs 16 HLBM steps per sample
+    x = Xn[:batch].contiguous()
+    y = torch.empty_like(x)
+    for _ in range(3):
+        sur.forward(x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        sur.forward(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_sur = e0.elapsed_time(e1) / 1e3 / (reps * batch)
+    case = inputs.random_fourier(n=n, seed=1)
+    s = hlbm.Solver(n, n, stream=sh, precision=hlbm.HLBM_FP32, **case.params())
+    s.init(*case.fields())
+    s.step(K)
+    s.synchronize()
+    t0 = time.perf_counter()
+    reps_h = 50
+    s.step(K * reps_h)
+    s.synchronize()
+    t_hlbm = (time.perf_counter() - t0) / reps_h
+    s.close()
+    sur.close()
+    line = {"metric": "surrogate K=16 call vs 16 HLBM steps (256^2)", "value": t_hlbm / t_sur, "unit": "x",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
+            "config": {"workload": "256^2 periodic random-Fourier fields (8 lowest modes, amplitude 0.05, Mach "
+                                   "0.3-1.2), K = 16, net 4-64x5-4 3x3 periodic conv, GELU",
+                       "samples": int(Xn.shape[0]), "train": ntrain, "epochs": args.sur_epochs, "batch": batch},
+            "surrogate_s_per_sample": t_sur, "hlbm_s_per_16_steps": t_hlbm,
+            "train_samples_per_s": samples / t_train,
+            "train_tflops": 3 * fwd_flops * samples / t_train / 1e12,
+            "data_generation_s": t_data, "loss_first_last": [hist[0], hist[-1]],
+            "heldout_mse_normalised": float(np.mean(mse)) if mse else None,
+            "heldout_mse_identity": float(np.mean(mse_id)) if mse_id else None,
+            "heldout_maxabs_err_normalised": max(errs) if errs else None,
+            "heldout_maxabs_err_identity": max(errs_id) if errs_id else None,
+            "field_error_bound_note": "errors in units of the per-channel standard deviation of the inputs"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.surrogate:
+        return run_surrogate(args)
     if args.batched:
         return run_batched(args)
     return run_ours(args)

@@ -94,8 +94,15 @@ typedef struct {
                               value (this synchronises); 0: never */
     int32_t check_cfl;     /* != 0: hlbm_init_fields returns HLBM_ERR_CFL when
                               max(|u| + sqrt(gamma theta / 3)) >= 1 */
-    int32_t reserved[6];   /* must be zero */
+    int32_t ablation;      /* 0 for the method of the paper; bits restore parts
+                              of the original model it improves on (Sec. 3.2):
+                              HLBM_ABL_CENTRED_E1, HLBM_ABL_NO_E2 */
+    int32_t reserved[5];   /* must be zero */
 } hlbm_params;
+
+/* ablation bits: E1 by second-order centred differences instead of the
+ * upwind scheme; no polyatomic correction E2 */
+enum { HLBM_ABL_CENTRED_E1 = 1, HLBM_ABL_NO_E2 = 2 };
 
 typedef struct hlbm_handle hlbm_handle;
 

@@ -261,6 +261,7 @@ typedef struct {
     int bc[4];              /* x-, x+, y-, y+ */
     double bcs[4][4];       /* Dirichlet (rho, ux, uy, theta) per side */
     int phi_mode;           /* 0: Phi from a1 (eq viscous heat discret), 1: finite differences */
+    int ablation;           /* bit 1: centred E1, bit 2: no E2 (parts of the original model) */
     double cv, cp, lambda;
     /* Dirichlet ghost values per side */
     double b_s[4], b_feq[4][Q], b_gx[4], b_gy[4];
@@ -348,7 +349,7 @@ static double theta_of(const hlbmo *o, double rho, double s)
 void hlbmo_destroy(hlbmo *o);
 
 hlbmo *hlbmo_create(int nx, int ny, double gamma, double Pr, double mu, double sigma,
-                    const int bc[4], const double bc_state[16], int phi_mode)
+                    const int bc[4], const double bc_state[16], int phi_mode, int ablation)
 {
     if (nx < 1 || ny < 1) return NULL;
     hlbmo *o = (hlbmo *)calloc(1, sizeof(hlbmo));
@@ -356,6 +357,7 @@ hlbmo *hlbmo_create(int nx, int ny, double gamma, double Pr, double mu, double s
     make_tables();
     o->nx = nx; o->ny = ny; o->px = nx + 2 * G; o->py = ny + 2 * G;
     o->gamma = gamma; o->Pr = Pr; o->mu = mu; o->sigma = sigma; o->phi_mode = phi_mode;
+    o->ablation = ablation;
     for (int k = 0; k < 4; k++) {
         o->bc[k] = bc[k];
         for (int q = 0; q < 4; q++) o->bcs[k][q] = bc_state ? bc_state[4 * k + q] : 0.0;
@@ -424,7 +426,9 @@ static double sgn(double v) { return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0); }
 
 /* Correction force psi of one level (Algorithm 1, steps 4 and 9): Gamma from
  * the ghost-filled macros, E1 by the upwind difference of Sec. 3.2, E2 by
- * centred differences (eq E2 corr term), psi by eq (Psialgo). */
+ * centred differences (eq E2 corr term), psi by eq (Psialgo).  The ablation
+ * bits restore parts of the original model the paper improves on: bit 1
+ * takes E1 by centred differences, bit 2 drops E2. */
 static void compute_psi(hlbmo *o, const double *rho, const double *ux, const double *uy,
                         const double *th, double *psi[Q])
 {
@@ -437,7 +441,8 @@ static void compute_psi(hlbmo *o, const double *rho, const double *ux, const dou
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             const int k = IX(o, x, y);
-            const double sx = sgn(ux[k]), sy = sgn(uy[k]);
+            const double sx = (o->ablation & 1) ? 0.0 : sgn(ux[k]);
+            const double sy = (o->ablation & 1) ? 0.0 : sgn(uy[k]);
             const double e1xx = 0.5 * (1.0 + sx) * (o->gx[k] - o->gx[IX(o, x - 1, y)])
                               + 0.5 * (1.0 - sx) * (o->gx[IX(o, x + 1, y)] - o->gx[k]);
             const double e1yy = 0.5 * (1.0 + sy) * (o->gy[k] - o->gy[IX(o, x, y - 1)])
@@ -446,7 +451,7 @@ static void compute_psi(hlbmo *o, const double *rho, const double *ux, const dou
             velocity_gradient(o, ux, uy, x, y, Gm);
             const double p = rho[k] * CS2 * th[k];                 /* eq (perfect gas) */
             const double divu = Gm[0][0] + Gm[1][1];
-            const double e2 = p * ((DIM + 2.0) / DIM - o->gamma) * divu;
+            const double e2 = (o->ablation & 2) ? 0.0 : p * ((DIM + 2.0) / DIM - o->gamma) * divu;
             double out[Q];
             hlbmo_psi_cell(e1xx + e2, 0.0, e1yy + e2, out);
             for (int i = 0; i < Q; i++) psi[i][k] = out[i];

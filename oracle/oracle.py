@@ -51,7 +51,7 @@ def _load():
         lib = ctypes.CDLL(LIB)
         lib.hlbmo_create.restype = ctypes.c_void_p
         lib.hlbmo_create.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D,
-                                     ctypes.POINTER(ctypes.c_int), _PD, ctypes.c_int]
+                                     ctypes.POINTER(ctypes.c_int), _PD, ctypes.c_int, ctypes.c_int]
         lib.hlbmo_destroy.argtypes = [ctypes.c_void_p]
         lib.hlbmo_init.restype = ctypes.c_int
         lib.hlbmo_init.argtypes = [ctypes.c_void_p, _PD, _PD, _PD, _PD, _PD]
@@ -143,17 +143,17 @@ class Oracle:
     """FP64 CPU solver following Algorithm 1.  Arrays are row-major [ny][nx]."""
 
     def __init__(self, nx, ny, gamma=1.4, Pr=0.71, mu=1e-3, sigma=0.0,
-                 bc=(BC_PERIODIC,) * 4, bc_state=None, phi_mode=0):
+                 bc=(BC_PERIODIC,) * 4, bc_state=None, phi_mode=0, ablation=0):
         self.lib = _load()
         self.nx, self.ny = int(nx), int(ny)
         bcs = np.zeros(16) if bc_state is None else _f64(bc_state, 16)
         bca = (ctypes.c_int * 4)(*[int(b) for b in bc])
         self._h = self.lib.hlbmo_create(self.nx, self.ny, gamma, Pr, mu, sigma, bca,
-                                        _ptr(bcs), int(phi_mode))
+                                        _ptr(bcs), int(phi_mode), int(ablation))
         if not self._h:
             raise ValueError("oracle: invalid arguments or out of memory")
         self.params = dict(gamma=gamma, Pr=Pr, mu=mu, sigma=sigma, bc=tuple(bc),
-                           bc_state=bcs.copy(), phi_mode=phi_mode)
+                           bc_state=bcs.copy(), phi_mode=phi_mode, ablation=ablation)
 
     def __del__(self):
         h = getattr(self, "_h", None)

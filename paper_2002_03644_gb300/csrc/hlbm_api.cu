@@ -299,7 +299,8 @@ static int validate(const hlbm_params *p)
     if ((p->bc[0] == HLBM_BC_PERIODIC) != (p->bc[1] == HLBM_BC_PERIODIC)) return HLBM_ERR_ARG;
     if ((p->bc[2] == HLBM_BC_PERIODIC) != (p->bc[3] == HLBM_BC_PERIODIC)) return HLBM_ERR_ARG;
     if (p->diag_every < 0) return HLBM_ERR_ARG;
-    for (int k = 0; k < 6; k++)
+    if (p->ablation < 0 || p->ablation > (HLBM_ABL_CENTRED_E1 | HLBM_ABL_NO_E2)) return HLBM_ERR_ARG;
+    for (int k = 0; k < 5; k++)
         if (p->reserved[k] != 0) return HLBM_ERR_ARG;
     return HLBM_OK;
 }
@@ -320,7 +321,8 @@ static void fill_kparams(hlbm_handle *h)
     k.lambda = p.mu * cp / p.Pr;  // conductivity from the definition of Pr
     k.gm1 = p.gamma - 1.0;
     k.inv_cv = 1.0 / k.cv;
-    k.two_minus_gamma = 2.0 - p.gamma;  // (D + 2) / D - gamma, D = 2
+    k.two_minus_gamma = (p.ablation & HLBM_ABL_NO_E2) ? 0.0 : 2.0 - p.gamma;  // (D + 2) / D - gamma, D = 2
+    k.e1_centred = (p.ablation & HLBM_ABL_CENTRED_E1) ? 1 : 0;
     k.gamma = p.gamma;
     for (int s = 0; s < 4; s++) {
         if (p.bc[s] != HLBM_BC_DIRICHLET) continue;

@@ -55,6 +55,7 @@ struct KParams {
     int bc[4];                 // x-, x+, y-, y+
     int phi_mode;              // 0 regularised, 1 finite differences
     int sigma_nonzero;
+    int e1_centred;            // 1: E1 by centred differences (ablation)
     double mu, sigma, lambda;  // lambda = mu c_p / Pr
     double gm1, inv_cv, cv, two_minus_gamma, gamma;
     // Dirichlet side constants: macros, entropy, closure defect, populations
@@ -467,8 +468,9 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
         const T gxp = gamma_defect(nRho[k + 1], uxp, nTh[k + 1]);
         const T gym = gamma_defect(nRho[k - R1X], uym, nTh[k - R1X]);
         const T gyp = gamma_defect(nRho[k + R1X], uyp, nTh[k + R1X]);
-        const T e1xx = ux > T(0) ? gxc - gxm : (ux < T(0) ? gxp - gxc : T(0.5) * (gxp - gxm));
-        const T e1yy = uy > T(0) ? gyc - gym : (uy < T(0) ? gyp - gyc : T(0.5) * (gyp - gym));
+        const bool cen = kp.e1_centred != 0;
+        const T e1xx = (ux > T(0) && !cen) ? gxc - gxm : ((ux < T(0) && !cen) ? gxp - gxc : T(0.5) * (gxp - gxm));
+        const T e1yy = (uy > T(0) && !cen) ? gyc - gym : ((uy < T(0) && !cen) ? gyp - gyc : T(0.5) * (gyp - gym));
         const T e2 = p * cs.two_m_gamma * (dxux + dyuy);
         const T ex = e1xx + e2, ey = e1yy + e2;
         // a1^FD = -tau_bar p (grad u + grad u^T - div u I), tau_bar p = mu + p/2
@@ -593,10 +595,11 @@ __global__ void init_kernel(const double *__restrict__ rho, const double *__rest
     }
     auto gam = [](double r, double u, double t) { return r * u * (1.0 - t - u * u); };
     const double gxc = gam(r0, u0, t0), gyc = gam(r0, v0, t0);
-    const double e1xx = u0 > 0.0 ? gxc - gam(rxm, uxm, txm)
-                      : (u0 < 0.0 ? gam(rxp, uxp, txp) - gxc : 0.5 * (gam(rxp, uxp, txp) - gam(rxm, uxm, txm)));
-    const double e1yy = v0 > 0.0 ? gyc - gam(rym, vym, tym)
-                      : (v0 < 0.0 ? gam(ryp, vyp, typ) - gyc : 0.5 * (gam(ryp, vyp, typ) - gam(rym, vym, tym)));
+    const bool cen = kp.e1_centred != 0;
+    const double e1xx = (u0 > 0.0 && !cen) ? gxc - gam(rxm, uxm, txm)
+                      : ((u0 < 0.0 && !cen) ? gam(rxp, uxp, txp) - gxc : 0.5 * (gam(rxp, uxp, txp) - gam(rxm, uxm, txm)));
+    const double e1yy = (v0 > 0.0 && !cen) ? gyc - gam(rym, vym, tym)
+                      : ((v0 < 0.0 && !cen) ? gam(ryp, vyp, typ) - gyc : 0.5 * (gam(ryp, vyp, typ) - gam(rym, vym, tym)));
     const double e2 = p * kp.two_minus_gamma * (dxux + dyuy);
     const double omega = (2.0 * kp.mu - p) / (2.0 * kp.mu + p);
     double f[9];

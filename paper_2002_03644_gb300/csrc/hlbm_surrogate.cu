@@ -6,7 +6,7 @@
 // to a multiple of 16; FP32 master weights W[l][co][ci][tap] (tap = 3 (p+1) +
 // (q+1) for the offset (p, q) in rows and columns) and their BF16 copies
 // arranged for the tensor-core B operand: Wb[tap][co][ci] (forward) and
-// Wd[tap'][ci][co] with the tap mirrored (input gradient).
+// Wd[tap][ci][co] (input gradient, read with the negated offset of the tap).
 //
 // Convolution = implicit GEMM on the BF16 tensor cores (mma.sync m16n8k16,
 // FP32 accumulators): out[pixel, n] = sum_tap sum_k B[tap][n][k] *
@@ -210,17 +210,17 @@ wgrad_kernel(const __nv_bfloat16 *__restrict__ h, int cin_pad, int cin, const fl
     if (tap == 4 && (int)threadIdx.x < cout) atomicAdd(&db[threadIdx.x], bacc);
 }
 
-// y = x + net(x) (residual), loss = mean((y - t)^2), dnet = dy = 2 (y - t) / n
-__global__ void residual_loss_kernel(const __nv_bfloat16 *__restrict__ xin, int cin_pad,
-                                     const float *__restrict__ zlast, int cpad_last, const float *__restrict__ target,
-                                     int c_real, int npix, float *__restrict__ y, float *__restrict__ dz_last,
-                                     double *__restrict__ loss_acc)
+// y = x + net(x) with the FP32 input x, loss = mean((y - t)^2),
+// dnet = dy = 2 (y - t) / n
+__global__ void residual_loss_kernel(const float *__restrict__ xin, const float *__restrict__ zlast, int cpad_last,
+                                     const float *__restrict__ target, int c_real, int npix, float *__restrict__ y,
+                                     float *__restrict__ dz_last, double *__restrict__ loss_acc)
 {
     double local = 0.0;
     const long long n = (long long)npix * c_real;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int p = (int)(e / c_real), c = (int)(e - (long long)p * c_real);
-        const float yy = __bfloat162float(xin[(size_t)p * cin_pad + c]) + zlast[(size_t)p * cpad_last + c];
+        const float yy = xin[e] + zlast[(size_t)p * cpad_last + c];
         y[e] = yy;
         if (target) {
             const float d = yy - target[e];
@@ -259,7 +259,8 @@ __global__ void to_bf16_kernel(const float *__restrict__ x, long long n, __nv_bf
 }
 
 // master W[co][ci][tap] (real channels) -> Wb[tap][co_pad][ci_pad] and
-// Wd[tap'][ci_pad][co_pad] with tap' the mirrored tap (8 - tap)
+// Wd[tap][ci_pad][co_pad] (the input-gradient pass negates the offset of
+// the tap, not the tap index)
 __global__ void arrange_weights_kernel(const float *__restrict__ Wm, int cout, int cin, int cout_pad, int cin_pad,
                                        __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Wd)
 {
@@ -270,7 +271,7 @@ __global__ void arrange_weights_kernel(const float *__restrict__ Wm, int cout, i
         const int co = rem / cin_pad, ci = rem - co * cin_pad;
         const float w = (co < cout && ci < cin) ? Wm[((size_t)co * cin + ci) * 9 + tap] : 0.0f;
         Wb[e] = __float2bfloat16_rn(w);
-        Wd[((size_t)(8 - tap) * cin_pad + ci) * cout_pad + co] = __float2bfloat16_rn(w);
+        Wd[((size_t)tap * cin_pad + ci) * cout_pad + co] = __float2bfloat16_rn(w);
     }
 }
 
@@ -351,6 +352,7 @@ struct hlbm_sur {
     __nv_bfloat16 *gbuf[2] = {nullptr, nullptr};     // BF16 gradient ping-pong
     float *dz = nullptr, *dz2 = nullptr;             // FP32 gradient ping-pong (pre-activations)
     float *y = nullptr;
+    float *xin = nullptr;   // FP32 copy of the last forward input (residual path)
     double *loss = nullptr;
     int last_batch = 0;
     int64_t adam_t = 0;
@@ -365,7 +367,7 @@ void hlbm_sur_destroy(hlbm_sur *s)
     cudaFree(s->p); cudaFree(s->g); cudaFree(s->m); cudaFree(s->v);
     for (int l = 0; l < MAX_LAYERS; l++) { cudaFree(s->Wb[l]); cudaFree(s->Wd[l]); cudaFree(s->z[l]); }
     for (int l = 0; l <= MAX_LAYERS; l++) cudaFree(s->act[l]);
-    cudaFree(s->gbuf[0]); cudaFree(s->gbuf[1]); cudaFree(s->dz); cudaFree(s->dz2); cudaFree(s->y); cudaFree(s->loss);
+    cudaFree(s->gbuf[0]); cudaFree(s->gbuf[1]); cudaFree(s->dz); cudaFree(s->dz2); cudaFree(s->y); cudaFree(s->xin); cudaFree(s->loss);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -404,6 +406,7 @@ int hlbm_sur_create(int nlayer, const int *widths, int H, int W, int batch_max, 
               cudaMalloc(&s->m, off * 4) == cudaSuccess && cudaMalloc(&s->v, off * 4) == cudaSuccess &&
               cudaMalloc(&s->loss, sizeof(double)) == cudaSuccess &&
               cudaMalloc(&s->y, npix * widths[0] * 4) == cudaSuccess &&
+              cudaMalloc(&s->xin, npix * widths[0] * 4) == cudaSuccess &&
               cudaMalloc(&s->dz, npix * MAXC * 4) == cudaSuccess && cudaMalloc(&s->dz2, npix * MAXC * 4) == cudaSuccess &&
               cudaMalloc(&s->gbuf[0], npix * MAXC * 2) == cudaSuccess &&
               cudaMalloc(&s->gbuf[1], npix * MAXC * 2) == cudaSuccess;
@@ -467,6 +470,8 @@ int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B)
 {
     if (!s || !x || B < 1 || B > s->bmax) return HLBM_ERR_ARG;
     const int npix = B * s->H * s->W;
+    if (cudaMemcpyAsync(s->xin, x, (size_t)npix * s->width[0] * 4, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+        return HLBM_ERR_CUDA;
     pack_input_kernel<<<1024, 256, 0, s->stream>>>(x, s->width[0], s->cpad_in[0], npix, s->act[0]);
     if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
     for (int l = 0; l < s->L; l++) {
@@ -475,8 +480,8 @@ int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B)
                          npix, s->H, s->W, last ? 0 : 1, 0};
         if (launch_conv(s->cpad_in[l], s->cpad_out[l], a, s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
     }
-    residual_loss_kernel<<<1024, 256, 0, s->stream>>>(s->act[0], s->cpad_in[0], s->z[s->L - 1], s->cpad_out[s->L - 1],
-                                                      nullptr, s->width[0], npix, s->y, nullptr, nullptr);
+    residual_loss_kernel<<<1024, 256, 0, s->stream>>>(s->xin, s->z[s->L - 1], s->cpad_out[s->L - 1], nullptr,
+                                                      s->width[0], npix, s->y, nullptr, nullptr);
     if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
     if (y && cudaMemcpyAsync(y, s->y, (size_t)npix * s->width[0] * 4, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
         return HLBM_ERR_CUDA;
@@ -498,8 +503,8 @@ int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss_out)
         cudaMemsetAsync(s->loss, 0, sizeof(double), s->stream) != cudaSuccess ||
         cudaMemsetAsync(dzf[cur], 0, (size_t)npix * s->cpad_out[L - 1] * 4, s->stream) != cudaSuccess)
         return HLBM_ERR_CUDA;
-    residual_loss_kernel<<<1024, 256, 0, s->stream>>>(s->act[0], s->cpad_in[0], s->z[L - 1], s->cpad_out[L - 1], target,
-                                                      s->width[0], npix, s->y, dzf[cur], s->loss);
+    residual_loss_kernel<<<1024, 256, 0, s->stream>>>(s->xin, s->z[L - 1], s->cpad_out[L - 1], target, s->width[0],
+                                                      npix, s->y, dzf[cur], s->loss);
     if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
     // BF16 copy of the top gradient for the tensor-core input-gradient pass
     to_bf16_kernel<<<1024, 256, 0, s->stream>>>(dzf[cur], (long long)npix * s->cpad_out[L - 1], s->gbuf[0]);
@@ -514,8 +519,8 @@ int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss_out)
         if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
         if (l == 0) break;
         // dz_{l-1} = (W_l^T * dz_l) . GELU'(z_{l-1}): the transposed
-        // convolution on the tensor cores (mirrored taps), GELU' in the
-        // epilogue, FP32 and BF16 results
+        // convolution on the tensor cores (dz read at p - offset(tap)),
+        // GELU' in the epilogue, FP32 and BF16 results
         const ConvArgs a{s->gbuf[gb], s->Wd[l], nullptr, 0, s->gbuf[gb ^ 1], dzf[cur ^ 1], s->z[l - 1], npix, s->H,
                          s->W, 2, 1};
         if (launch_conv(s->cpad_out[l], s->cpad_in[l], a, s->stream) != cudaSuccess) return HLBM_ERR_CUDA;

@@ -306,8 +306,9 @@ fused_step_tma_kernel(const __grid_constant__ TmaMaps maps, const float *__restr
             const float gxp = gamma_defect(nRho[k + 1], uxp, nTh[k + 1]);
             const float gym = gamma_defect(nRho[k - R1X], uym, nTh[k - R1X]);
             const float gyp = gamma_defect(nRho[k + R1X], uyp, nTh[k + R1X]);
-            const float e1xx = ux > 0.0f ? gxc - gxm : (ux < 0.0f ? gxp - gxc : 0.5f * (gxp - gxm));
-            const float e1yy = uy > 0.0f ? gyc - gym : (uy < 0.0f ? gyp - gyc : 0.5f * (gyp - gym));
+            const bool cen = kp.e1_centred != 0;
+            const float e1xx = (ux > 0.0f && !cen) ? gxc - gxm : ((ux < 0.0f && !cen) ? gxp - gxc : 0.5f * (gxp - gxm));
+            const float e1yy = (uy > 0.0f && !cen) ? gyc - gym : ((uy < 0.0f && !cen) ? gyp - gyc : 0.5f * (gyp - gym));
             const float e2 = p * cs.two_m_gamma * (dxux + dyuy);
             const float ex = e1xx + e2, ey = e1yy + e2;
             const float cfd = -(cs.mu + 0.5f * p);

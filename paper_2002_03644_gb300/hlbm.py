@@ -23,6 +23,7 @@ HLBM_MEM_HOST, HLBM_MEM_DEVICE = 0, 1
 HLBM_OK, HLBM_ERR_ARG, HLBM_ERR_CFL, HLBM_ERR_NONFINITE = 0, -1, -2, -3
 HLBM_ERR_CUDA, HLBM_ERR_STATE, HLBM_ERR_NOMEM, HLBM_ERR_UNSUPPORTED = -4, -5, -6, -7
 HLBM_ERR_TIMEOUT = -8
+HLBM_ABL_CENTRED_E1, HLBM_ABL_NO_E2 = 1, 2
 
 ENTRY_POINTS = (
     "hlbm_create", "hlbm_init_fields", "hlbm_step", "hlbm_get_macros", "hlbm_get_populations",
@@ -45,12 +46,12 @@ class hlbm_params(ctypes.Structure):
         ("sigma", ctypes.c_double),
         ("bc", ctypes.c_int32 * 4), ("bc_state", (ctypes.c_double * 4) * 4),
         ("diag_every", ctypes.c_int32), ("check_cfl", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("ablation", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
     ]
 
 
 def make_params(nx, ny, precision=HLBM_FP64, gamma=1.4, Pr=0.71, mu=1e-4, sigma=0.0,
-                bc=(HLBM_BC_PERIODIC,) * 4, bc_state=None, phi_mode=0, diag_every=0, check_cfl=0):
+                bc=(HLBM_BC_PERIODIC,) * 4, bc_state=None, phi_mode=0, diag_every=0, check_cfl=0, ablation=0):
     p = hlbm_params()
     p.nx, p.ny, p.precision, p.phi_mode = int(nx), int(ny), int(precision), int(phi_mode)
     p.gamma, p.Pr, p.mu, p.sigma = float(gamma), float(Pr), float(mu), float(sigma)
@@ -61,7 +62,7 @@ def make_params(nx, ny, precision=HLBM_FP64, gamma=1.4, Pr=0.71, mu=1e-4, sigma=
         for k in range(4):
             for q in range(4):
                 p.bc_state[k][q] = float(bs[k, q])
-    p.diag_every, p.check_cfl = int(diag_every), int(check_cfl)
+    p.diag_every, p.check_cfl, p.ablation = int(diag_every), int(check_cfl), int(ablation)
     return p
 
 

@@ -62,13 +62,14 @@ class Case:
     bc: tuple = (BC_PERIODIC,) * 4
     bc_state: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((4, 4)))
     phi_mode: int = 0
+    ablation: int = 0  # bit 1: centred E1, bit 2: no E2 (original-model parts)
     steps: int = 100
     meta: dict = dataclasses.field(default_factory=dict)
 
     def params(self) -> dict:
         return dict(gamma=self.gamma, Pr=self.Pr, mu=self.mu, sigma=self.sigma,
                     bc=tuple(self.bc), bc_state=np.asarray(self.bc_state, dtype=np.float64).reshape(16),
-                    phi_mode=self.phi_mode)
+                    phi_mode=self.phi_mode, ablation=self.ablation)
 
     def fields(self):
         return self.rho, self.ux, self.uy, self.theta
@@ -264,3 +265,21 @@ def batch_sweep(ncase=64, seed=2002, steps=2000, mu=1.5e-6, beta=0.2, cfl=0.7):
         c.name = f"vortex{n}_Ma{ma:.2f}_g{gamma}"
         out.append(c)
     return out
+
+
+def random_fourier(n=256, seed=0, modes=8, amp=0.05, ma_range=(0.3, 1.2), theta0=300.0 / 1478.75,
+                   gamma=1.4, Pr=0.71, mu=1e-4, sigma=0.0):
+    """Seeded smooth periodic field for the surrogate's training data: the
+    `modes` lowest Fourier modes per axis with random amplitudes (overall
+    relative amplitude `amp`) on rho, u_x, u_y and theta, around a mean flow
+    of Mach uniform in ma_range in a random direction."""
+    r = uniform01(seed, 2)
+    ma = ma_range[0] + (ma_range[1] - ma_range[0]) * r[0]
+    ang = 2.0 * math.pi * r[1]
+    c0 = math.sqrt(gamma * theta0 * CS2)
+    u0 = (ma * c0 * math.cos(ang), ma * c0 * math.sin(ang))
+    case = random_smooth(n, n, seed=seed + 1, amp=amp, modes=modes, rho0=1.0, theta0=theta0, u0=u0,
+                         gamma=gamma, Pr=Pr, mu=mu, sigma=sigma)
+    case.name = "random_fourier"
+    case.meta.update(Ma=ma, angle=ang)
+    return case

@@ -1,0 +1,225 @@
+"""Learned K-step surrogate of the hybrid LBM step.
+
+A stack of periodic 3x3 convolutions maps the normalised state
+(rho, u_x, u_y, theta) on a periodic grid to the state K time steps later
+(y = x + net(x)).  Forward, backward and Adam run in the library's own CUDA
+kernels (include/hlbm.h, hlbm_sur_*); this module only prepares data and
+drives them.  Training data are rollouts of the HLBM solver itself.
+The HLBM stays the judge and the fallback: `hybrid_rollout` re-runs the
+solver every `judge_every` surrogate calls and continues from the solver's
+state when the surrogate's error exceeds a tolerance.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import hlbm, inputs
+
+FIELDS = ("rho", "ux", "uy", "theta")
+
+
+def init_params(widths, seed=0, last_scale=1e-2):
+    """He-normal weights, zero biases; the last layer starts small so that
+    the untrained network is close to y = x."""
+    rng = np.random.default_rng(seed)
+    out = []
+    L = len(widths) - 1
+    for l in range(L):
+        ci, co = widths[l], widths[l + 1]
+        w = rng.normal(size=(co, ci, 9)) * math.sqrt(2.0 / (9 * ci))
+        if l == L - 1:
+            w *= last_scale
+        out.append(w.ravel())
+        out.append(np.zeros(co))
+    return np.concatenate(out).astype(np.float32)
+
+
+def solver_state(solver):
+    m = solver.macros()
+    return np.stack([m[k] for k in FIELDS], axis=-1)  # [ny, nx, 4]
+
+
+def make_dataset(nsamples, n=256, K=16, pairs_per_run=4, seed=0, mu=1e-4, stream=None):
+    """(x, y) pairs [nsamples, n, n, 4] (float64): the HLBM state and the
+    state K steps later, from seeded random-Fourier initial fields (several
+    consecutive pairs per run)."""
+    xs, ys = [], []
+    run = 0
+    while len(xs) < nsamples:
+        case = inputs.random_fourier(n=n, seed=seed * 100003 + run, mu=mu)
+        s = hlbm.Solver(n, n, stream=stream, precision=hlbm.HLBM_FP32, **case.params())
+        s.init(*case.fields())
+        cur = solver_state(s)
+        for _ in range(pairs_per_run):
+            s.step(K)
+            nxt = solver_state(s)
+            xs.append(cur)
+            ys.append(nxt)
+            cur = nxt
+            if len(xs) >= nsamples:
+                break
+        s.close()
+        run += 1
+    return np.stack(xs), np.stack(ys)
+
+
+def make_dataset_device(nsamples, n=256, K=16, pairs_per_run=4, seed=0, mu=1e-4, stream=None):
+    """Like make_dataset, but the pairs stay on the GPU as float32 tensors
+    [nsamples, n, n, 4] (the solver writes its fields straight into device
+    memory)."""
+    import torch
+    X = torch.empty((nsamples, n, n, 4), dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(X)
+    f64 = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(4)]
+    filled, run = 0, 0
+
+    def grab(s, dst):
+        hlbm.hlbm_get_macros(s.h, rho=f64[0], ux=f64[1], uy=f64[2], theta=f64[3], n=n * n)
+        for q in range(4):
+            dst[..., q] = f64[q]
+
+    while filled < nsamples:
+        case = inputs.random_fourier(n=n, seed=seed * 100003 + run, mu=mu)
+        s = hlbm.Solver(n, n, stream=stream, precision=hlbm.HLBM_FP32, **case.params())
+        s.init(*case.fields())
+        grab(s, X[filled])
+        for k in range(pairs_per_run):
+            s.step(K)
+            grab(s, Y[filled])
+            filled += 1
+            if filled >= nsamples:
+                break
+            if k + 1 < pairs_per_run:
+                X[filled].copy_(Y[filled - 1])
+        s.close()
+        run += 1
+    return X, Y
+
+
+class DeviceNormaliser:
+    """Per-channel affine map fitted on training inputs held on the GPU."""
+
+    def __init__(self, X):
+        flat = X.reshape(-1, X.shape[-1]).double()
+        self.mean = flat.mean(dim=0).float()
+        self.std = (flat.std(dim=0) + 1e-12).float()
+
+    def fwd(self, a):
+        return (a - self.mean) / self.std
+
+    def inv(self, a):
+        return a * self.std + self.mean
+
+
+class Normaliser:
+    """Per-channel affine map fitted on training inputs."""
+
+    def __init__(self, x):
+        self.mean = x.reshape(-1, x.shape[-1]).mean(axis=0)
+        self.std = x.reshape(-1, x.shape[-1]).std(axis=0) + 1e-12
+
+    def fwd(self, a):
+        return (a - self.mean) / self.std
+
+    def inv(self, a):
+        return a * self.std + self.mean
+
+
+class Surrogate:
+    """Owns one hlbm_sur handle.  Tensors are CUDA float32 [B, H, W, C]."""
+
+    def __init__(self, widths=(4, 64, 64, 64, 64, 64, 4), H=256, W=256, batch_max=16, seed=0, stream=None):
+        self.widths = tuple(int(w) for w in widths)
+        self.H, self.W, self.batch_max = int(H), int(W), int(batch_max)
+        self.s = hlbm.hlbm_sur_create(self.widths, H, W, batch_max, stream)
+        self.nparam = hlbm.hlbm_sur_param_count(self.s)
+        self.set_params(init_params(self.widths, seed))
+
+    def close(self):
+        if self.s:
+            hlbm.hlbm_sur_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparam
+        hlbm.hlbm_sur_set_params(self.s, p)
+
+    def params(self):
+        p = np.zeros(self.nparam, dtype=np.float32)
+        hlbm.hlbm_sur_get_params(self.s, params=p)
+        return p
+
+    def grads(self):
+        g = np.zeros(self.nparam, dtype=np.float32)
+        hlbm.hlbm_sur_get_params(self.s, grads=g)
+        return g
+
+    def forward(self, x, y=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        hlbm.hlbm_sur_forward(self.s, x, y, x.shape[0])
+        return y
+
+    def train_step(self, x, target, lr):
+        hlbm.hlbm_sur_forward(self.s, x, None, x.shape[0])
+        loss = hlbm.hlbm_sur_backward(self.s, target)
+        hlbm.hlbm_sur_adam(self.s, lr)
+        return loss
+
+    def fit(self, X, Y, epochs=10, batch=8, lr=1e-3, seed=0, log=None):
+        """X, Y: CUDA float32 [N, H, W, C] (normalised).  Returns the mean
+        loss of every epoch."""
+        import torch
+        rng = np.random.default_rng(seed)
+        hist = []
+        N = X.shape[0]
+        for ep in range(epochs):
+            order = rng.permutation(N)
+            tot, cnt = 0.0, 0
+            for b0 in range(0, N - batch + 1, batch):
+                idx = torch.as_tensor(order[b0:b0 + batch], device=X.device)
+                tot += self.train_step(X[idx].contiguous(), Y[idx].contiguous(), lr)
+                cnt += 1
+            hist.append(tot / max(cnt, 1))
+            if log:
+                log(ep, hist[-1])
+        return hist
+
+
+def hybrid_rollout(sur, norm, case, calls, K=16, judge_every=8, tol=None, stream=None):
+    """Advance `case` by calls * K steps with the surrogate, re-running the
+    HLBM over the same K steps every `judge_every` calls.  The judged error
+    (max-abs over the normalised fields) is recorded; above `tol` the
+    rollout continues from the solver's state (fallback).  Returns the final
+    state [H, W, 4] and a list of (call, error, fell_back)."""
+    import torch
+    n = case.nx
+    state = np.stack(case.fields(), axis=-1)
+    log = []
+    for k in range(calls):
+        x = torch.from_numpy(norm.fwd(state)[None].astype(np.float32)).cuda()
+        y = norm.inv(sur.forward(x)[0].double().cpu().numpy())
+        if (k + 1) % judge_every == 0:
+            s = hlbm.Solver(n, n, stream=stream, precision=hlbm.HLBM_FP32, **case.params())
+            s.init(*[np.ascontiguousarray(state[..., q]) for q in range(4)])
+            s.step(K)
+            ref = solver_state(s)
+            s.close()
+            err = float(np.abs(norm.fwd(y) - norm.fwd(ref)).max())
+            back = tol is not None and err > tol
+            log.append((k, err, back))
+            state = ref if back else y
+        else:
+            state = y
+    return state, log

@@ -88,6 +88,15 @@ def test_phi_mode_fd_and_device_inputs(hl, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("ablation", [1, 2, 3])
+def test_original_model_ablations(hl, precision, ablation):
+    case = inputs.random_smooth(41, 37, seed=13, amp=0.05, mu=2e-3, sigma=0.3, gamma=1.3)
+    case.ablation = ablation
+    _, _, got, ref = run_pair(hl, case, precision, 12)
+    compare(got, ref, case.gamma, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_given_initial_a1(hl, precision):
     case = inputs.random_smooth(30, 26, seed=4, amp=0.04, mu=3e-3, sigma=0.4)
     rng = np.random.default_rng(3)

@@ -1,0 +1,126 @@
+"""The learned surrogate's CUDA kernels against the FP64 reference
+(oracle/surrogate_oracle.py), and what training buys.
+
+Tolerance: the GPU multiplies BF16 operands (8-bit mantissa, relative
+rounding 2^-9) and accumulates in FP32, and it also rounds every layer's
+output to BF16.  For sums of a few hundred products with random signs
+this leaves a relative error of order 1e-3 to 1e-2 in outputs and
+gradients.  So outputs and gradients are compared norm-wise at 3e-2, and
+gradients must also point the same way (cosine > 0.999).  Adam's update is
+plain FP32 and is compared at 1e-5."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import surrogate_oracle as S
+from paper_2002_03644_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2002_03644_gb300 import hlbm, surrogate
+    torch.cuda.set_device(0)
+    return torch, hlbm, surrogate
+
+
+def unpack(widths, flat):
+    out, o = [], 0
+    for ci, co in zip(widths[:-1], widths[1:]):
+        w = flat[o:o + co * ci * 9].reshape(co, ci, 3, 3).astype(np.float64)
+        o += co * ci * 9
+        b = flat[o:o + co].astype(np.float64)
+        o += co
+        out.append((w, b))
+    return out
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("widths", [(4, 16, 16, 4), (4, 32, 64, 32, 4)])
+def test_forward_and_gradients_match_reference(env, widths):
+    torch, hlbm, surrogate = env
+    B, H, W = 2, 12, 20
+    sur = surrogate.Surrogate(widths, H, W, batch_max=B, seed=3)
+    p = sur.params()
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(B, H, W, widths[0])).astype(np.float32)
+    t = (x + 0.1 * rng.normal(size=x.shape)).astype(np.float32)
+    xg, tg = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    y = sur.forward(xg).cpu().numpy()
+    params = unpack(widths, p)
+    xo = x.transpose(0, 3, 1, 2).astype(np.float64)
+    to = t.transpose(0, 3, 1, 2).astype(np.float64)
+    yo, cache = S.forward(params, xo)
+    # compare the network part y - x (the residual adds the input exactly)
+    assert rel(y.transpose(0, 3, 1, 2) - xo, yo - xo) < 3e-2
+    loss = hlbm.hlbm_sur_backward(sur.s, tg)
+    assert abs(loss - S.loss(yo, to)) < 3e-2 * S.loss(yo, to)
+    grads, _ = S.backward(params, cache, yo, to)
+    g = sur.grads()
+    go = np.concatenate([np.concatenate([dw.ravel(), db]) for dw, db in grads])
+    assert rel(g, go) < 3e-2
+    cos = float(g @ go / (np.linalg.norm(g) * np.linalg.norm(go)))
+    assert cos > 0.999, cos
+    # every layer's weight gradient on its own
+    o = 0
+    for (dw, db) in grads:
+        n = dw.size
+        assert rel(g[o:o + n], dw.ravel()) < 1e-1
+        o += n + db.size
+    sur.close()
+
+
+def test_adam_matches_reference(env):
+    torch, hlbm, surrogate = env
+    widths = (4, 16, 4)
+    sur = surrogate.Surrogate(widths, 8, 8, batch_max=1, seed=1)
+    p0 = sur.params().astype(np.float64)
+    rng = np.random.default_rng(2)
+    x = torch.from_numpy(rng.normal(size=(1, 8, 8, 4)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(size=(1, 8, 8, 4)).astype(np.float32)).cuda()
+    m = np.zeros_like(p0)
+    v = np.zeros_like(p0)
+    pref = p0.copy()
+    for step in range(1, 4):
+        hlbm.hlbm_sur_forward(sur.s, x, None, 1)
+        hlbm.hlbm_sur_backward(sur.s, t)
+        g = sur.grads().astype(np.float64)
+        hlbm.hlbm_sur_adam(sur.s, 1e-3)
+        pref, m, v = S.adam_update(pref, g, m, v, step, lr=1e-3)
+        assert np.abs(sur.params() - pref).max() < 1e-5
+    sur.close()
+
+
+def test_training_beats_persistence_and_hybrid_rollout(env):
+    """Trained on HLBM rollouts (32^2 periodic random-Fourier fields, K = 8),
+    the network predicts held-out pairs better than the trivial y = x; in a
+    hybrid rollout the HLBM judge records the surrogate's error every 4
+    calls and takes over when it exceeds the tolerance."""
+    torch, hlbm, surrogate = env
+    n, K = 32, 8
+    X, Y = surrogate.make_dataset(72, n=n, K=K, pairs_per_run=4, seed=7, mu=2e-3)
+    norm = surrogate.Normaliser(X[:60])
+    Xn = torch.from_numpy(norm.fwd(X).astype(np.float32)).cuda()
+    Yn = torch.from_numpy(norm.fwd(Y).astype(np.float32)).cuda()
+    sur = surrogate.Surrogate((4, 32, 32, 4), n, n, batch_max=12, seed=0)
+    hist = sur.fit(Xn[:60], Yn[:60], epochs=80, batch=12, lr=1e-3)
+    assert hist[-1] < 0.4 * hist[0], hist[::10]
+    pred = sur.forward(Xn[60:].contiguous())
+    mse_net = float(((pred - Yn[60:]) ** 2).mean())
+    mse_id = float(((Xn[60:] - Yn[60:]) ** 2).mean())
+    assert mse_net < 0.5 * mse_id, (mse_net, mse_id)
+    case = inputs.random_fourier(n=n, seed=999, mu=2e-3)
+    state, log = surrogate.hybrid_rollout(sur, norm, case, calls=8, K=K, judge_every=4, tol=1e-9)
+    assert len(log) == 2 and all(back for _, _, back in log)  # tol so small that the HLBM always takes over
+    assert np.isfinite(state).all()
+    sur.close()
