@@ -176,7 +176,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("hlbm_device.cuh", "hlbm_api.cu"):
+    for f in ("hlbm_device.cuh", "hlbm_tma.cuh", "hlbm_march.cuh", "hlbm_api.cu"):
         h.update(open(os.path.join(ROOT, "paper_2002_03644_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -184,6 +184,10 @@ def kernel_source_hash():
 def kernel_name(precision, cells):
     """The fused-step kernel the library launches for this precision (the
     FP32 choice follows HLBM_FP32_TMA / HLBM_FP32_TILE like the library)."""
+    march = int(os.environ.get("HLBM_MARCH", "-1"))
+    if 0 <= march < 4:
+        t = {"fp64": "double,FullStore<double>", "fp16pop": "float,HalfStore", "bf16pop": "float,BF16Store"}
+        return "march_step_kernel<%s,%d>" % (t.get(precision, "float,FullStore<float>"), (128, 96, 64, 224)[march])
     if precision == "fp64":
         return "fused_step_kernel<double,FullStore<double>,32,8,256>"
     if precision in ("fp16pop", "bf16pop"):

@@ -17,6 +17,7 @@
 #include "hlbm.h"
 #include "hlbm_device.cuh"
 #include "hlbm_tma.cuh"
+#include "hlbm_march.cuh"
 
 using namespace hlbm;
 
@@ -63,6 +64,8 @@ struct hlbm_handle {
     int tma_grid = 0;
     int tma_variant = 0;        // FP32 kernel choice, fixed at create
     int tile_variant = 0;
+    int march_variant = -1;     // row-marching kernel (strip width by index), -1 off
+    int march_nseg = 1;         // row segments per strip
     int *d_err = nullptr;       // device-side timeout flag of the TMA kernel
     int64_t step = 0;
     bool initialized = false;
@@ -232,9 +235,88 @@ static cudaError_t launch_tma(hlbm_handle *h)
     return cudaGetLastError();
 }
 
+// Row-marching kernel: strips of W columns (index k of kMarchW), each cut
+// into row segments so that the grid fills the GPU once (resident CTAs per
+// SM x SMs, from the occupancy calculator), with segments of at least
+// kMarchMinRows rows.  HLBM_MARCH_ROWS=<n> fixes the segment height instead.
+constexpr int kNumMarch = 4;
+constexpr int kMarchMinRows = 8;
+
+template <typename T, typename S, int W>
+static cudaError_t march_setup(hlbm_handle *h)
+{
+    using G = MarchGeom<T, W>;
+    cudaError_t e = cudaFuncSetAttribute(march_step_kernel<T, S, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::smem_bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_step_kernel<T, S, W>, G::NT, G::smem_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return e;
+    const long long strips = (h->p.nx + W - 1) / W;
+    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+    long long nseg = (cap + strips - 1) / strips;
+    const long long most = h->p.ny / kMarchMinRows > 0 ? h->p.ny / kMarchMinRows : 1;
+    if (nseg > most) nseg = most;
+    const int rows = env_choice("HLBM_MARCH_ROWS", 0, 1, 1 << 20);
+    if (rows > 0) nseg = (h->p.ny + rows - 1) / rows;
+    if (nseg > 65535) nseg = 65535;
+    h->march_nseg = (int)(nseg > 0 ? nseg : 1);
+    return cudaSuccess;
+}
+
+template <typename T, typename S, int W>
+static cudaError_t launch_march(hlbm_handle *h)
+{
+    using G = MarchGeom<T, W>;
+    dim3 grid((h->p.nx + W - 1) / W, h->march_nseg);
+    const int a = h->cur, b = h->cur ^ 1;
+    march_step_kernel<T, S, W><<<grid, G::NT, G::smem_bytes, h->stream>>>(
+        pop_planes<T, S>(h, a), aux_planes<T, S>(h, a), pop_planes<T, S>(h, b), aux_planes<T, S>(h, b), h->kp,
+        h->march_nseg);
+    return cudaGetLastError();
+}
+
+// Strip widths of the marching kernel: 128, 96, 64, 224 columns.
+template <typename T, typename S, template <typename, typename, int> class Op>
+static cudaError_t march_dispatch(hlbm_handle *h)
+{
+    switch (h->march_variant) {
+    case 1: return Op<T, S, 96>::run(h);
+    case 2: return Op<T, S, 64>::run(h);
+    case 3: return Op<T, S, 224>::run(h);
+    default: return Op<T, S, 128>::run(h);
+    }
+}
+template <typename T, typename S, int W> struct MarchSetupOp {
+    static cudaError_t run(hlbm_handle *h) { return march_setup<T, S, W>(h); }
+};
+template <typename T, typename S, int W> struct MarchLaunchOp {
+    static cudaError_t run(hlbm_handle *h) { return launch_march<T, S, W>(h); }
+};
+
+static cudaError_t setup_march(hlbm_handle *h)
+{
+    h->march_variant = env_choice("HLBM_MARCH", -1, -1, kNumMarch);
+    if (h->march_variant < 0) return cudaSuccess;
+    return with_types(h, [&](auto ty) {
+        using T = typename decltype(ty)::t;
+        using S = typename decltype(ty)::s;
+        return march_dispatch<T, S, MarchSetupOp>(h);
+    });
+}
+
 static cudaError_t launch_one_step(hlbm_handle *h)
 {
     using F32 = FullStore<float>;
+    if (h->march_variant >= 0) {
+        return with_types(h, [&](auto ty) {
+            using T = typename decltype(ty)::t;
+            using S = typename decltype(ty)::s;
+            return march_dispatch<T, S, MarchLaunchOp>(h);
+        });
+    }
     if (h->p.precision == HLBM_FP64) return launch_step<double, FullStore<double>, TX64, TY64, NT64>(h);
     if (h->p.precision == HLBM_FP32_F16POP) return launch_step<float, HalfStore, 32, 32, 512>(h);
     if (h->p.precision == HLBM_FP32_BF16POP) return launch_step<float, BF16Store, 32, 32, 512>(h);
@@ -428,7 +510,7 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         return HLBM_ERR_CUDA;
     }
     fill_kparams(h);
-    if (params->precision == HLBM_FP32 && setup_fp32_kernel(h) != cudaSuccess) {
+    if ((params->precision == HLBM_FP32 && setup_fp32_kernel(h) != cudaSuccess) || setup_march(h) != cudaSuccess) {
         cudaGetLastError();
         hlbm_destroy(h);
         return HLBM_ERR_CUDA;

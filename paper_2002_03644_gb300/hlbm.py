@@ -344,6 +344,19 @@ def hlbm_batch_destroy(b):
         _lib().hlbm_batch_destroy(b)
 
 
+def torch_stream_handle(stream=None):
+    """Stream handle for the C ABI: `stream` itself (an int handle or a
+    torch.cuda.Stream), else torch's current stream.  torch's legacy default
+    stream (handle 0) is passed as cudaStreamLegacy (1): a NULL stream asks
+    the library for a stream of its own, which is not ordered with torch's
+    work."""
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    import torch
+    h = int(torch.cuda.current_stream().cuda_stream)
+    return h if h != 0 else 1
+
+
 def hlbm_sur_create(widths, H, W, batch_max, stream=None):
     arr = (ctypes.c_int * len(widths))(*[int(w) for w in widths])
     s = _P()

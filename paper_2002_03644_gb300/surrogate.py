@@ -129,12 +129,15 @@ class Normaliser:
 
 
 class Surrogate:
-    """Owns one hlbm_sur handle.  Tensors are CUDA float32 [B, H, W, C]."""
+    """Owns one hlbm_sur handle.  Tensors are CUDA float32 [B, H, W, C].
+    Its work runs on `stream` (default: torch's current stream at creation),
+    so that tensors passed in and out are ordered with torch's own work on
+    that stream."""
 
     def __init__(self, widths=(4, 64, 64, 64, 64, 64, 4), H=256, W=256, batch_max=16, seed=0, stream=None):
         self.widths = tuple(int(w) for w in widths)
         self.H, self.W, self.batch_max = int(H), int(W), int(batch_max)
-        self.s = hlbm.hlbm_sur_create(self.widths, H, W, batch_max, stream)
+        self.s = hlbm.hlbm_sur_create(self.widths, H, W, batch_max, hlbm.torch_stream_handle(stream))
         self.nparam = hlbm.hlbm_sur_param_count(self.s)
         self.set_params(init_params(self.widths, seed))
 

@@ -98,3 +98,16 @@ def test_product_path_has_no_oracle_dependency():
                 txt = open(os.path.join(dirpath, f)).read()
                 for pat in (r"^\s*(from|import)\s+oracle", r"hlbm_oracle", r"libhlbm_oracle", r"hlbmo_"):
                     assert not re.search(pat, txt, flags=re.M), (os.path.join(dirpath, f), pat)
+
+
+def test_stream_handles_passed_through():
+    """An explicit stream (int handle or an object with .cuda_stream) reaches
+    the C ABI unchanged; torch's legacy default stream is never passed as
+    NULL, which would ask the library for an unordered stream of its own."""
+    from paper_2002_03644_gb300 import hlbm
+
+    class FakeStream:
+        cuda_stream = 0x5eed
+
+    assert hlbm.torch_stream_handle(7) == 7
+    assert hlbm.torch_stream_handle(FakeStream()) == 0x5eed
