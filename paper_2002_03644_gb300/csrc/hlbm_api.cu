@@ -239,7 +239,7 @@ static cudaError_t launch_tma(hlbm_handle *h)
 // into row segments so that the grid fills the GPU once (resident CTAs per
 // SM x SMs, from the occupancy calculator), with segments of at least
 // kMarchMinRows rows.  HLBM_MARCH_ROWS=<n> fixes the segment height instead.
-constexpr int kNumMarch = 4;
+constexpr int kNumMarch = 8;
 constexpr int kMarchMinRows = 8;
 
 template <typename T, typename S, int W>
@@ -278,23 +278,60 @@ static cudaError_t launch_march(hlbm_handle *h)
     return cudaGetLastError();
 }
 
-// Strip widths of the marching kernel: 128, 96, 64, 224 columns.
-template <typename T, typename S, template <typename, typename, int> class Op>
+// Paired-column marching kernel with NT threads (strips of 2 (NT - 4) columns).
+template <typename T, typename S, int NT>
+static cudaError_t pair_setup(hlbm_handle *h)
+{
+    using G = PairGeom<T, NT>;
+    cudaError_t e = cudaFuncSetAttribute(march_pair_kernel<T, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::smem_bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_pair_kernel<T, S, NT>, NT, G::smem_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return e;
+    const long long strips = (h->p.nx + G::W - 1) / G::W;
+    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+    long long nseg = (cap + strips - 1) / strips;
+    const long long most = h->p.ny / kMarchMinRows > 0 ? h->p.ny / kMarchMinRows : 1;
+    if (nseg > most) nseg = most;
+    const int rows = env_choice("HLBM_MARCH_ROWS", 0, 1, 1 << 20);
+    if (rows > 0) nseg = (h->p.ny + rows - 1) / rows;
+    if (nseg > 65535) nseg = 65535;
+    h->march_nseg = (int)(nseg > 0 ? nseg : 1);
+    return cudaSuccess;
+}
+
+template <typename T, typename S, int NT>
+static cudaError_t launch_pair(hlbm_handle *h)
+{
+    using G = PairGeom<T, NT>;
+    dim3 grid((h->p.nx + G::W - 1) / G::W, h->march_nseg);
+    const int a = h->cur, b = h->cur ^ 1;
+    march_pair_kernel<T, S, NT><<<grid, NT, G::smem_bytes, h->stream>>>(
+        pop_planes<T, S>(h, a), aux_planes<T, S>(h, a), pop_planes<T, S>(h, b), aux_planes<T, S>(h, b), h->kp,
+        h->march_nseg);
+    return cudaGetLastError();
+}
+
+// Marching kernels: 0-3 one column per thread, strips of 128, 96, 64, 224
+// columns; 4-7 two columns per thread, 64, 96, 128, 160 threads (strips
+// of 120, 184, 248, 312 columns).
+template <typename T, typename S, bool Launch>
 static cudaError_t march_dispatch(hlbm_handle *h)
 {
     switch (h->march_variant) {
-    case 1: return Op<T, S, 96>::run(h);
-    case 2: return Op<T, S, 64>::run(h);
-    case 3: return Op<T, S, 224>::run(h);
-    default: return Op<T, S, 128>::run(h);
+    case 1: return Launch ? launch_march<T, S, 96>(h) : march_setup<T, S, 96>(h);
+    case 2: return Launch ? launch_march<T, S, 64>(h) : march_setup<T, S, 64>(h);
+    case 3: return Launch ? launch_march<T, S, 224>(h) : march_setup<T, S, 224>(h);
+    case 4: return Launch ? launch_pair<T, S, 64>(h) : pair_setup<T, S, 64>(h);
+    case 5: return Launch ? launch_pair<T, S, 96>(h) : pair_setup<T, S, 96>(h);
+    case 6: return Launch ? launch_pair<T, S, 128>(h) : pair_setup<T, S, 128>(h);
+    case 7: return Launch ? launch_pair<T, S, 160>(h) : pair_setup<T, S, 160>(h);
+    default: return Launch ? launch_march<T, S, 128>(h) : march_setup<T, S, 128>(h);
     }
 }
-template <typename T, typename S, int W> struct MarchSetupOp {
-    static cudaError_t run(hlbm_handle *h) { return march_setup<T, S, W>(h); }
-};
-template <typename T, typename S, int W> struct MarchLaunchOp {
-    static cudaError_t run(hlbm_handle *h) { return launch_march<T, S, W>(h); }
-};
 
 static cudaError_t setup_march(hlbm_handle *h)
 {
@@ -303,7 +340,7 @@ static cudaError_t setup_march(hlbm_handle *h)
     return with_types(h, [&](auto ty) {
         using T = typename decltype(ty)::t;
         using S = typename decltype(ty)::s;
-        return march_dispatch<T, S, MarchSetupOp>(h);
+        return march_dispatch<T, S, false>(h);
     });
 }
 
@@ -314,7 +351,7 @@ static cudaError_t launch_one_step(hlbm_handle *h)
         return with_types(h, [&](auto ty) {
             using T = typename decltype(ty)::t;
             using S = typename decltype(ty)::s;
-            return march_dispatch<T, S, MarchLaunchOp>(h);
+            return march_dispatch<T, S, true>(h);
         });
     }
     if (h->p.precision == HLBM_FP64) return launch_step<double, FullStore<double>, TX64, TY64, NT64>(h);

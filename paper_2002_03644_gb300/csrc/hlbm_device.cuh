@@ -76,20 +76,36 @@ struct KParams {
 // (s, a1_xx, a1_xy, a1_yy) always in the arithmetic type T.  Full storage
 // keeps F_i itself; the 16-bit forms keep F_i - f_ref_i, the difference from
 // one reference equilibrium per case, rounded to FP16 or BF16.
+// raw2 holds two horizontally adjacent stored values (one aligned access).
+template <typename T> struct Vec2;
+template <> struct Vec2<float> {
+    using type = float2;
+    static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Vec2<double> {
+    using type = double2;
+    static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
 template <typename T> struct FullStore {
     using raw = T;
+    using raw2 = typename Vec2<T>::type;
     static __device__ __forceinline__ T get(raw r, int, const KParams &) { return r; }
     static __device__ __forceinline__ raw put(T v, int, const KParams &) { return v; }
+    static __device__ __forceinline__ raw2 pack(raw a, raw b) { return Vec2<T>::make(a, b); }
 };
 struct HalfStore {
     using raw = __half;
+    using raw2 = __half2;
     static __device__ __forceinline__ float get(raw r, int i, const KParams &kp) { return __half2float(r) + kp.f_ref[i]; }
     static __device__ __forceinline__ raw put(float v, int i, const KParams &kp) { return __float2half_rn(v - kp.f_ref[i]); }
+    static __device__ __forceinline__ raw2 pack(raw a, raw b) { return __halves2half2(a, b); }
 };
 struct BF16Store {
     using raw = __nv_bfloat16;
+    using raw2 = __nv_bfloat162;
     static __device__ __forceinline__ float get(raw r, int i, const KParams &kp) { return __bfloat162float(r) + kp.f_ref[i]; }
     static __device__ __forceinline__ raw put(float v, int i, const KParams &kp) { return __float2bfloat16_rn(v - kp.f_ref[i]); }
+    static __device__ __forceinline__ raw2 pack(raw a, raw b) { return __halves2bfloat162(a, b); }
 };
 // auxiliary plane indices
 constexpr int A_S = 0, A_XX = 1, A_XY = 2, A_YY = 3;

@@ -312,4 +312,420 @@ march_step_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
     }
 }
 
+// ---- paired-column form -----------------------------------------------------------
+// The same pipeline with each thread owning two horizontally adjacent
+// columns: global and shared-memory traffic moves in 2-element accesses, a
+// cell's x neighbours come from its partner or one neighbouring pair, and a
+// cell's own level-(n+1) values stay in the registers of the thread that
+// computed them until its collision one iteration later.
+//   NT threads; ring columns x0-4 .. x0+2NT-5 (pair t = columns 2t, 2t+1);
+//   load phase on every pair, phase 2 on pairs 1 .. NT-2 (x0-2 .. x0+W+1),
+//   phase 3 on pairs 2 .. NT-3 (the W = 2 (NT - 4) output columns).
+
+// Level-n+1 values of one cell and the second moments of its pulled
+// populations (used by a1^PR when sigma > 0).
+template <typename T>
+struct CellN1 {
+    T rho, ux, uy, th, s, mxx, myy, mxy;
+};
+
+// Steps 5-8 for one cell (the arithmetic of phase 2 of the tiled kernel).
+// W/E/S/N = x-1, x+1, y-1, y+1; g[] the pulled populations.
+template <typename T>
+__device__ __forceinline__ CellN1<T> level_np1(const Consts<T> &cs, const KParams &kp, T rho0, T ux0, T uy0, T th0,
+                                              T uxW, T uxE, T uxS, T uxN, T uyW, T uyE, T uyS, T uyN, T thW, T thE,
+                                              T thS, T thN, T sWW, T sW, T s0, T sE, T sEE, T sSS, T sS, T sN, T sNN,
+                                              T a_xx, T a_xy, T a_yy, const T g[9])
+{
+    const T third = T(1) / T(3);
+    const T dxux = T(0.5) * (uxE - uxW);
+    const T dyux = T(0.5) * (uxN - uxS);
+    const T dxuy = T(0.5) * (uyE - uyW);
+    const T dyuy = T(0.5) * (uyN - uyS);
+    const T lap = (thE + thW) + (thN + thS) - T(4) * th0;
+    const T adv = muscl_adv(ux0, sWW, sW, s0, sE, sEE) + muscl_adv(uy0, sSS, sS, s0, sN, sNN);
+    const T rt = rho0 * th0;
+    const T p0 = rt * third;
+    T phi;
+    if (kp.phi_mode == 0) {
+        phi = -fdiv(cs.two_mu, cs.two_mu + p0) * (a_xx * dxux + a_xy * (dyux + dxuy) + a_yy * dyuy);
+    } else {
+        const T d1 = dxux - dyuy, d2 = dyux + dxuy;
+        phi = cs.mu * (d1 * d1 + d2 * d2);
+    }
+    CellN1<T> o;
+    o.s = s0 - adv + fdiv(cs.lam * lap + phi, rt);
+    T jx, jy;
+    moments(g, o.rho, jx, jy);
+    const T ir = fdiv(T(1), o.rho);
+    o.ux = jx * ir;
+    o.uy = jy * ir;
+    o.th = cs.theta(o.rho, o.s);
+    const T diag = (g[5] + g[6]) + (g[7] + g[8]);
+    o.mxx = (g[1] + g[3]) + diag;
+    o.myy = (g[2] + g[4]) + diag;
+    o.mxy = (g[5] - g[6]) + (g[7] - g[8]);
+    return o;
+}
+
+// Steps 9-11 and the next collision for one cell (phase 3 of the tiled
+// kernel) from its level-(n+1) values and those of its four neighbours.
+template <typename T>
+__device__ __forceinline__ void collide_cell(const Consts<T> &cs, const KParams &kp, const CellN1<T> &c, T rW,
+                                             T uxW, T uyW, T thW, T rE, T uxE, T uyE, T thE, T rS, T uxS, T uyS,
+                                             T thS, T rN, T uxN, T uyN, T thN, T f[9], T &axx, T &axy, T &ayy)
+{
+    const T third = T(1) / T(3);
+    const T rho = c.rho, ux = c.ux, uy = c.uy, th = c.th;
+    const T dxux = T(0.5) * (uxE - uxW);
+    const T dyux = T(0.5) * (uxN - uxS);
+    const T dxuy = T(0.5) * (uyE - uyW);
+    const T dyuy = T(0.5) * (uyN - uyS);
+    const T p = rho * th * third;
+    const T gxc = gamma_defect(rho, ux, th), gyc = gamma_defect(rho, uy, th);
+    const T gxm = gamma_defect(rW, uxW, thW), gxp = gamma_defect(rE, uxE, thE);
+    const T gym = gamma_defect(rS, uyS, thS), gyp = gamma_defect(rN, uyN, thN);
+    const bool cen = kp.e1_centred != 0;
+    const T e1xx = (ux > T(0) && !cen) ? gxc - gxm : ((ux < T(0) && !cen) ? gxp - gxc : T(0.5) * (gxp - gxm));
+    const T e1yy = (uy > T(0) && !cen) ? gyc - gym : ((uy < T(0) && !cen) ? gyp - gyc : T(0.5) * (gyp - gym));
+    const T e2 = p * cs.two_m_gamma * (dxux + dyuy);
+    const T ex = e1xx + e2, ey = e1yy + e2;
+    const T cfd = -(cs.mu + T(0.5) * p);
+    const T fdxx = cfd * (dxux - dyuy), fdxy = cfd * (dyux + dxuy);
+    if (kp.sigma_nonzero) {
+        const T prxx = c.mxx - rho * ux * ux - p + T(0.5) * ex;
+        const T pryy = c.myy - rho * uy * uy - p + T(0.5) * ey;
+        const T prxy = c.mxy - rho * ux * uy;
+        axx = cs.sigma * prxx + cs.one_m_sigma * fdxx;
+        ayy = cs.sigma * pryy - cs.one_m_sigma * fdxx;
+        axy = cs.sigma * prxy + cs.one_m_sigma * fdxy;
+    } else {
+        axx = fdxx; ayy = -fdxx; axy = fdxy;
+    }
+    const T omega = fdiv(cs.two_mu - p, cs.two_mu + p);
+    build_populations(rho, ux, uy, th, axx, axy, ayy, ex, ey, omega, f);
+}
+
+template <typename T, int NT>
+struct PairGeom {
+    static constexpr int NP = NT - 4;   // output pairs
+    static constexpr int W = 2 * NP;    // output columns
+    static constexpr int CW = 2 * NT;   // ring columns
+    static constexpr int OFF_F = 0;                      // [3][9][CW]
+    static constexpr int OFF_M = OFF_F + 3 * 9 * CW;     // [3][4][CW]  rho, u_x, u_y, theta (level n)
+    static constexpr int OFF_S = OFF_M + 3 * 4 * CW;     // [5][CW]
+    static constexpr int OFF_N = OFF_S + 5 * CW;         // [3][4][CW]  rho, u_x, u_y, theta (level n+1)
+    static constexpr int N = OFF_N + 3 * 4 * CW;
+    static constexpr size_t smem_bytes = sizeof(T) * (size_t)N;
+};
+
+// Mapped offset of a column (or -(side+1)) in a row already mapped to mr.
+__device__ __forceinline__ int cell_at(int mr, int mc, int pitch) { return join_map(mr, mc, pitch); }
+
+template <typename T, typename S, int NT>
+__global__ void __launch_bounds__(NT)
+march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
+                  typename S::raw *__restrict__ outF, T *__restrict__ outA, const KParams kp, const int nseg)
+{
+    using G = PairGeom<T, NT>;
+    using V = typename Vec2<T>::type;
+    using raw = typename S::raw;
+    using raw2 = typename S::raw2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *const rF = reinterpret_cast<V *>(reinterpret_cast<T *>(smem_raw) + G::OFF_F);  // [3][9][NT]
+    V *const rM = reinterpret_cast<V *>(reinterpret_cast<T *>(smem_raw) + G::OFF_M);  // [3][4][NT]
+    V *const rS = reinterpret_cast<V *>(reinterpret_cast<T *>(smem_raw) + G::OFF_S);  // [5][NT]
+    V *const rN = reinterpret_cast<V *>(reinterpret_cast<T *>(smem_raw) + G::OFF_N);  // [3][4][NT]
+
+    Consts<T> cs;
+    cs.load(kp);
+    const Side<T> side{kp};
+    const long long P = kp.plane;
+    const int pitch = kp.pitch;
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * G::W;
+    const int ys = seg_start(blockIdx.y, nseg, kp.ny), ye = seg_start(blockIdx.y + 1, nseg, kp.ny);
+    const int base = ys - 4;
+
+    // load-phase pair t: columns gxL, gxL + 1
+    const int gxL = x0 - 4 + 2 * t;
+    const int mcLa = map_col(gxL, kp), mcLb = map_col(gxL + 1, kp);
+    const bool vecL = gxL >= 0 && gxL + 1 < kp.nx;
+    // phase-2 / phase-3 pair q = t + 1: columns gx2, gx2 + 1
+    const int gx2 = gxL + 2;
+    const bool do2 = t < NT - 2;
+    const int mc2a = map_col(gx2, kp), mc2b = map_col(gx2 + 1, kp);
+    const bool vec2 = gx2 >= 0 && gx2 + 1 < kp.nx;
+    // Dirichlet x sides: level n+1 beyond them is the side's state
+    bool dir2[2];
+    int side2[2];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const int gx = gx2 + c;
+        side2[c] = gx < 0 ? 0 : 1;
+        dir2[c] = (gx < 0 || gx >= kp.nx) && kp.bc[side2[c]] == BC_DIRICHLET;
+    }
+    const bool do3 = t >= 1 && t <= G::NP;
+    const bool v3a = do3 && gx2 < kp.nx, v3b = do3 && gx2 + 1 < kp.nx;
+    // zero-gradient x sides: the neighbour beyond the edge is the edge cell itself
+    const bool zgW = gx2 == 0 && kp.bc[0] == BC_ZEROGRAD;             // west of cell a
+    const bool zgEa = gx2 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD;    // east of cell a
+    const bool zgEb = gx2 + 1 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD; // east of cell b
+
+    // prefetch registers: F(n) of row r+2, s(n) of row r+3 (load pair),
+    // a1(n) of row r+1 (phase-2 pair)
+    T pFa[9], pFb[9], pSa = T(0), pSb = T(0), pA[2][3];
+#pragma unroll
+    for (int i = 0; i < 9; i++) { pFa[i] = T(0); pFb[i] = T(0); }
+#pragma unroll
+    for (int c = 0; c < 2; c++) { pA[c][0] = T(0); pA[c][1] = T(0); pA[c][2] = T(0); }
+
+    auto load_F = [&](int mr, T *fa, T *fb) {
+        if (mr >= 0 && vecL) {
+            const raw *src = inF + ((long long)mr * pitch + gxL);
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                const raw2 v = *reinterpret_cast<const raw2 *>(src + i * P);
+                fa[i] = S::get(v.x, i, kp);
+                fb[i] = S::get(v.y, i, kp);
+            }
+        } else {
+            const int oa = cell_at(mr, mcLa, pitch), ob = cell_at(mr, mcLb, pitch);
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                fa[i] = oa >= 0 ? S::get(inF[oa + i * P], i, kp) : side.F(-oa - 1, i);
+                fb[i] = ob >= 0 ? S::get(inF[ob + i * P], i, kp) : side.F(-ob - 1, i);
+            }
+        }
+    };
+    auto load_s = [&](int mr, T &sa, T &sb) {
+        if (mr >= 0 && vecL) {
+            const V v = *reinterpret_cast<const V *>(inA + A_S * P + ((long long)mr * pitch + gxL));
+            sa = v.x;
+            sb = v.y;
+        } else {
+            const int oa = cell_at(mr, mcLa, pitch), ob = cell_at(mr, mcLb, pitch);
+            sa = oa >= 0 ? inA[A_S * P + oa] : side.s_(-oa - 1);
+            sb = ob >= 0 ? inA[A_S * P + ob] : side.s_(-ob - 1);
+        }
+    };
+    auto fetch = [&](int r) {
+        load_F(map_row(r + 2, kp), pFa, pFb);
+        load_s(map_row(r + 3, kp), pSa, pSb);
+        if (kp.phi_mode == 0 && do2) {
+            const int mr = map_row(r + 1, kp);
+            if (mr >= 0 && vec2) {
+                const T *src = inA + ((long long)mr * pitch + gx2);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const V v = *reinterpret_cast<const V *>(src + (A_XX + k) * P);
+                    pA[0][k] = v.x;
+                    pA[1][k] = v.y;
+                }
+            } else {
+                const int oa = cell_at(mr, mc2a, pitch), ob = cell_at(mr, mc2b, pitch);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    pA[0][k] = oa >= 0 ? inA[(A_XX + k) * P + oa] : T(0);
+                    pA[1][k] = ob >= 0 ? inA[(A_XX + k) * P + ob] : T(0);
+                }
+            }
+        }
+    };
+
+    // s(n) of rows ys-3 and ys-2 (the latter kept for the level-n theta of row ys-2)
+    T sPa = T(0), sPb = T(0);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int gy = ys - 3 + k;
+        load_s(map_row(gy, kp), sPa, sPb);
+        rS[((gy - base) % 5) * NT + t] = Vec2<T>::make(sPa, sPb);
+    }
+    fetch(base);
+
+    // ring slots of rows r .. r+2 (F, M), r-1 .. r+3 (s), r-1 .. r+1 (level n+1)
+    int fs0 = (ys - 4 - base) % 3, fs1 = (ys - 3 - base) % 3, fs2 = (ys - 2 - base) % 3;
+    int ss0 = (ys - 5 - base + 5) % 5, ss1 = (ys - 4 - base) % 5, ss2 = (ys - 3 - base) % 5,
+        ss3 = (ys - 2 - base) % 5, ss4 = (ys - 1 - base) % 5;
+    int ns0 = (ys - 5 - base + 3) % 3, ns1 = (ys - 4 - base) % 3, ns2 = (ys - 3 - base) % 3;
+    CellN1<T> cur[2], nxt[2];
+#pragma unroll
+    for (int c = 0; c < 2; c++) cur[c] = nxt[c] = CellN1<T>{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+
+    for (int r = base; r < ye; r++) {
+        // ---- load phase: row r+2 of F(n) and the level-n macros, row r+3 of s(n)
+        {
+            T fa[9], fb[9];
+#pragma unroll
+            for (int i = 0; i < 9; i++) { fa[i] = pFa[i]; fb[i] = pFb[i]; }
+            const T sna = pSa, snb = pSb;
+            T a2[2][3];
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) a2[c][k] = pA[c][k];
+            if (r + 1 < ye) fetch(r + 1);
+#pragma unroll
+            for (int i = 0; i < 9; i++) rF[(fs2 * 9 + i) * NT + t] = Vec2<T>::make(fa[i], fb[i]);
+            const int mr = map_row(r + 2, kp);
+            T m[2][4];
+            auto macros = [&](const T *f, T sv, int o, T *mm) {
+                if (o >= 0) {
+                    T jx, jy;
+                    moments(f, mm[0], jx, jy);
+                    const T ir = fdiv(T(1), mm[0]);
+                    mm[1] = jx * ir;
+                    mm[2] = jy * ir;
+                    mm[3] = cs.theta(mm[0], sv);
+                } else {
+                    const int sd = -o - 1;
+                    mm[0] = side.rho(sd); mm[1] = side.ux(sd); mm[2] = side.uy(sd); mm[3] = side.th(sd);
+                }
+            };
+            macros(fa, sPa, cell_at(mr, mcLa, pitch), m[0]);
+            macros(fb, sPb, cell_at(mr, mcLb, pitch), m[1]);
+#pragma unroll
+            for (int k = 0; k < 4; k++) rM[(fs2 * 4 + k) * NT + t] = Vec2<T>::make(m[0][k], m[1][k]);
+            rS[ss4 * NT + t] = Vec2<T>::make(sna, snb);
+            sPa = sna;
+            sPb = snb;
+            __syncthreads();
+
+            // ---- phase 2: level n+1 of row r+1 on pair q = t + 1
+            const int y2 = r + 1;
+            if (y2 >= ys - 1 && do2) {
+                const int q = t + 1;
+                // level-n macros: rho at the pair, u and theta at pairs q-1, q, q+1 and rows y2 +- 1
+                const V rho0 = rM[(fs1 * 4 + 0) * NT + q];
+                V mc[3][3], ms[3], mn[3];  // [field ux, uy, th][pair q-1, q, q+1]
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    mc[k][0] = rM[(fs1 * 4 + 1 + k) * NT + q - 1];
+                    mc[k][1] = rM[(fs1 * 4 + 1 + k) * NT + q];
+                    mc[k][2] = rM[(fs1 * 4 + 1 + k) * NT + q + 1];
+                    ms[k] = rM[(fs0 * 4 + 1 + k) * NT + q];
+                    mn[k] = rM[(fs2 * 4 + 1 + k) * NT + q];
+                }
+                // s: pairs q-1 .. q+1 of row y2, pair q of rows y2-2 .. y2+2
+                const V sc0 = rS[ss2 * NT + q - 1], sc1 = rS[ss2 * NT + q], sc2 = rS[ss2 * NT + q + 1];
+                const V sS2 = rS[ss0 * NT + q], sS1 = rS[ss1 * NT + q], sN1 = rS[ss3 * NT + q], sN2 = rS[ss4 * NT + q];
+                // pull: F_i from (x - c_ix, y - c_iy); rows y2 (fs1), y2-1 (fs0), y2+1 (fs2)
+                T ga[9], gb[9];
+                {
+                    const V f0 = rF[(fs1 * 9 + 0) * NT + q], f2 = rF[(fs0 * 9 + 2) * NT + q], f4 = rF[(fs2 * 9 + 4) * NT + q];
+                    ga[0] = f0.x; gb[0] = f0.y;
+                    ga[2] = f2.x; gb[2] = f2.y;
+                    ga[4] = f4.x; gb[4] = f4.y;
+                    // c_x = +1 (1, 5, 8): from x-1
+                    const V f1l = rF[(fs1 * 9 + 1) * NT + q - 1], f1c = rF[(fs1 * 9 + 1) * NT + q];
+                    const V f5l = rF[(fs0 * 9 + 5) * NT + q - 1], f5c = rF[(fs0 * 9 + 5) * NT + q];
+                    const V f8l = rF[(fs2 * 9 + 8) * NT + q - 1], f8c = rF[(fs2 * 9 + 8) * NT + q];
+                    ga[1] = f1l.y; gb[1] = f1c.x;
+                    ga[5] = f5l.y; gb[5] = f5c.x;
+                    ga[8] = f8l.y; gb[8] = f8c.x;
+                    // c_x = -1 (3, 6, 7): from x+1
+                    const V f3c = rF[(fs1 * 9 + 3) * NT + q], f3r = rF[(fs1 * 9 + 3) * NT + q + 1];
+                    const V f6c = rF[(fs0 * 9 + 6) * NT + q], f6r = rF[(fs0 * 9 + 6) * NT + q + 1];
+                    const V f7c = rF[(fs2 * 9 + 7) * NT + q], f7r = rF[(fs2 * 9 + 7) * NT + q + 1];
+                    ga[3] = f3c.y; gb[3] = f3r.x;
+                    ga[6] = f6c.y; gb[6] = f6r.x;
+                    ga[7] = f7c.y; gb[7] = f7r.x;
+                }
+                nxt[0] = level_np1<T>(cs, kp, rho0.x, mc[0][1].x, mc[1][1].x, mc[2][1].x,
+                                      mc[0][0].y, mc[0][1].y, ms[0].x, mn[0].x,
+                                      mc[1][0].y, mc[1][1].y, ms[1].x, mn[1].x,
+                                      mc[2][0].y, mc[2][1].y, ms[2].x, mn[2].x,
+                                      sc0.x, sc0.y, sc1.x, sc1.y, sc2.x, sS2.x, sS1.x, sN1.x, sN2.x,
+                                      a2[0][0], a2[0][1], a2[0][2], ga);
+                nxt[1] = level_np1<T>(cs, kp, rho0.y, mc[0][1].y, mc[1][1].y, mc[2][1].y,
+                                      mc[0][1].x, mc[0][2].x, ms[0].y, mn[0].y,
+                                      mc[1][1].x, mc[1][2].x, ms[1].y, mn[1].y,
+                                      mc[2][1].x, mc[2][2].x, ms[2].y, mn[2].y,
+                                      sc0.y, sc1.x, sc1.y, sc2.x, sc2.y, sS2.y, sS1.y, sN1.y, sN2.y,
+                                      a2[1][0], a2[1][1], a2[1][2], gb);
+                // Dirichlet cells hold the side's constants
+                const bool out2y = y2 < 0 || y2 >= kp.ny;
+                const int side2y = y2 < 0 ? 2 : 3;
+                const bool dir2y = out2y && kp.bc[side2y] == BC_DIRICHLET;
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    if (dir2y || dir2[c]) {
+                        const int sd = dir2y ? side2y : side2[c];
+                        nxt[c].rho = side.rho(sd); nxt[c].ux = side.ux(sd); nxt[c].uy = side.uy(sd);
+                        nxt[c].th = side.th(sd); nxt[c].s = side.s_(sd);
+                    }
+                }
+                rN[(ns2 * 4 + 0) * NT + q] = Vec2<T>::make(nxt[0].rho, nxt[1].rho);
+                rN[(ns2 * 4 + 1) * NT + q] = Vec2<T>::make(nxt[0].ux, nxt[1].ux);
+                rN[(ns2 * 4 + 2) * NT + q] = Vec2<T>::make(nxt[0].uy, nxt[1].uy);
+                rN[(ns2 * 4 + 3) * NT + q] = Vec2<T>::make(nxt[0].th, nxt[1].th);
+            }
+        }
+        __syncthreads();
+
+        // ---- phase 3: row r on pair q = t + 1 (own values from the previous iteration)
+        if (r >= ys && do3) {
+            const int q = t + 1;
+            const bool zS = r == 0 && kp.bc[2] == BC_ZEROGRAD;
+            const bool zN = r == kp.ny - 1 && kp.bc[3] == BC_ZEROGRAD;
+            V nW[4], nE[4], nS[4], nN[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                nW[k] = rN[(ns1 * 4 + k) * NT + q - 1];
+                nE[k] = rN[(ns1 * 4 + k) * NT + q + 1];
+                nS[k] = rN[(ns0 * 4 + k) * NT + q];
+                nN[k] = rN[(ns2 * 4 + k) * NT + q];
+            }
+            const CellN1<T> &A = cur[0], &B = cur[1];
+            // cell a: west = pair q-1 (.y), east = cell b; cell b: west = cell a, east = pair q+1 (.x)
+            const T aWr = zgW ? A.rho : nW[0].y, aWux = zgW ? A.ux : nW[1].y, aWuy = zgW ? A.uy : nW[2].y,
+                    aWth = zgW ? A.th : nW[3].y;
+            const T aEr = zgEa ? A.rho : B.rho, aEux = zgEa ? A.ux : B.ux, aEuy = zgEa ? A.uy : B.uy,
+                    aEth = zgEa ? A.th : B.th;
+            const T bEr = zgEb ? B.rho : nE[0].x, bEux = zgEb ? B.ux : nE[1].x, bEuy = zgEb ? B.uy : nE[2].x,
+                    bEth = zgEb ? B.th : nE[3].x;
+            T fa[9], fb[9], aa[3], ab[3];
+            if (v3a) {
+                collide_cell<T>(cs, kp, A, aWr, aWux, aWuy, aWth, aEr, aEux, aEuy, aEth,
+                                zS ? A.rho : nS[0].x, zS ? A.ux : nS[1].x, zS ? A.uy : nS[2].x, zS ? A.th : nS[3].x,
+                                zN ? A.rho : nN[0].x, zN ? A.ux : nN[1].x, zN ? A.uy : nN[2].x, zN ? A.th : nN[3].x,
+                                fa, aa[0], aa[1], aa[2]);
+            }
+            if (v3b) {
+                collide_cell<T>(cs, kp, B, A.rho, A.ux, A.uy, A.th, bEr, bEux, bEuy, bEth,
+                                zS ? B.rho : nS[0].y, zS ? B.ux : nS[1].y, zS ? B.uy : nS[2].y, zS ? B.th : nS[3].y,
+                                zN ? B.rho : nN[0].y, zN ? B.ux : nN[1].y, zN ? B.uy : nN[2].y, zN ? B.th : nN[3].y,
+                                fb, ab[0], ab[1], ab[2]);
+            }
+            const long long o = (long long)r * pitch + gx2;
+            if (v3a && v3b) {
+                raw *dF = outF + o;
+#pragma unroll
+                for (int i = 0; i < 9; i++)
+                    *reinterpret_cast<raw2 *>(dF + i * P) = S::pack(S::put(fa[i], i, kp), S::put(fb[i], i, kp));
+                T *dA = outA + o;
+                *reinterpret_cast<V *>(dA + A_S * P) = Vec2<T>::make(A.s, B.s);
+#pragma unroll
+                for (int k = 0; k < 3; k++) *reinterpret_cast<V *>(dA + (A_XX + k) * P) = Vec2<T>::make(aa[k], ab[k]);
+            } else if (v3a) {
+                raw *dF = outF + o;
+#pragma unroll
+                for (int i = 0; i < 9; i++) dF[i * P] = S::put(fa[i], i, kp);
+                T *dA = outA + o;
+                dA[A_S * P] = A.s;
+#pragma unroll
+                for (int k = 0; k < 3; k++) dA[(A_XX + k) * P] = aa[k];
+            }
+        }
+        // next row: the values computed in phase 2 become the cells' own
+#pragma unroll
+        for (int c = 0; c < 2; c++) cur[c] = nxt[c];
+        {
+            const int f = fs0; fs0 = fs1; fs1 = fs2; fs2 = f;
+            const int sx = ss0; ss0 = ss1; ss1 = ss2; ss2 = ss3; ss3 = ss4; ss4 = sx;
+            const int n = ns0; ns0 = ns1; ns1 = ns2; ns2 = n;
+        }
+    }
+}
+
 }  // namespace hlbm

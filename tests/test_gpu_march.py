@@ -1,7 +1,9 @@
-"""The row-marching fused kernel (HLBM_MARCH=<k>, strip widths 128, 96, 64
-and 224 columns) against the FP64 oracle: the same tolerances as the tiled
-kernel (1e-10 FP64, 1e-4 FP32), every boundary set, grids that leave a
-ragged last strip, and row segments of 1, 3 and all rows (each segment
+"""The row-marching fused kernels against the FP64 oracle: HLBM_MARCH=0-3
+(one column per thread, strips of 128, 96, 64, 224 columns) and 4-7 (two
+columns per thread, strips of 120, 184, 248, 312 columns).  The same
+tolerances as the tiled kernel (1e-10 FP64, 1e-4 FP32), every boundary set,
+grids that leave a ragged last strip (odd widths included, so that a pair
+straddles the edge), and row segments of 1, 3 and all rows (each segment
 refills its row rings from four rows above its first row)."""
 import numpy as np
 import pytest
@@ -30,7 +32,7 @@ def hl():
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("variant", range(4))
+@pytest.mark.parametrize("variant", range(8))
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 2, 2, 1)])
 def test_march_variants(hl, precision, variant, bc):
     case = inputs.random_smooth(173, 141, seed=31, amp=0.04, u0=(0.06, 0.01), theta0=0.2, mu=3e-3,
@@ -41,22 +43,24 @@ def test_march_variants(hl, precision, variant, bc):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("variant", [2, 4])
 @pytest.mark.parametrize("bc", BCS)
-def test_march_boundaries(hl, precision, bc):
+def test_march_boundaries(hl, precision, variant, bc):
     case = inputs.random_smooth(53, 41, seed=21, amp=0.04, u0=(0.06, 0.01), theta0=0.2, mu=3e-3,
                                 sigma=0.5, bc=bc, bc_state=BS)
-    with _env(HLBM_MARCH=2, HLBM_MARCH_ROWS=5):
+    with _env(HLBM_MARCH=variant, HLBM_MARCH_ROWS=5):
         _, _, got, ref = run_pair(hl, case, precision, 20)
     compare(got, ref, case.gamma, TOL[precision])
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("variant", [0, 5])
 @pytest.mark.parametrize("rows", [1, 3, 100000])
-@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 5), (37, 23), (130, 67)])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 5), (37, 23), (130, 67), (185, 9)])
 @pytest.mark.parametrize("sigma", [0.0, 0.7])
-def test_march_segments(hl, precision, rows, nx, ny, sigma):
+def test_march_segments(hl, precision, variant, rows, nx, ny, sigma):
     case = inputs.random_smooth(nx, ny, seed=100 + nx, amp=0.05, mu=2e-3, sigma=sigma)
-    with _env(HLBM_MARCH=0, HLBM_MARCH_ROWS=rows):
+    with _env(HLBM_MARCH=variant, HLBM_MARCH_ROWS=rows):
         _, _, got, ref = run_pair(hl, case, precision, 12)
     compare(got, ref, case.gamma, TOL[precision])
 
@@ -67,9 +71,10 @@ def test_march_phi_fd_and_ablations(hl, precision):
         case = inputs.random_smooth(70, 44, seed=8, amp=0.05, mu=2e-3, sigma=0.3)
         case.phi_mode = phi_mode
         case.ablation = ablation
-        with _env(HLBM_MARCH=1):
-            _, _, got, ref = run_pair(hl, case, precision, 10)
-        compare(got, ref, case.gamma, TOL[precision])
+        for variant in (1, 6):
+            with _env(HLBM_MARCH=variant):
+                _, _, got, ref = run_pair(hl, case, precision, 10)
+            compare(got, ref, case.gamma, TOL[precision])
 
 
 def test_march_16bit_forms_within_their_bounds(hl):
@@ -78,8 +83,8 @@ def test_march_16bit_forms_within_their_bounds(hl):
     ora.init(*case.fields())
     ora.step(200)
     ref = ora.macros()
-    for prec in (2, 3):
-        with _env(HLBM_MARCH=0):
+    for prec, variant in ((2, 0), (3, 0), (2, 5), (3, 5)):
+        with _env(HLBM_MARCH=variant):
             s = hl.Solver(case.nx, case.ny, precision=prec, **case.params())
         s.init(*case.fields())
         s.step(200)
