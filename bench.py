@@ -181,13 +181,18 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_name(precision, cells):
-    """The fused-step kernel the library launches for this precision (the
-    FP32 choice follows HLBM_FP32_TMA / HLBM_FP32_TILE like the library)."""
-    march = int(os.environ.get("HLBM_MARCH", "-1"))
+def kernel_name(precision, cells, sigma=0.0, phi_mode=0):
+    """The fused-step kernel the library launches for this precision: the
+    row-marching kernel for FP32 and the 16-bit forms unless HLBM_MARCH=-1
+    (then the tiled kernels, chosen by HLBM_FP32_TMA / HLBM_FP32_TILE), the
+    tiled kernel for FP64 unless HLBM_MARCH selects a marching variant."""
+    march = int(os.environ.get("HLBM_MARCH", "-1" if precision == "fp64" else "0"))
     if 0 <= march < 4:
         t = {"fp64": "double,FullStore<double>", "fp16pop": "float,HalfStore", "bf16pop": "float,BF16Store"}
-        return "march_step_kernel<%s,%d>" % (t.get(precision, "float,FullStore<float>"), (128, 96, 64, 224)[march])
+        f64 = precision == "fp64"
+        nt, minb = [(64, 8), (96, 5), (128, 4), (64, 1)][march]
+        return "march_pair_kernel<%s,%d,%d,%s,%s>" % (t.get(precision, "float,FullStore<float>"), nt, 1 if f64 else minb,
+                                                      str(sigma > 0).lower(), str(phi_mode == 0).lower())
     if precision == "fp64":
         return "fused_step_kernel<double,FullStore<double>,32,8,256>"
     if precision in ("fp16pop", "bf16pop"):
@@ -373,7 +378,7 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(args.precision, args.n),
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
-                "kernel": kernel_name(args.precision, cells),
+                "kernel": kernel_name(args.precision, cells, case.sigma, case.phi_mode),
                 "algorithmic_bytes_per_launch": bpc * cells}
     else:
         roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "GB/s", "frac": None,

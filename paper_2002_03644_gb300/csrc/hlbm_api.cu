@@ -64,7 +64,7 @@ struct hlbm_handle {
     int tma_grid = 0;
     int tma_variant = 0;        // FP32 kernel choice, fixed at create
     int tile_variant = 0;
-    int march_variant = -1;     // row-marching kernel (strip width by index), -1 off
+    int march_variant = -1;     // row-marching kernel variant, -1: tiled / TMA kernels
     int march_nseg = 1;         // row segments per strip
     int *d_err = nullptr;       // device-side timeout flag of the TMA kernel
     int64_t step = 0;
@@ -134,11 +134,10 @@ static cudaError_t launch_step(hlbm_handle *h)
     return cudaGetLastError();
 }
 
-// FP32 kernels.  By default grids of up to 2048^2 cells use the plain tiled
-// kernel with 32x32 tiles and larger grids the persistent TMA kernel with
-// 32x16 tiles (the faster of the two at each size in GB300 sweeps of the
-// vortex).  HLBM_FP32_TMA=<k> forces TMA tile k, HLBM_FP32_TMA=-1 the plain
-// kernel with HLBM_FP32_TILE=<k> (tuning sweeps).
+// Tiled FP32 kernels (HLBM_MARCH=-1).  Grids of up to 2048^2 cells use the
+// plain tiled kernel with 32x32 tiles and larger grids the persistent TMA
+// kernel with 32x16 tiles.  HLBM_FP32_TMA=<k> forces TMA tile k,
+// HLBM_FP32_TMA=-1 the plain kernel with HLBM_FP32_TILE=<k> (tuning sweeps).
 constexpr int kNumFp32Tiles = 5;  // plain: 32x16x256, 64x16x256, 32x8x128, 64x32x512, 32x32x512
 constexpr int kNumTma = 4;        // TMA: 32x16x512, 32x16x256, 64x16x512, 32x32x512
 
@@ -235,65 +234,44 @@ static cudaError_t launch_tma(hlbm_handle *h)
     return cudaGetLastError();
 }
 
-// Row-marching kernel: strips of W columns (index k of kMarchW), each cut
-// into row segments so that the grid fills the GPU once (resident CTAs per
-// SM x SMs, from the occupancy calculator), with segments of at least
-// kMarchMinRows rows.  HLBM_MARCH_ROWS=<n> fixes the segment height instead.
-constexpr int kNumMarch = 8;
+// Row-marching kernel (paired columns, see hlbm_march.cuh).  Its row
+// segments are cut so that the grid fills the GPU once (resident CTAs per
+// SM x SMs, from the occupancy calculator), at most kMarchMaxRows and at
+// least kMarchMinRows rows high.  HLBM_MARCH_ROWS=<n> fixes the height.
+constexpr int kNumMarch = 4;
 constexpr int kMarchMinRows = 8;
+constexpr int kMarchMaxRows = 32;
 
-template <typename T, typename S, int W>
-static cudaError_t march_setup(hlbm_handle *h)
+// Paired-column marching kernel with NT threads (strips of 2 (NT - 4)
+// columns), register budget set by MINB resident CTAs per SM; the
+// instantiation matches the handle's sigma > 0 and Phi choice.
+template <typename T, typename S, int NT, int MINB>
+static void *pair_kernel_ptr(const hlbm_handle *h)
 {
-    using G = MarchGeom<T, W>;
-    cudaError_t e = cudaFuncSetAttribute(march_step_kernel<T, S, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::smem_bytes);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_step_kernel<T, S, W>, G::NT, G::smem_bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    if (e != cudaSuccess) return e;
-    const long long strips = (h->p.nx + W - 1) / W;
-    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * sms;
-    long long nseg = (cap + strips - 1) / strips;
-    const long long most = h->p.ny / kMarchMinRows > 0 ? h->p.ny / kMarchMinRows : 1;
-    if (nseg > most) nseg = most;
-    const int rows = env_choice("HLBM_MARCH_ROWS", 0, 1, 1 << 20);
-    if (rows > 0) nseg = (h->p.ny + rows - 1) / rows;
-    if (nseg > 65535) nseg = 65535;
-    h->march_nseg = (int)(nseg > 0 ? nseg : 1);
-    return cudaSuccess;
+    const bool sig = h->kp.sigma_nonzero != 0, phi0 = h->kp.phi_mode == 0;
+    if (sig) return phi0 ? (void *)march_pair_kernel<T, S, NT, MINB, true, true>
+                         : (void *)march_pair_kernel<T, S, NT, MINB, true, false>;
+    return phi0 ? (void *)march_pair_kernel<T, S, NT, MINB, false, true>
+                : (void *)march_pair_kernel<T, S, NT, MINB, false, false>;
 }
 
-template <typename T, typename S, int W>
-static cudaError_t launch_march(hlbm_handle *h)
-{
-    using G = MarchGeom<T, W>;
-    dim3 grid((h->p.nx + W - 1) / W, h->march_nseg);
-    const int a = h->cur, b = h->cur ^ 1;
-    march_step_kernel<T, S, W><<<grid, G::NT, G::smem_bytes, h->stream>>>(
-        pop_planes<T, S>(h, a), aux_planes<T, S>(h, a), pop_planes<T, S>(h, b), aux_planes<T, S>(h, b), h->kp,
-        h->march_nseg);
-    return cudaGetLastError();
-}
-
-// Paired-column marching kernel with NT threads (strips of 2 (NT - 4) columns).
-template <typename T, typename S, int NT>
+template <typename T, typename S, int NT, int MINB>
 static cudaError_t pair_setup(hlbm_handle *h)
 {
     using G = PairGeom<T, NT>;
-    cudaError_t e = cudaFuncSetAttribute(march_pair_kernel<T, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::smem_bytes);
+    const void *fn = pair_kernel_ptr<T, S, NT, MINB>(h);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_pair_kernel<T, S, NT>, NT, G::smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, G::smem_bytes);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
     const long long strips = (h->p.nx + G::W - 1) / G::W;
     const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * sms;
     long long nseg = (cap + strips - 1) / strips;
+    const long long least = (h->p.ny + kMarchMaxRows - 1) / kMarchMaxRows;
+    if (nseg < least) nseg = least;
     const long long most = h->p.ny / kMarchMinRows > 0 ? h->p.ny / kMarchMinRows : 1;
     if (nseg > most) nseg = most;
     const int rows = env_choice("HLBM_MARCH_ROWS", 0, 1, 1 << 20);
@@ -303,39 +281,49 @@ static cudaError_t pair_setup(hlbm_handle *h)
     return cudaSuccess;
 }
 
-template <typename T, typename S, int NT>
+template <typename T, typename S, int NT, int MINB>
 static cudaError_t launch_pair(hlbm_handle *h)
 {
     using G = PairGeom<T, NT>;
     dim3 grid((h->p.nx + G::W - 1) / G::W, h->march_nseg);
     const int a = h->cur, b = h->cur ^ 1;
-    march_pair_kernel<T, S, NT><<<grid, NT, G::smem_bytes, h->stream>>>(
-        pop_planes<T, S>(h, a), aux_planes<T, S>(h, a), pop_planes<T, S>(h, b), aux_planes<T, S>(h, b), h->kp,
-        h->march_nseg);
+    const typename S::raw *inF = pop_planes<T, S>(h, a);
+    const T *inA = aux_planes<T, S>(h, a);
+    typename S::raw *outF = pop_planes<T, S>(h, b);
+    T *outA = aux_planes<T, S>(h, b);
+    const bool sig = h->kp.sigma_nonzero != 0, phi0 = h->kp.phi_mode == 0;
+    if (sig && phi0)
+        march_pair_kernel<T, S, NT, MINB, true, true><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
+    else if (sig)
+        march_pair_kernel<T, S, NT, MINB, true, false><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
+    else if (phi0)
+        march_pair_kernel<T, S, NT, MINB, false, true><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
+    else
+        march_pair_kernel<T, S, NT, MINB, false, false><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
     return cudaGetLastError();
 }
 
-// Marching kernels: 0-3 one column per thread, strips of 128, 96, 64, 224
-// columns; 4-7 two columns per thread, 64, 96, 128, 160 threads (strips
-// of 120, 184, 248, 312 columns).
+// Marching kernel variants: 0 = 64 threads at <= 128 registers (strips of
+// 120 columns; the default), 1 = 96 threads at <= 136, 2 = 128 threads at
+// <= 128, 3 = 64 threads without a register cap.  FP64 runs without a cap
+// (its pair state does not fit 128 registers).
 template <typename T, typename S, bool Launch>
 static cudaError_t march_dispatch(hlbm_handle *h)
 {
+    constexpr bool f64 = sizeof(T) == 8;
     switch (h->march_variant) {
-    case 1: return Launch ? launch_march<T, S, 96>(h) : march_setup<T, S, 96>(h);
-    case 2: return Launch ? launch_march<T, S, 64>(h) : march_setup<T, S, 64>(h);
-    case 3: return Launch ? launch_march<T, S, 224>(h) : march_setup<T, S, 224>(h);
-    case 4: return Launch ? launch_pair<T, S, 64>(h) : pair_setup<T, S, 64>(h);
-    case 5: return Launch ? launch_pair<T, S, 96>(h) : pair_setup<T, S, 96>(h);
-    case 6: return Launch ? launch_pair<T, S, 128>(h) : pair_setup<T, S, 128>(h);
-    case 7: return Launch ? launch_pair<T, S, 160>(h) : pair_setup<T, S, 160>(h);
-    default: return Launch ? launch_march<T, S, 128>(h) : march_setup<T, S, 128>(h);
+    case 1: return Launch ? launch_pair<T, S, 96, f64 ? 1 : 5>(h) : pair_setup<T, S, 96, f64 ? 1 : 5>(h);
+    case 2: return Launch ? launch_pair<T, S, 128, f64 ? 1 : 4>(h) : pair_setup<T, S, 128, f64 ? 1 : 4>(h);
+    case 3: return Launch ? launch_pair<T, S, 64, 1>(h) : pair_setup<T, S, 64, 1>(h);
+    default: return Launch ? launch_pair<T, S, 64, f64 ? 1 : 8>(h) : pair_setup<T, S, 64, f64 ? 1 : 8>(h);
     }
 }
 
 static cudaError_t setup_march(hlbm_handle *h)
 {
-    h->march_variant = env_choice("HLBM_MARCH", -1, -1, kNumMarch);
+    // FP32 and the 16-bit storage forms march by default; FP64 uses the
+    // tiled kernel.  HLBM_MARCH=<k> picks a variant, -1 the tiled / TMA kernels.
+    h->march_variant = env_choice("HLBM_MARCH", h->p.precision == HLBM_FP64 ? -1 : 0, -1, kNumMarch);
     if (h->march_variant < 0) return cudaSuccess;
     return with_types(h, [&](auto ty) {
         using T = typename decltype(ty)::t;
@@ -547,7 +535,8 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         return HLBM_ERR_CUDA;
     }
     fill_kparams(h);
-    if ((params->precision == HLBM_FP32 && setup_fp32_kernel(h) != cudaSuccess) || setup_march(h) != cudaSuccess) {
+    if (setup_march(h) != cudaSuccess ||
+        (h->march_variant < 0 && params->precision == HLBM_FP32 && setup_fp32_kernel(h) != cudaSuccess)) {
         cudaGetLastError();
         hlbm_destroy(h);
         return HLBM_ERR_CUDA;

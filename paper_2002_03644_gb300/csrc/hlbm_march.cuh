@@ -1,22 +1,20 @@
 // hlbm_march.cuh -- the fused step of Algorithm 1 (steps 5-11) as a
-// row-marching kernel: each CTA owns a strip of W columns and walks down a
-// segment of rows, so that only the x halo is loaded and computed twice.
+// row-marching kernel: each CTA owns a strip of columns and walks down a
+// segment of rows, so that only the x halo is loaded and computed twice
+// (a tiled kernel recomputes a halo in both directions).
 //
 // Per row r of the segment one iteration does, separated by two barriers:
-//   load:    F(n) of row r+2 on columns x0-2 .. x0+W+1 and s(n) of row r+3
-//            on x0-3 .. x0+W+2 (prefetched into registers one iteration
-//            earlier), the level-n rho, u, theta of row r+2 (local moments
-//            of F(n), theta from s(n) of the same cell)
-//   phase 2: level n+1 of row r+1 on x0-1 .. x0+W: the entropy update
-//            (step 7), pull-streaming and moments (steps 5-6), theta
-//            (step 8), and the second moments of the pulled populations
-//            when sigma > 0
-//   phase 3: row r on x0 .. x0+W-1: E1, E2, a1 and the regularised
-//            collision (steps 9-11), written as F(n+1), s(n+1), a1(n+1).
-// Rows live in shared-memory rings: 3 rows of F and of the level-n macros,
-// 5 rows of s, 3 rows of level-(n+1) values.  A segment starts four rows
-// early to fill them.  The arithmetic of every cell is that of the tiled
-// kernel, term by term, so both give the same numbers.
+//   load:    F(n) of row r+2 and s(n) of row r+3 (prefetched into registers
+//            one iteration earlier), the level-n rho, u, theta of row r+2
+//            (local moments of F(n), theta from s(n) of the same cell)
+//   phase 2: level n+1 of row r+1: the entropy update (step 7),
+//            pull-streaming and moments (steps 5-6), theta (step 8), and
+//            the second moments of the pulled populations when sigma > 0
+//   phase 3: row r: E1, E2, a1 and the regularised collision (steps 9-11),
+//            written as F(n+1), s(n+1), a1(n+1).
+// Rows live in shared-memory rings; a segment starts four rows early to
+// fill them.  The arithmetic of every cell is that of the tiled kernel,
+// term by term.
 //
 // Boundaries use the index maps of the tiled kernel: a row or column off
 // the domain maps to its periodic image, to the nearest edge cell
@@ -28,21 +26,6 @@
 #include "hlbm_device.cuh"
 
 namespace hlbm {
-
-template <typename T, int W>
-struct MarchGeom {
-    static constexpr int NT = W + 32;       // the last warp covers the x halo
-    static constexpr int FC = W + 4;        // F and level-n macro columns
-    static constexpr int SC = W + 6;        // s columns
-    static constexpr int NC = W + 2;        // level-(n+1) columns
-    static constexpr int NQ = 8;            // rho, u_x, u_y, theta, s, m_xx, m_yy, m_xy
-    static constexpr int OFF_F = 0;                      // [3][9][FC]
-    static constexpr int OFF_M = OFF_F + 3 * 9 * FC;     // [3][4][FC]
-    static constexpr int OFF_S = OFF_M + 3 * 4 * FC;     // [5][SC]
-    static constexpr int OFF_N = OFF_S + 5 * SC;         // [3][NQ][NC]
-    static constexpr int N = OFF_N + 3 * NQ * NC;
-    static constexpr size_t smem_bytes = sizeof(T) * (size_t)N;
-};
 
 // Row (or column) of the cell that gy (gx) maps to, or -(side + 1) on a
 // Dirichlet side.
@@ -77,241 +60,6 @@ __device__ __forceinline__ int seg_start(int k, int nseg, int ny)
     return (int)(((long long)k * ny) / nseg);
 }
 
-template <typename T, typename S, int W>
-__global__ void __launch_bounds__(W + 32)
-march_step_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
-                  typename S::raw *__restrict__ outF, T *__restrict__ outA, const KParams kp, const int nseg)
-{
-    using G = MarchGeom<T, W>;
-    constexpr int FC = G::FC, SC = G::SC, NC = G::NC, NQ = G::NQ;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *const rF = reinterpret_cast<T *>(smem_raw) + G::OFF_F;
-    T *const rM = reinterpret_cast<T *>(smem_raw) + G::OFF_M;
-    T *const rS = reinterpret_cast<T *>(smem_raw) + G::OFF_S;
-    T *const rN = reinterpret_cast<T *>(smem_raw) + G::OFF_N;
-
-    Consts<T> cs;
-    cs.load(kp);
-    const Side<T> side{kp};
-    const T third = T(1) / T(3);
-    const long long P = kp.plane;
-    const int pitch = kp.pitch;
-    const int t = threadIdx.x;
-    const int x0 = blockIdx.x * W;
-    const int ys = seg_start(blockIdx.y, nseg, kp.ny), ye = seg_start(blockIdx.y + 1, nseg, kp.ny);
-    const int base = ys - 4;  // ring slots count rows from here (all used rows lie above it)
-
-    // load-phase column (s on t < SC, F and macros on 1 <= t < SC - 1)
-    const int mcL = map_col(x0 - 3 + t, kp);
-    const bool doS = t < SC, doF = t >= 1 && t < SC - 1;
-    // phase-2 column
-    const int gx2 = x0 - 1 + t;
-    const int mc2 = map_col(gx2, kp);
-    const bool do2 = t < NC;
-    const bool out2x = gx2 < 0 || gx2 >= kp.nx;
-    const int side2x = gx2 < 0 ? 0 : 1;
-    const bool dir2x = out2x && kp.bc[side2x] == BC_DIRICHLET;
-    const bool zg2x = out2x && kp.bc[side2x] == BC_ZEROGRAD;
-    // phase-3 column and its neighbours in the level-(n+1) ring
-    const int gx3 = x0 + t;
-    const bool do3 = t < W && gx3 < kp.nx;
-    const int cl = (gx3 == 0 && kp.bc[0] == BC_ZEROGRAD) ? t + 1 : t;
-    const int cr = (gx3 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD) ? t + 1 : t + 2;
-
-    // prefetch registers: F(n) of row r+2, s(n) of row r+3, a1(n) of row r+1
-    T pF[9], pS = T(0), pA0 = T(0), pA1 = T(0), pA2 = T(0);
-#pragma unroll
-    for (int i = 0; i < 9; i++) pF[i] = T(0);
-    auto fetch = [&](int r) {
-        if (doF) {
-            const int o = join_map(map_row(r + 2, kp), mcL, pitch);
-            if (o >= 0) {
-                const typename S::raw *src = inF + o;
-#pragma unroll
-                for (int i = 0; i < 9; i++) pF[i] = S::get(src[i * P], i, kp);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 9; i++) pF[i] = side.F(-o - 1, i);
-            }
-        }
-        if (doS) {
-            const int o = join_map(map_row(r + 3, kp), mcL, pitch);
-            pS = o >= 0 ? __ldg(inA + A_S * P + o) : side.s_(-o - 1);
-        }
-        if (kp.phi_mode == 0 && do2) {
-            const int o = join_map(map_row(r + 1, kp), mc2, pitch);
-            if (o >= 0) {
-                pA0 = __ldg(inA + A_XX * P + o);
-                pA1 = __ldg(inA + A_XY * P + o);
-                pA2 = __ldg(inA + A_YY * P + o);
-            }
-        }
-    };
-
-    // s(n) of rows ys-3 and ys-2; the latter stays in a register for the
-    // level-n theta of row ys-2
-    T s_prev = T(0);
-    if (doS) {
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            const int gy = ys - 3 + k;
-            const int o = join_map(map_row(gy, kp), mcL, pitch);
-            const T v = o >= 0 ? __ldg(inA + A_S * P + o) : side.s_(-o - 1);
-            rS[((gy - base) % 5) * SC + t] = v;
-            s_prev = v;
-        }
-    }
-    fetch(base);
-
-    for (int r = base; r < ye; r++) {
-        // ---- load phase: row r+2 of F(n) and of the level-n macros, row r+3 of s(n)
-        T f[9];
-#pragma unroll
-        for (int i = 0; i < 9; i++) f[i] = pF[i];
-        const T snew = pS, a_xx = pA0, a_xy = pA1, a_yy = pA2;
-        if (r + 1 < ye) fetch(r + 1);
-        if (doF) {
-            const int yF = r + 2;
-            const int sl = (yF - base) % 3;
-            const int c = t - 1;
-#pragma unroll
-            for (int i = 0; i < 9; i++) rF[(sl * 9 + i) * FC + c] = f[i];
-            const int o = join_map(map_row(yF, kp), mcL, pitch);
-            T rho, ux, uy, th;
-            if (o >= 0) {
-                T jx, jy;
-                moments(f, rho, jx, jy);
-                const T ir = fdiv(T(1), rho);
-                ux = jx * ir;
-                uy = jy * ir;
-                th = cs.theta(rho, s_prev);
-            } else {
-                const int sd = -o - 1;
-                rho = side.rho(sd); ux = side.ux(sd); uy = side.uy(sd); th = side.th(sd);
-            }
-            T *m = rM + sl * 4 * FC + c;
-            m[0] = rho; m[FC] = ux; m[2 * FC] = uy; m[3 * FC] = th;
-        }
-        if (doS) {
-            rS[((r + 3 - base) % 5) * SC + t] = snew;
-            s_prev = snew;
-        }
-        __syncthreads();
-
-        // ---- phase 2: level n+1 of row r+1
-        const int y2 = r + 1;
-        if (y2 >= ys - 1 && do2) {
-            const bool out2y = y2 < 0 || y2 >= kp.ny;
-            const int side2y = y2 < 0 ? 2 : 3;
-            const bool dir2y = out2y && kp.bc[side2y] == BC_DIRICHLET;
-            const bool zg2y = out2y && kp.bc[side2y] == BC_ZEROGRAD;
-            T *n = rN + ((y2 - base) % 3) * NQ * NC + t;
-            if (dir2y || dir2x) {
-                const int sd = dir2y ? side2y : side2x;
-                n[0] = side.rho(sd); n[NC] = side.ux(sd); n[2 * NC] = side.uy(sd);
-                n[3 * NC] = side.th(sd); n[4 * NC] = side.s_(sd);
-            } else if (!(zg2y || zg2x)) {
-                const int m0 = (y2 - base) % 3, mm = (y2 - 1 - base) % 3, mp = (y2 + 1 - base) % 3;
-                const int cF = t + 1;
-                const T *M0 = rM + m0 * 4 * FC + cF, *Mm = rM + mm * 4 * FC + cF, *Mp = rM + mp * 4 * FC + cF;
-                const T rho0 = M0[0], ux0 = M0[FC], uy0 = M0[2 * FC], th0 = M0[3 * FC];
-                const T dxux = T(0.5) * (M0[FC + 1] - M0[FC - 1]);
-                const T dyux = T(0.5) * (Mp[FC] - Mm[FC]);
-                const T dxuy = T(0.5) * (M0[2 * FC + 1] - M0[2 * FC - 1]);
-                const T dyuy = T(0.5) * (Mp[2 * FC] - Mm[2 * FC]);
-                const T lap = (M0[3 * FC + 1] + M0[3 * FC - 1]) + (Mp[3 * FC] + Mm[3 * FC]) - T(4) * th0;
-                const int cS = t + 2;
-                const T *S0 = rS + ((y2 - base) % 5) * SC + cS;
-                const T s0 = S0[0];
-                const T sym2 = rS[((y2 - 2 - base) % 5) * SC + cS], sym = rS[((y2 - 1 - base) % 5) * SC + cS];
-                const T syp = rS[((y2 + 1 - base) % 5) * SC + cS], syp2 = rS[((y2 + 2 - base) % 5) * SC + cS];
-                const T adv = muscl_adv(ux0, S0[-2], S0[-1], s0, S0[1], S0[2]) + muscl_adv(uy0, sym2, sym, s0, syp, syp2);
-                const T rt = rho0 * th0;
-                const T p0 = rt * third;
-                T phi;
-                if (kp.phi_mode == 0) {
-                    phi = -fdiv(cs.two_mu, cs.two_mu + p0) * (a_xx * dxux + a_xy * (dyux + dxuy) + a_yy * dyuy);
-                } else {
-                    const T d1 = dxux - dyuy, d2 = dyux + dxuy;
-                    phi = cs.mu * (d1 * d1 + d2 * d2);
-                }
-                const T s1 = s0 - adv + fdiv(cs.lam * lap + phi, rt);
-                // pull: F_i from (x - c_ix, y - c_iy)
-                T g[9];
-#pragma unroll
-                for (int i = 0; i < 9; i++) {
-                    const int sl = cyi(i) > 0 ? mm : (cyi(i) < 0 ? mp : m0);
-                    g[i] = rF[(sl * 9 + i) * FC + cF - cxi(i)];
-                }
-                T rho1, jx, jy;
-                moments(g, rho1, jx, jy);
-                const T ir = fdiv(T(1), rho1);
-                n[0] = rho1; n[NC] = jx * ir; n[2 * NC] = jy * ir;
-                n[3 * NC] = cs.theta(rho1, s1);
-                n[4 * NC] = s1;
-                if (kp.sigma_nonzero) {
-                    const T diag = (g[5] + g[6]) + (g[7] + g[8]);
-                    n[5 * NC] = (g[1] + g[3]) + diag;
-                    n[6 * NC] = (g[2] + g[4]) + diag;
-                    n[7 * NC] = (g[5] - g[6]) + (g[7] - g[8]);
-                }
-            }
-        }
-        __syncthreads();
-
-        // ---- phase 3: steps 9-11 and the next collision on row r
-        if (r >= ys && do3) {
-            const int n0 = (r - base) % 3;
-            const int nm = (r == 0 && kp.bc[2] == BC_ZEROGRAD) ? n0 : (r - 1 - base) % 3;
-            const int np = (r == kp.ny - 1 && kp.bc[3] == BC_ZEROGRAD) ? n0 : (r + 1 - base) % 3;
-            const T *N0 = rN + n0 * NQ * NC, *Nm = rN + nm * NQ * NC, *Np = rN + np * NQ * NC;
-            const int k = t + 1;
-            const T rho = N0[k], ux = N0[NC + k], uy = N0[2 * NC + k], th = N0[3 * NC + k];
-            const T uxm = N0[NC + cl], uxp = N0[NC + cr], uym = Nm[2 * NC + k], uyp = Np[2 * NC + k];
-            const T dxux = T(0.5) * (uxp - uxm);
-            const T dyux = T(0.5) * (Np[NC + k] - Nm[NC + k]);
-            const T dxuy = T(0.5) * (N0[2 * NC + cr] - N0[2 * NC + cl]);
-            const T dyuy = T(0.5) * (uyp - uym);
-            const T p = rho * th * third;
-            const T gxc = gamma_defect(rho, ux, th), gyc = gamma_defect(rho, uy, th);
-            const T gxm = gamma_defect(N0[cl], uxm, N0[3 * NC + cl]);
-            const T gxp = gamma_defect(N0[cr], uxp, N0[3 * NC + cr]);
-            const T gym = gamma_defect(Nm[k], uym, Nm[3 * NC + k]);
-            const T gyp = gamma_defect(Np[k], uyp, Np[3 * NC + k]);
-            const bool cen = kp.e1_centred != 0;
-            const T e1xx = (ux > T(0) && !cen) ? gxc - gxm : ((ux < T(0) && !cen) ? gxp - gxc : T(0.5) * (gxp - gxm));
-            const T e1yy = (uy > T(0) && !cen) ? gyc - gym : ((uy < T(0) && !cen) ? gyp - gyc : T(0.5) * (gyp - gym));
-            const T e2 = p * cs.two_m_gamma * (dxux + dyuy);
-            const T ex = e1xx + e2, ey = e1yy + e2;
-            const T cfd = -(cs.mu + T(0.5) * p);
-            const T fdxx = cfd * (dxux - dyuy), fdxy = cfd * (dyux + dxuy);
-            T axx, axy, ayy;
-            if (kp.sigma_nonzero) {
-                const T prxx = N0[5 * NC + k] - rho * ux * ux - p + T(0.5) * ex;
-                const T pryy = N0[6 * NC + k] - rho * uy * uy - p + T(0.5) * ey;
-                const T prxy = N0[7 * NC + k] - rho * ux * uy;
-                axx = cs.sigma * prxx + cs.one_m_sigma * fdxx;
-                ayy = cs.sigma * pryy - cs.one_m_sigma * fdxx;
-                axy = cs.sigma * prxy + cs.one_m_sigma * fdxy;
-            } else {
-                axx = fdxx; ayy = -fdxx; axy = fdxy;
-            }
-            const T omega = fdiv(cs.two_mu - p, cs.two_mu + p);
-            T fo[9];
-            build_populations(rho, ux, uy, th, axx, axy, ayy, ex, ey, omega, fo);
-            const long long o = (long long)r * pitch + gx3;
-            typename S::raw *dF = outF + o;
-#pragma unroll
-            for (int i = 0; i < 9; i++) dF[i * P] = S::put(fo[i], i, kp);
-            T *dA = outA + o;
-            dA[A_S * P] = N0[4 * NC + k];
-            dA[A_XX * P] = axx;
-            dA[A_XY * P] = axy;
-            dA[A_YY * P] = ayy;
-        }
-    }
-}
-
 // ---- paired-column form -----------------------------------------------------------
 // The same pipeline with each thread owning two horizontally adjacent
 // columns: global and shared-memory traffic moves in 2-element accesses, a
@@ -321,6 +69,10 @@ march_step_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
 //   NT threads; ring columns x0-4 .. x0+2NT-5 (pair t = columns 2t, 2t+1);
 //   load phase on every pair, phase 2 on pairs 1 .. NT-2 (x0-2 .. x0+W+1),
 //   phase 3 on pairs 2 .. NT-3 (the W = 2 (NT - 4) output columns).
+// The pull reads population i of row y - c_iy only, so the F rows are kept
+// by population group: (4, 7, 8) for one row (they stream from y + 1),
+// (0, 1, 3) for two, (2, 5, 6) for three (they stream from y - 1).
+// SIG (sigma > 0) and PHI0 (regularised Phi) are compile-time choices.
 
 // Level-n+1 values of one cell and the second moments of its pulled
 // populations (used by a1^PR when sigma > 0).
@@ -331,11 +83,11 @@ struct CellN1 {
 
 // Steps 5-8 for one cell (the arithmetic of phase 2 of the tiled kernel).
 // W/E/S/N = x-1, x+1, y-1, y+1; g[] the pulled populations.
-template <typename T>
-__device__ __forceinline__ CellN1<T> level_np1(const Consts<T> &cs, const KParams &kp, T rho0, T ux0, T uy0, T th0,
-                                              T uxW, T uxE, T uxS, T uxN, T uyW, T uyE, T uyS, T uyN, T thW, T thE,
-                                              T thS, T thN, T sWW, T sW, T s0, T sE, T sEE, T sSS, T sS, T sN, T sNN,
-                                              T a_xx, T a_xy, T a_yy, const T g[9])
+template <typename T, bool SIG, bool PHI0>
+__device__ __forceinline__ CellN1<T> level_np1(const Consts<T> &cs, T rho0, T ux0, T uy0, T th0, T uxW, T uxE,
+                                              T uxS, T uxN, T uyW, T uyE, T uyS, T uyN, T thW, T thE, T thS, T thN,
+                                              T sWW, T sW, T s0, T sE, T sEE, T sSS, T sS, T sN, T sNN, T a_xx,
+                                              T a_xy, T a_yy, const T g[9])
 {
     const T third = T(1) / T(3);
     const T dxux = T(0.5) * (uxE - uxW);
@@ -347,7 +99,7 @@ __device__ __forceinline__ CellN1<T> level_np1(const Consts<T> &cs, const KParam
     const T rt = rho0 * th0;
     const T p0 = rt * third;
     T phi;
-    if (kp.phi_mode == 0) {
+    if (PHI0) {
         phi = -fdiv(cs.two_mu, cs.two_mu + p0) * (a_xx * dxux + a_xy * (dyux + dxuy) + a_yy * dyuy);
     } else {
         const T d1 = dxux - dyuy, d2 = dyux + dxuy;
@@ -361,19 +113,23 @@ __device__ __forceinline__ CellN1<T> level_np1(const Consts<T> &cs, const KParam
     o.ux = jx * ir;
     o.uy = jy * ir;
     o.th = cs.theta(o.rho, o.s);
-    const T diag = (g[5] + g[6]) + (g[7] + g[8]);
-    o.mxx = (g[1] + g[3]) + diag;
-    o.myy = (g[2] + g[4]) + diag;
-    o.mxy = (g[5] - g[6]) + (g[7] - g[8]);
+    if (SIG) {
+        const T diag = (g[5] + g[6]) + (g[7] + g[8]);
+        o.mxx = (g[1] + g[3]) + diag;
+        o.myy = (g[2] + g[4]) + diag;
+        o.mxy = (g[5] - g[6]) + (g[7] - g[8]);
+    } else {
+        o.mxx = o.myy = o.mxy = T(0);
+    }
     return o;
 }
 
 // Steps 9-11 and the next collision for one cell (phase 3 of the tiled
 // kernel) from its level-(n+1) values and those of its four neighbours.
-template <typename T>
-__device__ __forceinline__ void collide_cell(const Consts<T> &cs, const KParams &kp, const CellN1<T> &c, T rW,
-                                             T uxW, T uyW, T thW, T rE, T uxE, T uyE, T thE, T rS, T uxS, T uyS,
-                                             T thS, T rN, T uxN, T uyN, T thN, T f[9], T &axx, T &axy, T &ayy)
+template <typename T, bool SIG>
+__device__ __forceinline__ void collide_cell(const Consts<T> &cs, bool cen, const CellN1<T> &c, T rW, T uxW, T uyW,
+                                             T thW, T rE, T uxE, T uyE, T thE, T rS, T uxS, T uyS, T thS, T rN,
+                                             T uxN, T uyN, T thN, T f[9], T &axx, T &axy, T &ayy)
 {
     const T third = T(1) / T(3);
     const T rho = c.rho, ux = c.ux, uy = c.uy, th = c.th;
@@ -385,14 +141,13 @@ __device__ __forceinline__ void collide_cell(const Consts<T> &cs, const KParams 
     const T gxc = gamma_defect(rho, ux, th), gyc = gamma_defect(rho, uy, th);
     const T gxm = gamma_defect(rW, uxW, thW), gxp = gamma_defect(rE, uxE, thE);
     const T gym = gamma_defect(rS, uyS, thS), gyp = gamma_defect(rN, uyN, thN);
-    const bool cen = kp.e1_centred != 0;
     const T e1xx = (ux > T(0) && !cen) ? gxc - gxm : ((ux < T(0) && !cen) ? gxp - gxc : T(0.5) * (gxp - gxm));
     const T e1yy = (uy > T(0) && !cen) ? gyc - gym : ((uy < T(0) && !cen) ? gyp - gyc : T(0.5) * (gyp - gym));
     const T e2 = p * cs.two_m_gamma * (dxux + dyuy);
     const T ex = e1xx + e2, ey = e1yy + e2;
     const T cfd = -(cs.mu + T(0.5) * p);
     const T fdxx = cfd * (dxux - dyuy), fdxy = cfd * (dyux + dxuy);
-    if (kp.sigma_nonzero) {
+    if (SIG) {
         const T prxx = c.mxx - rho * ux * ux - p + T(0.5) * ex;
         const T pryy = c.myy - rho * uy * uy - p + T(0.5) * ey;
         const T prxy = c.mxy - rho * ux * uy;
@@ -411,19 +166,18 @@ struct PairGeom {
     static constexpr int NP = NT - 4;   // output pairs
     static constexpr int W = 2 * NP;    // output columns
     static constexpr int CW = 2 * NT;   // ring columns
-    static constexpr int OFF_F = 0;                      // [3][9][CW]
-    static constexpr int OFF_M = OFF_F + 3 * 9 * CW;     // [3][4][CW]  rho, u_x, u_y, theta (level n)
-    static constexpr int OFF_S = OFF_M + 3 * 4 * CW;     // [5][CW]
+    static constexpr int OFF_GA = 0;                     // [3][CW]     F_4, F_7, F_8 of row r+2
+    static constexpr int OFF_GB = OFF_GA + 3 * CW;       // [2][3][CW]  F_0, F_1, F_3 of rows r+1, r+2
+    static constexpr int OFF_GC = OFF_GB + 6 * CW;       // [3][3][CW]  F_2, F_5, F_6 of rows r .. r+2
+    static constexpr int OFF_M = OFF_GC + 9 * CW;        // [3][4][CW]  rho, u_x, u_y, theta (level n)
+    static constexpr int OFF_S = OFF_M + 12 * CW;        // [5][CW]
     static constexpr int OFF_N = OFF_S + 5 * CW;         // [3][4][CW]  rho, u_x, u_y, theta (level n+1)
-    static constexpr int N = OFF_N + 3 * 4 * CW;
+    static constexpr int N = OFF_N + 12 * CW;
     static constexpr size_t smem_bytes = sizeof(T) * (size_t)N;
 };
 
-// Mapped offset of a column (or -(side+1)) in a row already mapped to mr.
-__device__ __forceinline__ int cell_at(int mr, int mc, int pitch) { return join_map(mr, mc, pitch); }
-
-template <typename T, typename S, int NT>
-__global__ void __launch_bounds__(NT)
+template <typename T, typename S, int NT, int MINB, bool SIG, bool PHI0>
+__global__ void __launch_bounds__(NT, MINB)
 march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
                   typename S::raw *__restrict__ outF, T *__restrict__ outA, const KParams kp, const int nseg)
 {
@@ -432,14 +186,18 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
     using raw = typename S::raw;
     using raw2 = typename S::raw2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *const rF = reinterpret_cast<V *>(reinterpret_cast<T *>(smem_raw) + G::OFF_F);  // [3][9][NT]
-    V *const rM = reinterpret_cast<V *>(reinterpret_cast<T *>(smem_raw) + G::OFF_M);  // [3][4][NT]
-    V *const rS = reinterpret_cast<V *>(reinterpret_cast<T *>(smem_raw) + G::OFF_S);  // [5][NT]
-    V *const rN = reinterpret_cast<V *>(reinterpret_cast<T *>(smem_raw) + G::OFF_N);  // [3][4][NT]
+    T *const sm = reinterpret_cast<T *>(smem_raw);
+    V *const gA = reinterpret_cast<V *>(sm + G::OFF_GA);  // [3][NT] pairs
+    V *const gB = reinterpret_cast<V *>(sm + G::OFF_GB);  // [2][3][NT]
+    V *const gC = reinterpret_cast<V *>(sm + G::OFF_GC);  // [3][3][NT]
+    V *const rM = reinterpret_cast<V *>(sm + G::OFF_M);   // [3][4][NT]
+    V *const rS = reinterpret_cast<V *>(sm + G::OFF_S);   // [5][NT]
+    V *const rN = reinterpret_cast<V *>(sm + G::OFF_N);   // [3][4][NT]
 
     Consts<T> cs;
     cs.load(kp);
     const Side<T> side{kp};
+    const bool cen = kp.e1_centred != 0;
     const long long P = kp.plane;
     const int pitch = kp.pitch;
     const int t = threadIdx.x;
@@ -490,7 +248,7 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
                 fb[i] = S::get(v.y, i, kp);
             }
         } else {
-            const int oa = cell_at(mr, mcLa, pitch), ob = cell_at(mr, mcLb, pitch);
+            const int oa = join_map(mr, mcLa, pitch), ob = join_map(mr, mcLb, pitch);
 #pragma unroll
             for (int i = 0; i < 9; i++) {
                 fa[i] = oa >= 0 ? S::get(inF[oa + i * P], i, kp) : side.F(-oa - 1, i);
@@ -504,7 +262,7 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
             sa = v.x;
             sb = v.y;
         } else {
-            const int oa = cell_at(mr, mcLa, pitch), ob = cell_at(mr, mcLb, pitch);
+            const int oa = join_map(mr, mcLa, pitch), ob = join_map(mr, mcLb, pitch);
             sa = oa >= 0 ? inA[A_S * P + oa] : side.s_(-oa - 1);
             sb = ob >= 0 ? inA[A_S * P + ob] : side.s_(-ob - 1);
         }
@@ -512,7 +270,7 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
     auto fetch = [&](int r) {
         load_F(map_row(r + 2, kp), pFa, pFb);
         load_s(map_row(r + 3, kp), pSa, pSb);
-        if (kp.phi_mode == 0 && do2) {
+        if (PHI0 && do2) {
             const int mr = map_row(r + 1, kp);
             if (mr >= 0 && vec2) {
                 const T *src = inA + ((long long)mr * pitch + gx2);
@@ -523,7 +281,7 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
                     pA[1][k] = v.y;
                 }
             } else {
-                const int oa = cell_at(mr, mc2a, pitch), ob = cell_at(mr, mc2b, pitch);
+                const int oa = join_map(mr, mc2a, pitch), ob = join_map(mr, mc2b, pitch);
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
                     pA[0][k] = oa >= 0 ? inA[(A_XX + k) * P + oa] : T(0);
@@ -543,18 +301,19 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
     }
     fetch(base);
 
-    // ring slots of rows r .. r+2 (F, M), r-1 .. r+3 (s), r-1 .. r+1 (level n+1)
-    int fs0 = (ys - 4 - base) % 3, fs1 = (ys - 3 - base) % 3, fs2 = (ys - 2 - base) % 3;
-    int ss0 = (ys - 5 - base + 5) % 5, ss1 = (ys - 4 - base) % 5, ss2 = (ys - 3 - base) % 5,
-        ss3 = (ys - 2 - base) % 5, ss4 = (ys - 1 - base) % 5;
-    int ns0 = (ys - 5 - base + 3) % 3, ns1 = (ys - 4 - base) % 3, ns2 = (ys - 3 - base) % 3;
+    // ring slots: level-n rows r .. r+2 (fs*, also F_2,5,6), F_0,1,3 rows r+1 / r+2
+    // (bs*), s rows r-1 .. r+3 (ss*), level n+1 rows r-1 .. r+1 (ns*)
+    int fs0 = 0, fs1 = 1, fs2 = 2;
+    int bs1 = 1, bs2 = 0;
+    int ss0 = 4, ss1 = 0, ss2 = 1, ss3 = 2, ss4 = 3;
+    int ns0 = 2, ns1 = 0, ns2 = 1;
     CellN1<T> cur[2], nxt[2];
 #pragma unroll
     for (int c = 0; c < 2; c++) cur[c] = nxt[c] = CellN1<T>{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
 
     for (int r = base; r < ye; r++) {
-        // ---- load phase: row r+2 of F(n) and the level-n macros, row r+3 of s(n)
         {
+            // ---- load phase: row r+2 of F(n) and the level-n macros, row r+3 of s(n)
             T fa[9], fb[9];
 #pragma unroll
             for (int i = 0; i < 9; i++) { fa[i] = pFa[i]; fb[i] = pFb[i]; }
@@ -565,8 +324,15 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
 #pragma unroll
                 for (int k = 0; k < 3; k++) a2[c][k] = pA[c][k];
             if (r + 1 < ye) fetch(r + 1);
-#pragma unroll
-            for (int i = 0; i < 9; i++) rF[(fs2 * 9 + i) * NT + t] = Vec2<T>::make(fa[i], fb[i]);
+            gA[0 * NT + t] = Vec2<T>::make(fa[4], fb[4]);
+            gA[1 * NT + t] = Vec2<T>::make(fa[7], fb[7]);
+            gA[2 * NT + t] = Vec2<T>::make(fa[8], fb[8]);
+            gB[(bs2 * 3 + 0) * NT + t] = Vec2<T>::make(fa[0], fb[0]);
+            gB[(bs2 * 3 + 1) * NT + t] = Vec2<T>::make(fa[1], fb[1]);
+            gB[(bs2 * 3 + 2) * NT + t] = Vec2<T>::make(fa[3], fb[3]);
+            gC[(fs2 * 3 + 0) * NT + t] = Vec2<T>::make(fa[2], fb[2]);
+            gC[(fs2 * 3 + 1) * NT + t] = Vec2<T>::make(fa[5], fb[5]);
+            gC[(fs2 * 3 + 2) * NT + t] = Vec2<T>::make(fa[6], fb[6]);
             const int mr = map_row(r + 2, kp);
             T m[2][4];
             auto macros = [&](const T *f, T sv, int o, T *mm) {
@@ -582,8 +348,8 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
                     mm[0] = side.rho(sd); mm[1] = side.ux(sd); mm[2] = side.uy(sd); mm[3] = side.th(sd);
                 }
             };
-            macros(fa, sPa, cell_at(mr, mcLa, pitch), m[0]);
-            macros(fb, sPb, cell_at(mr, mcLb, pitch), m[1]);
+            macros(fa, sPa, join_map(mr, mcLa, pitch), m[0]);
+            macros(fb, sPb, join_map(mr, mcLb, pitch), m[1]);
 #pragma unroll
             for (int k = 0; k < 4; k++) rM[(fs2 * 4 + k) * NT + t] = Vec2<T>::make(m[0][k], m[1][k]);
             rS[ss4 * NT + t] = Vec2<T>::make(sna, snb);
@@ -609,40 +375,41 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
                 // s: pairs q-1 .. q+1 of row y2, pair q of rows y2-2 .. y2+2
                 const V sc0 = rS[ss2 * NT + q - 1], sc1 = rS[ss2 * NT + q], sc2 = rS[ss2 * NT + q + 1];
                 const V sS2 = rS[ss0 * NT + q], sS1 = rS[ss1 * NT + q], sN1 = rS[ss3 * NT + q], sN2 = rS[ss4 * NT + q];
-                // pull: F_i from (x - c_ix, y - c_iy); rows y2 (fs1), y2-1 (fs0), y2+1 (fs2)
+                // pull: F_i from (x - c_ix, y - c_iy): F_0,1,3 of row y2 (bs1), F_2,5,6 of
+                // row y2-1 (fs0), F_4,7,8 of row y2+1
                 T ga[9], gb[9];
                 {
-                    const V f0 = rF[(fs1 * 9 + 0) * NT + q], f2 = rF[(fs0 * 9 + 2) * NT + q], f4 = rF[(fs2 * 9 + 4) * NT + q];
+                    const V f0 = gB[(bs1 * 3 + 0) * NT + q], f2 = gC[(fs0 * 3 + 0) * NT + q], f4 = gA[0 * NT + q];
                     ga[0] = f0.x; gb[0] = f0.y;
                     ga[2] = f2.x; gb[2] = f2.y;
                     ga[4] = f4.x; gb[4] = f4.y;
                     // c_x = +1 (1, 5, 8): from x-1
-                    const V f1l = rF[(fs1 * 9 + 1) * NT + q - 1], f1c = rF[(fs1 * 9 + 1) * NT + q];
-                    const V f5l = rF[(fs0 * 9 + 5) * NT + q - 1], f5c = rF[(fs0 * 9 + 5) * NT + q];
-                    const V f8l = rF[(fs2 * 9 + 8) * NT + q - 1], f8c = rF[(fs2 * 9 + 8) * NT + q];
+                    const V f1l = gB[(bs1 * 3 + 1) * NT + q - 1], f1c = gB[(bs1 * 3 + 1) * NT + q];
+                    const V f5l = gC[(fs0 * 3 + 1) * NT + q - 1], f5c = gC[(fs0 * 3 + 1) * NT + q];
+                    const V f8l = gA[2 * NT + q - 1], f8c = gA[2 * NT + q];
                     ga[1] = f1l.y; gb[1] = f1c.x;
                     ga[5] = f5l.y; gb[5] = f5c.x;
                     ga[8] = f8l.y; gb[8] = f8c.x;
                     // c_x = -1 (3, 6, 7): from x+1
-                    const V f3c = rF[(fs1 * 9 + 3) * NT + q], f3r = rF[(fs1 * 9 + 3) * NT + q + 1];
-                    const V f6c = rF[(fs0 * 9 + 6) * NT + q], f6r = rF[(fs0 * 9 + 6) * NT + q + 1];
-                    const V f7c = rF[(fs2 * 9 + 7) * NT + q], f7r = rF[(fs2 * 9 + 7) * NT + q + 1];
+                    const V f3c = gB[(bs1 * 3 + 2) * NT + q], f3r = gB[(bs1 * 3 + 2) * NT + q + 1];
+                    const V f6c = gC[(fs0 * 3 + 2) * NT + q], f6r = gC[(fs0 * 3 + 2) * NT + q + 1];
+                    const V f7c = gA[1 * NT + q], f7r = gA[1 * NT + q + 1];
                     ga[3] = f3c.y; gb[3] = f3r.x;
                     ga[6] = f6c.y; gb[6] = f6r.x;
                     ga[7] = f7c.y; gb[7] = f7r.x;
                 }
-                nxt[0] = level_np1<T>(cs, kp, rho0.x, mc[0][1].x, mc[1][1].x, mc[2][1].x,
-                                      mc[0][0].y, mc[0][1].y, ms[0].x, mn[0].x,
-                                      mc[1][0].y, mc[1][1].y, ms[1].x, mn[1].x,
-                                      mc[2][0].y, mc[2][1].y, ms[2].x, mn[2].x,
-                                      sc0.x, sc0.y, sc1.x, sc1.y, sc2.x, sS2.x, sS1.x, sN1.x, sN2.x,
-                                      a2[0][0], a2[0][1], a2[0][2], ga);
-                nxt[1] = level_np1<T>(cs, kp, rho0.y, mc[0][1].y, mc[1][1].y, mc[2][1].y,
-                                      mc[0][1].x, mc[0][2].x, ms[0].y, mn[0].y,
-                                      mc[1][1].x, mc[1][2].x, ms[1].y, mn[1].y,
-                                      mc[2][1].x, mc[2][2].x, ms[2].y, mn[2].y,
-                                      sc0.y, sc1.x, sc1.y, sc2.x, sc2.y, sS2.y, sS1.y, sN1.y, sN2.y,
-                                      a2[1][0], a2[1][1], a2[1][2], gb);
+                nxt[0] = level_np1<T, SIG, PHI0>(cs, rho0.x, mc[0][1].x, mc[1][1].x, mc[2][1].x,
+                                                 mc[0][0].y, mc[0][1].y, ms[0].x, mn[0].x,
+                                                 mc[1][0].y, mc[1][1].y, ms[1].x, mn[1].x,
+                                                 mc[2][0].y, mc[2][1].y, ms[2].x, mn[2].x,
+                                                 sc0.x, sc0.y, sc1.x, sc1.y, sc2.x, sS2.x, sS1.x, sN1.x, sN2.x,
+                                                 a2[0][0], a2[0][1], a2[0][2], ga);
+                nxt[1] = level_np1<T, SIG, PHI0>(cs, rho0.y, mc[0][1].y, mc[1][1].y, mc[2][1].y,
+                                                 mc[0][1].x, mc[0][2].x, ms[0].y, mn[0].y,
+                                                 mc[1][1].x, mc[1][2].x, ms[1].y, mn[1].y,
+                                                 mc[2][1].x, mc[2][2].x, ms[2].y, mn[2].y,
+                                                 sc0.y, sc1.x, sc1.y, sc2.x, sc2.y, sS2.y, sS1.y, sN1.y, sN2.y,
+                                                 a2[1][0], a2[1][1], a2[1][2], gb);
                 // Dirichlet cells hold the side's constants
                 const bool out2y = y2 < 0 || y2 >= kp.ny;
                 const int side2y = y2 < 0 ? 2 : 3;
@@ -686,16 +453,16 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
                     bEth = zgEb ? B.th : nE[3].x;
             T fa[9], fb[9], aa[3], ab[3];
             if (v3a) {
-                collide_cell<T>(cs, kp, A, aWr, aWux, aWuy, aWth, aEr, aEux, aEuy, aEth,
-                                zS ? A.rho : nS[0].x, zS ? A.ux : nS[1].x, zS ? A.uy : nS[2].x, zS ? A.th : nS[3].x,
-                                zN ? A.rho : nN[0].x, zN ? A.ux : nN[1].x, zN ? A.uy : nN[2].x, zN ? A.th : nN[3].x,
-                                fa, aa[0], aa[1], aa[2]);
+                collide_cell<T, SIG>(cs, cen, A, aWr, aWux, aWuy, aWth, aEr, aEux, aEuy, aEth,
+                                     zS ? A.rho : nS[0].x, zS ? A.ux : nS[1].x, zS ? A.uy : nS[2].x, zS ? A.th : nS[3].x,
+                                     zN ? A.rho : nN[0].x, zN ? A.ux : nN[1].x, zN ? A.uy : nN[2].x, zN ? A.th : nN[3].x,
+                                     fa, aa[0], aa[1], aa[2]);
             }
             if (v3b) {
-                collide_cell<T>(cs, kp, B, A.rho, A.ux, A.uy, A.th, bEr, bEux, bEuy, bEth,
-                                zS ? B.rho : nS[0].y, zS ? B.ux : nS[1].y, zS ? B.uy : nS[2].y, zS ? B.th : nS[3].y,
-                                zN ? B.rho : nN[0].y, zN ? B.ux : nN[1].y, zN ? B.uy : nN[2].y, zN ? B.th : nN[3].y,
-                                fb, ab[0], ab[1], ab[2]);
+                collide_cell<T, SIG>(cs, cen, B, A.rho, A.ux, A.uy, A.th, bEr, bEux, bEuy, bEth,
+                                     zS ? B.rho : nS[0].y, zS ? B.ux : nS[1].y, zS ? B.uy : nS[2].y, zS ? B.th : nS[3].y,
+                                     zN ? B.rho : nN[0].y, zN ? B.ux : nN[1].y, zN ? B.uy : nN[2].y, zN ? B.th : nN[3].y,
+                                     fb, ab[0], ab[1], ab[2]);
             }
             const long long o = (long long)r * pitch + gx2;
             if (v3a && v3b) {
@@ -722,6 +489,7 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
         for (int c = 0; c < 2; c++) cur[c] = nxt[c];
         {
             const int f = fs0; fs0 = fs1; fs1 = fs2; fs2 = f;
+            const int b = bs1; bs1 = bs2; bs2 = b;
             const int sx = ss0; ss0 = ss1; ss1 = ss2; ss2 = ss3; ss3 = ss4; ss4 = sx;
             const int n = ns0; ns0 = ns1; ns1 = ns2; ns2 = n;
         }

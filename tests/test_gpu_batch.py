@@ -44,6 +44,7 @@ def test_batch_equals_separate_runs_bitwise(hl, monkeypatch):
         view.init(*c.fields())
     b.step(37)  # two graph replays of 16 steps and 5 single steps
     got = [v.macros() for v in b.cases]
+    monkeypatch.setenv("HLBM_MARCH", "-1")  # the single-case runs use the batch's tiled kernel
     monkeypatch.setenv("HLBM_FP32_TMA", "-1")
     monkeypatch.setenv("HLBM_FP32_TILE", TILE_ENV[tile])
     for g, c in zip(got, cases):
@@ -78,6 +79,7 @@ def test_autotune_keeps_results_and_picks_a_tile(hl, monkeypatch):
     # differently, so the reference follows the same tiles)
     first = "0"
     for v, c in zip(b.cases, cases):
+        monkeypatch.setenv("HLBM_MARCH", "-1")
         monkeypatch.setenv("HLBM_FP32_TMA", "-1")
         monkeypatch.setenv("HLBM_FP32_TILE", first)
         s1 = hl.Solver(c.nx, c.ny, precision=1, **c.params())

@@ -1,10 +1,12 @@
-"""The row-marching fused kernels against the FP64 oracle: HLBM_MARCH=0-3
-(one column per thread, strips of 128, 96, 64, 224 columns) and 4-7 (two
-columns per thread, strips of 120, 184, 248, 312 columns).  The same
+"""The row-marching fused kernel (two columns per thread) against the FP64
+oracle in all its variants: HLBM_MARCH=0 (64 threads, <= 128 registers, the
+FP32 default), 1 (96 threads), 2 (128 threads), 3 (64 threads, no register
+cap), each instantiated for sigma = 0 / > 0 and both Phi forms.  The same
 tolerances as the tiled kernel (1e-10 FP64, 1e-4 FP32), every boundary set,
 grids that leave a ragged last strip (odd widths included, so that a pair
 straddles the edge), and row segments of 1, 3 and all rows (each segment
-refills its row rings from four rows above its first row)."""
+refills its row rings from four rows above its first row).  The 16-bit
+storage forms are checked on both the marching and the tiled kernel."""
 import numpy as np
 import pytest
 
@@ -32,7 +34,7 @@ def hl():
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("variant", range(4))
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 2, 2, 1)])
 def test_march_variants(hl, precision, variant, bc):
     case = inputs.random_smooth(173, 141, seed=31, amp=0.04, u0=(0.06, 0.01), theta0=0.2, mu=3e-3,
@@ -43,7 +45,7 @@ def test_march_variants(hl, precision, variant, bc):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("variant", [2, 4])
+@pytest.mark.parametrize("variant", [0, 2])
 @pytest.mark.parametrize("bc", BCS)
 def test_march_boundaries(hl, precision, variant, bc):
     case = inputs.random_smooth(53, 41, seed=21, amp=0.04, u0=(0.06, 0.01), theta0=0.2, mu=3e-3,
@@ -54,7 +56,7 @@ def test_march_boundaries(hl, precision, variant, bc):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("variant", [0, 5])
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("rows", [1, 3, 100000])
 @pytest.mark.parametrize("nx,ny", [(1, 1), (3, 5), (37, 23), (130, 67), (185, 9)])
 @pytest.mark.parametrize("sigma", [0.0, 0.7])
@@ -71,7 +73,7 @@ def test_march_phi_fd_and_ablations(hl, precision):
         case = inputs.random_smooth(70, 44, seed=8, amp=0.05, mu=2e-3, sigma=0.3)
         case.phi_mode = phi_mode
         case.ablation = ablation
-        for variant in (1, 6):
+        for variant in (0, 3):
             with _env(HLBM_MARCH=variant):
                 _, _, got, ref = run_pair(hl, case, precision, 10)
             compare(got, ref, case.gamma, TOL[precision])
@@ -83,7 +85,7 @@ def test_march_16bit_forms_within_their_bounds(hl):
     ora.init(*case.fields())
     ora.step(200)
     ref = ora.macros()
-    for prec, variant in ((2, 0), (3, 0), (2, 5), (3, 5)):
+    for prec, variant in ((2, 0), (3, 0), (2, -1), (3, -1)):
         with _env(HLBM_MARCH=variant):
             s = hl.Solver(case.nx, case.ny, precision=prec, **case.params())
         s.init(*case.fields())

@@ -271,7 +271,7 @@ def test_error_paths(hl):
     assert e.value.code == hl.HLBM_ERR_NONFINITE
 
 
-# ---- the plain tiled FP32 kernel (HLBM_FP32_TMA=-1) and the other TMA tiles ---------
+# ---- the tiled FP32 kernels (HLBM_MARCH=-1): plain tiles and the TMA tiles ---------------
 
 class _env:
     def __init__(self, **kv):
@@ -291,8 +291,8 @@ class _env:
                 os.environ[k] = v
 
 
-KERNELS = [dict(HLBM_FP32_TMA=-1, HLBM_FP32_TILE=t) for t in range(5)] + \
-          [dict(HLBM_FP32_TMA=k) for k in range(4)]
+KERNELS = [dict(HLBM_MARCH=-1, HLBM_FP32_TMA=-1, HLBM_FP32_TILE=t) for t in range(5)] + \
+          [dict(HLBM_MARCH=-1, HLBM_FP32_TMA=k) for k in range(4)]
 
 
 @pytest.mark.parametrize("kern", KERNELS, ids=lambda d: "-".join(f"{k[5:]}{v}" for k, v in d.items()))
