@@ -1,7 +1,8 @@
 """Build of libhlbm.so (the CUDA library behind include/hlbm.h) for sm_103a.
 
-One translation unit compiled in place with nvcc; the shared object lands
-next to this file and is loaded by ``paper_2002_03644_gb300.hlbm``.
+The translation units are compiled in parallel with nvcc into a private
+folder, then linked into one shared object next to this file, which
+``paper_2002_03644_gb300.hlbm`` loads.
 """
 from __future__ import annotations
 
@@ -38,13 +39,25 @@ def up_to_date() -> bool:
 def build_library(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-shared",
-           "-I", INCLUDE, "-o", tmp, *SOURCES]
+    tag = f"tmp{os.getpid()}"
+    objdir = os.path.join(PKG, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    common = [nvcc(), "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-I", INCLUDE]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+        common.insert(1, "-Xptxas=-v")
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + f".{tag}.o")
+        objs.append(obj)
+        procs.append(subprocess.Popen(common + ["-c", src, "-o", obj]))
+    codes = [p.wait() for p in procs]
+    if any(codes):
+        raise subprocess.CalledProcessError(max(codes, key=abs), "nvcc")
+    tmp = LIB + f".{tag}"
+    subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
+    for o in objs:
+        os.remove(o)
     return LIB
 
 

@@ -159,6 +159,30 @@ __device__ __forceinline__ int locate(int gx, int gy, const KParams &kp, int pit
     return gy * pitch + gx;
 }
 
+// ---- FP32 hardware approximations ------------------------------------------
+// The PTX approximate reciprocal, base-2 logarithm and base-2 exponential
+// (relative error of a few ulp, denormals flushed).  The state never holds
+// denormal or huge values, so the range handling of the library functions
+// is not needed; the FP32 parity bound (1e-4) is far above these errors.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ---- precision-dependent helpers -------------------------------------------
 template <typename T> struct Consts;
 
@@ -171,7 +195,7 @@ template <> struct Consts<float> {
         sigma = kp.f_sigma; one_m_sigma = kp.f_one_m_sigma; two_m_gamma = kp.f_two_m_gamma;
     }
     // theta = rho^(gamma-1) exp(s / c_v) = 2^((gamma-1) log2 rho + s / (c_v ln 2))
-    __device__ __forceinline__ float theta(float rho, float s) const { return exp2f(fmaf(gm1, __log2f(rho), s * s2exp)); }
+    __device__ __forceinline__ float theta(float rho, float s) const { return ex2_approx(fmaf(gm1, lg2_approx(rho), s * s2exp)); }
 };
 
 template <> struct Consts<double> {
@@ -265,9 +289,9 @@ __device__ __forceinline__ int classify_r1(int gx, int gy, const KParams &kp, in
     return (cx || cy) ? 2 : 0;
 }
 
-// Division and reciprocal: the hardware approximation in FP32 (about 2 ulp,
-// well inside the FP32 parity bound), IEEE division in FP64.
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+// Division: a times the approximate reciprocal in FP32 (about 2 ulp, well
+// inside the FP32 parity bound), IEEE division in FP64.
+__device__ __forceinline__ float fdiv(float a, float b) { return a * rcp_approx(b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
 // Van Albada limited slope from the two one-sided differences; zero at an
