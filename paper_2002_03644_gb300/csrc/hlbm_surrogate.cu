@@ -55,6 +55,27 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// B fragments of two n tiles (x4) or one (x2) from shared memory.
+__device__ __forceinline__ void ldsm_x4(uint32_t b[4], const void *p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t b[2], const void *p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(b[0]), "=r"(b[1]) : "r"(a));
+}
+
+constexpr int CONV_THREADS = 256;  // 8 warps x 32 pixels = 256 pixels per tile
+
+template <int CIN, int NOUT>
+struct ConvGeom {
+    static constexpr int LDB = CIN + 8;  // padded weight row (elements): conflict-free ldmatrix
+    static constexpr size_t smem_bytes = (size_t)9 * NOUT * LDB * sizeof(__nv_bfloat16);
+};
+
 // in  [npix][CIN]  (NHWC, pixels n*H*W + i*W + j), CIN multiple of 16
 // B   [9][NOUT][CIN] BF16, NOUT multiple of 8 and <= 64
 // bias[nbias] FP32 added to the first nbias outputs (bias may be NULL)
@@ -63,84 +84,120 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const 
 // mode 2 (input gradient): g = z * GELU'(zprev) (or z when zprev is NULL);
 //         z_f32 = g, out_bf16 = g
 // flip: use offset -(p, q) for tap (p, q) (input gradient)
+// A persistent CTA stages all nine taps' weights in shared memory once
+// (rows padded by 8 elements so that the 8 rows an ldmatrix reads fall in
+// different banks), then walks 256-pixel tiles; each warp computes 32
+// pixels (two m16 tiles) x NOUT outputs, so every weight fragment feeds two
+// MMAs.  A fragments are read from global memory (L1-resident neighbours).
 template <int CIN, int NOUT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(CONV_THREADS, 2)
 conv_mma_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ B,
                 const float *__restrict__ bias, int nbias, __nv_bfloat16 *__restrict__ out_bf,
                 float *__restrict__ z_f32, const float *__restrict__ zprev, int npix, int H, int W, int mode, int flip)
 {
     constexpr int NT = NOUT / 8;  // n tiles of 8
+    constexpr int LDB = ConvGeom<CIN, NOUT>::LDB;
+    constexpr int CH = CIN / 8;   // 16-byte chunks per weight row
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    __nv_bfloat16 *Bs = reinterpret_cast<__nv_bfloat16 *>(conv_smem);  // [9][NOUT][LDB]
+    for (int e = threadIdx.x; e < 9 * NOUT * CH; e += CONV_THREADS) {
+        const int row = e / CH, c = e - row * CH;
+        *reinterpret_cast<uint4 *>(Bs + row * LDB + c * 8) =
+            *reinterpret_cast<const uint4 *>(B + (size_t)row * CIN + c * 8);
+    }
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t4 = lane & 3;
-    const int pix0 = (blockIdx.x * 4 + warp) * 16;
-    if (pix0 >= npix) return;
+    // ldmatrix row address of this lane: matrix j = lane / 8 (n tile j / 2,
+    // k half j % 2), row lane % 8
+    const int lj = lane >> 3, lr = lane & 7;
     const int HW = H * W;
-    // the two pixel rows of this thread's A fragment
-    int pr[2];
-    pr[0] = pix0 + g;
-    pr[1] = pix0 + g + 8;
-    int pn[2], pi[2], pj[2];
+    const int ntiles = (npix + CONV_THREADS - 1) / CONV_THREADS;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int pix0 = tile * CONV_THREADS + warp * 32;
+        if (pix0 >= npix) continue;
+        // pixel rows of this lane's A fragments: q = 2 mt + h -> pix0 + 16 mt + 8 h + g
+        int pn[4], pi[4], pj[4];
 #pragma unroll
-    for (int r = 0; r < 2; r++) {
-        const int pp = pr[r] < npix ? pr[r] : npix - 1;
-        pn[r] = pp / HW;
-        const int rem = pp - pn[r] * HW;
-        pi[r] = rem / W;
-        pj[r] = rem - pi[r] * W;
-    }
-    float acc[NT][4];
+        for (int q = 0; q < 4; q++) {
+            const int p = pix0 + 16 * (q >> 1) + 8 * (q & 1) + g;
+            const int pp = p < npix ? p : npix - 1;
+            pn[q] = pp / HW;
+            const int rem = pp - pn[q] * HW;
+            pi[q] = rem / W;
+            pj[q] = rem - pi[q] * W;
+        }
+        float acc[2][NT][4];
 #pragma unroll
-    for (int n = 0; n < NT; n++)
+        for (int m = 0; m < 2; m++)
 #pragma unroll
-        for (int k = 0; k < 4; k++) acc[n][k] = 0.0f;
+            for (int n = 0; n < NT; n++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) acc[m][n][k] = 0.0f;
 
 #pragma unroll 1
-    for (int tap = 0; tap < 9; tap++) {
-        int dp = tap / 3 - 1, dq = tap % 3 - 1;
-        if (flip) { dp = -dp; dq = -dq; }
-        const __nv_bfloat16 *row[2];
+        for (int tap = 0; tap < 9; tap++) {
+            int dp = tap / 3 - 1, dq = tap % 3 - 1;
+            if (flip) { dp = -dp; dq = -dq; }
+            const __nv_bfloat16 *row[4];
 #pragma unroll
-        for (int r = 0; r < 2; r++) {
-            const int ii = wrap(pi[r] + dp, H), jj = wrap(pj[r] + dq, W);
-            row[r] = in + ((size_t)pn[r] * HW + (size_t)ii * W + jj) * CIN;
-        }
-        const __nv_bfloat16 *Bt = B + (size_t)tap * NOUT * CIN;
+            for (int q = 0; q < 4; q++) {
+                const int ii = wrap(pi[q] + dp, H), jj = wrap(pj[q] + dq, W);
+                row[q] = in + ((size_t)pn[q] * HW + (size_t)ii * W + jj) * CIN;
+            }
+            const __nv_bfloat16 *Bt = Bs + tap * NOUT * LDB;
 #pragma unroll
-        for (int k0 = 0; k0 < CIN; k0 += 16) {
-            uint32_t a[4];
-            a[0] = ld_pair(row[0] + k0 + 2 * t4);
-            a[1] = ld_pair(row[1] + k0 + 2 * t4);
-            a[2] = ld_pair(row[0] + k0 + 8 + 2 * t4);
-            a[3] = ld_pair(row[1] + k0 + 8 + 2 * t4);
+            for (int k0 = 0; k0 < CIN; k0 += 16) {
+                uint32_t a[2][4];
 #pragma unroll
-            for (int n = 0; n < NT; n++) {
-                const __nv_bfloat16 *bn = Bt + (size_t)(n * 8 + g) * CIN + k0;
-                uint32_t b[2];
-                b[0] = ld_pair(bn + 2 * t4);
-                b[1] = ld_pair(bn + 8 + 2 * t4);
-                mma_bf16(acc[n], a, b);
+                for (int m = 0; m < 2; m++) {
+                    a[m][0] = ld_pair(row[2 * m] + k0 + 2 * t4);
+                    a[m][1] = ld_pair(row[2 * m + 1] + k0 + 2 * t4);
+                    a[m][2] = ld_pair(row[2 * m] + k0 + 8 + 2 * t4);
+                    a[m][3] = ld_pair(row[2 * m + 1] + k0 + 8 + 2 * t4);
+                }
+#pragma unroll
+                for (int n = 0; n < NT; n += 2) {
+                    if (n + 1 < NT) {
+                        uint32_t b[4];
+                        ldsm_x4(b, Bt + (n * 8 + (lj >> 1) * 8 + lr) * LDB + k0 + (lj & 1) * 8);
+#pragma unroll
+                        for (int m = 0; m < 2; m++) {
+                            mma_bf16(acc[m][n], a[m], b);
+                            mma_bf16(acc[m][n + 1], a[m], b + 2);
+                        }
+                    } else {
+                        uint32_t b[2];
+                        ldsm_x2(b, Bt + (n * 8 + lr) * LDB + k0 + (lj & 1) * 8);
+#pragma unroll
+                        for (int m = 0; m < 2; m++) mma_bf16(acc[m][n], a[m], b);
+                    }
+                }
             }
         }
-    }
-    // epilogue: C fragment rows g, g+8; columns 2 t4, 2 t4 + 1 of each n tile
+        // epilogue: C fragment rows g, g+8 of each m tile; columns 2 t4, 2 t4 + 1 of each n tile
 #pragma unroll
-    for (int r = 0; r < 2; r++) {
-        const int p = pix0 + g + 8 * r;
-        if (p >= npix) continue;
+        for (int m = 0; m < 2; m++) {
 #pragma unroll
-        for (int n = 0; n < NT; n++) {
+            for (int r = 0; r < 2; r++) {
+                const int p = pix0 + 16 * m + g + 8 * r;
+                if (p >= npix) continue;
 #pragma unroll
-            for (int e = 0; e < 2; e++) {
-                const int col = n * 8 + 2 * t4 + e;
-                float z = acc[n][2 * r + e] + ((bias && col < nbias) ? bias[col] : 0.0f);
-                const size_t idx = (size_t)p * NOUT + col;
-                if (mode == 2) {
-                    if (zprev) z *= gelu_grad_f(zprev[idx]);
-                    out_bf[idx] = __float2bfloat16_rn(z);
-                    if (z_f32) z_f32[idx] = z;
-                } else {
-                    if (z_f32) z_f32[idx] = z;
-                    out_bf[idx] = __float2bfloat16_rn(mode == 1 ? gelu_f(z) : z);
+                for (int n = 0; n < NT; n++) {
+#pragma unroll
+                    for (int e = 0; e < 2; e++) {
+                        const int col = n * 8 + 2 * t4 + e;
+                        float z = acc[m][n][2 * r + e] + ((bias && col < nbias) ? bias[col] : 0.0f);
+                        const size_t idx = (size_t)p * NOUT + col;
+                        if (mode == 2) {
+                            if (zprev) z *= gelu_grad_f(zprev[idx]);
+                            out_bf[idx] = __float2bfloat16_rn(z);
+                            if (z_f32) z_f32[idx] = z;
+                        } else {
+                            if (z_f32) z_f32[idx] = z;
+                            out_bf[idx] = __float2bfloat16_rn(mode == 1 ? gelu_f(z) : z);
+                        }
+                    }
                 }
             }
         }
@@ -301,12 +358,26 @@ struct ConvArgs {
     int npix, H, W, mode, flip;
 };
 
+// Persistent grid: two CTAs per SM (the weights of a 64 x 64 layer take
+// 81 KB of shared memory), at most one CTA per 256-pixel tile.
 template <int CIN, int NOUT>
 cudaError_t launch_conv_t(const ConvArgs &a, cudaStream_t st)
 {
-    const int blocks = (a.npix + 63) / 64;
-    conv_mma_kernel<CIN, NOUT><<<blocks, 128, 0, st>>>(a.in, a.B, a.bias, a.nbias, a.out, a.z, a.zprev, a.npix, a.H,
-                                                       a.W, a.mode, a.flip);
+    using G = ConvGeom<CIN, NOUT>;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv_mma_kernel<CIN, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)G::smem_bytes);
+        if (e != cudaSuccess) { sms = 0; return e; }
+    }
+    const int tiles = (a.npix + CONV_THREADS - 1) / CONV_THREADS;
+    const int blocks = tiles < 2 * sms ? tiles : 2 * sms;
+    conv_mma_kernel<CIN, NOUT><<<blocks, CONV_THREADS, G::smem_bytes, st>>>(a.in, a.B, a.bias, a.nbias, a.out, a.z,
+                                                                          a.zprev, a.npix, a.H, a.W, a.mode, a.flip);
     return cudaGetLastError();
 }
 
