@@ -194,12 +194,17 @@ int hlbm_batch_case(hlbm_batch *b, int index, hlbm_handle **h);
  * the same ping-pong parity, which batch-only stepping guarantees). */
 int hlbm_batch_step(hlbm_batch *b, int64_t n);
 
-/* Time every compiled tile shape on the current states (restored afterwards)
+/* Time every compiled work shape on the current states (restored afterwards)
  * and keep the fastest; *tile receives its index (may be NULL).  The choice
- * holds until the next call. */
+ * holds until the next call.  Indices 0-4 are tiles of the tiled kernel
+ * (32x16, 64x16, 32x8, 64x32, 32x32); 5 and 6 are the row-marching kernel
+ * (strips of 120 columns, row segments of 16 and 32), tried only when all
+ * cases share one sigma > 0 / sigma = 0 and one phi_mode. */
 int hlbm_batch_autotune(hlbm_batch *b, int *tile);
 
-/* Tile shape index in use and its dimensions. */
+/* Work shape index in use and its dimensions: tile width and height and
+ * threads per CTA, or strip width, segment height and threads for the
+ * marching shapes. */
 int hlbm_batch_tile(const hlbm_batch *b, int *index, int *tx, int *ty, int *threads);
 
 void hlbm_batch_destroy(hlbm_batch *b);

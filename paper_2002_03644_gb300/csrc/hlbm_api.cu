@@ -241,6 +241,7 @@ static cudaError_t launch_tma(hlbm_handle *h)
 constexpr int kNumMarch = 4;
 constexpr int kMarchMinRows = 8;
 constexpr int kMarchMaxRows = 32;
+constexpr long long kMarchMinCells = 768ll * 768ll;  // GB300 sweep: tiled faster up to 768^2, marching at 1024^2
 
 // Paired-column marching kernel with NT threads (strips of 2 (NT - 4)
 // columns), register budget set by MINB resident CTAs per SM; the
@@ -321,9 +322,13 @@ static cudaError_t march_dispatch(hlbm_handle *h)
 
 static cudaError_t setup_march(hlbm_handle *h)
 {
-    // FP32 and the 16-bit storage forms march by default; FP64 uses the
-    // tiled kernel.  HLBM_MARCH=<k> picks a variant, -1 the tiled / TMA kernels.
-    h->march_variant = env_choice("HLBM_MARCH", h->p.precision == HLBM_FP64 ? -1 : 0, -1, kNumMarch);
+    // FP32 and the 16-bit storage forms march by default on grids of more
+    // than kMarchMinCells cells (below that a grid has too few strips and
+    // segments to fill the GPU, and the tiled kernel is faster); FP64 uses
+    // the tiled kernel.  HLBM_MARCH=<k> picks a variant, -1 the tiled / TMA
+    // kernels.
+    const bool big = (long long)h->p.nx * h->p.ny > kMarchMinCells;
+    h->march_variant = env_choice("HLBM_MARCH", (h->p.precision != HLBM_FP64 && big) ? 0 : -1, -1, kNumMarch);
     if (h->march_variant < 0) return cudaSuccess;
     return with_types(h, [&](auto ty) {
         using T = typename decltype(ty)::t;
@@ -779,6 +784,12 @@ struct TileShape {
 };
 constexpr TileShape kBatchTiles[] = {{32, 16, 256}, {64, 16, 256}, {32, 8, 128}, {64, 32, 512}, {32, 32, 512}};
 constexpr int kNumBatchTiles = 5;
+// Kinds 5 and 6: the row-marching kernel (64 threads, strips of 120
+// columns) with segments of 16 and 32 rows.  They need one sigma > 0 / Phi
+// choice for all cases (the kernel is specialised on both).
+constexpr int kBatchMarchRows[] = {16, 32};
+constexpr int kNumBatchKinds = kNumBatchTiles + 2;
+constexpr int kBatchMarchNT = 64, kBatchMarchMinB = 8;
 constexpr int kGraphSteps = 16;  // steps per captured graph (even: parity returns)
 
 }  // namespace
@@ -794,6 +805,9 @@ struct hlbm_batch {
     CasePlanes *d_planes = nullptr;
     int *d_tile_case = nullptr, *d_tile_first = nullptr;
     int ntiles = 0;
+    MarchItem *d_items = nullptr;  // marching kinds: (case, strip, segment) list
+    int nitems = 0;
+    bool march_ok = false, sig = false, phi0 = true;
     int grid = 0;
     size_t smem = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // starting parity 0 / 1
@@ -809,8 +823,29 @@ static cudaError_t batch_launch(hlbm_batch *b, int parity)
     return cudaGetLastError();
 }
 
+template <bool SIG, bool PHI0>
+static cudaError_t batch_march_launch(hlbm_batch *b, int parity)
+{
+    MarchTables tab;
+    tab.kps = b->d_kps; tab.planes = b->d_planes; tab.items = b->d_items; tab.nitems = b->nitems;
+    batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, SIG, PHI0><<<b->grid, kBatchMarchNT, b->smem, b->stream>>>(tab, parity);
+    return cudaGetLastError();
+}
+
+static const void *batch_march_fn(const hlbm_batch *b)
+{
+    if (b->sig) return b->phi0 ? (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, true, true>
+                               : (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, true, false>;
+    return b->phi0 ? (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, false, true>
+                   : (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, false, false>;
+}
+
 static cudaError_t batch_launch_any(hlbm_batch *b, int parity)
 {
+    if (b->tile >= kNumBatchTiles) {
+        if (b->sig) return b->phi0 ? batch_march_launch<true, true>(b, parity) : batch_march_launch<true, false>(b, parity);
+        return b->phi0 ? batch_march_launch<false, true>(b, parity) : batch_march_launch<false, false>(b, parity);
+    }
     switch (b->tile) {
     case 1: return batch_launch<64, 16, 256>(b, parity);
     case 2: return batch_launch<32, 8, 128>(b, parity);
@@ -843,9 +878,11 @@ static void batch_drop_graphs(hlbm_batch *b)
 static int batch_tables(hlbm_batch *b)
 {
     batch_drop_graphs(b);
-    const TileShape ts = kBatchTiles[b->tile];
+    const bool march = b->tile >= kNumBatchTiles;
+    const TileShape ts = kBatchTiles[march ? 0 : b->tile];
     const int nc = (int)b->cases.size();
     std::vector<int> tile_case, tile_first(nc);
+    std::vector<MarchItem> items;
     std::vector<KParams> kps(nc);
     std::vector<CasePlanes> planes(nc);
     for (int c = 0; c < nc; c++) {
@@ -853,6 +890,14 @@ static int batch_tables(hlbm_batch *b)
         tile_first[c] = (int)tile_case.size();
         const int nt = ((h->p.nx + ts.tx - 1) / ts.tx) * ((h->p.ny + ts.ty - 1) / ts.ty);
         tile_case.insert(tile_case.end(), nt, c);
+        if (march) {
+            // the segmentation of the single-case kernel with HLBM_MARCH_ROWS = rows
+            const int W = PairGeom<float, kBatchMarchNT>::W, rows = kBatchMarchRows[b->tile - kNumBatchTiles];
+            const int nseg = (h->p.ny + rows - 1) / rows;
+            for (int k = 0; k < nseg; k++)
+                for (int x0 = 0; x0 < h->p.nx; x0 += W)
+                    items.push_back({c, x0, (int)((long long)k * h->p.ny / nseg), (int)((long long)(k + 1) * h->p.ny / nseg)});
+        }
         kps[c] = h->kp;
         for (int q = 0; q < 2; q++) {
             planes[c].inF[q] = pop_planes<float, FullStore<float>>(h, q);
@@ -862,8 +907,12 @@ static int batch_tables(hlbm_batch *b)
         }
     }
     b->ntiles = (int)tile_case.size();
-    cudaFree(b->d_kps); cudaFree(b->d_planes); cudaFree(b->d_tile_case); cudaFree(b->d_tile_first);
-    b->d_kps = nullptr; b->d_planes = nullptr; b->d_tile_case = nullptr; b->d_tile_first = nullptr;
+    b->nitems = (int)items.size();
+    cudaFree(b->d_kps); cudaFree(b->d_planes); cudaFree(b->d_tile_case); cudaFree(b->d_tile_first); cudaFree(b->d_items);
+    b->d_kps = nullptr; b->d_planes = nullptr; b->d_tile_case = nullptr; b->d_tile_first = nullptr; b->d_items = nullptr;
+    if (march && (cudaMalloc(&b->d_items, b->nitems * sizeof(MarchItem)) != cudaSuccess ||
+                  cudaMemcpy(b->d_items, items.data(), b->nitems * sizeof(MarchItem), cudaMemcpyHostToDevice) != cudaSuccess))
+        return HLBM_ERR_NOMEM;
     if (cudaMalloc(&b->d_kps, nc * sizeof(KParams)) != cudaSuccess ||
         cudaMalloc(&b->d_planes, nc * sizeof(CasePlanes)) != cudaSuccess ||
         cudaMalloc(&b->d_tile_case, b->ntiles * sizeof(int)) != cudaSuccess ||
@@ -876,6 +925,17 @@ static int batch_tables(hlbm_batch *b)
         return HLBM_ERR_CUDA;
     int per_sm = 0, sms = 0;
     cudaError_t e;
+    if (march) {
+        b->smem = (PairGeom<float, kBatchMarchNT>::smem_bytes + 15) / 16 * 16 + sizeof(KParams);
+        const void *fn = batch_march_fn(b);
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchMarchNT, b->smem);
+        if (e != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+            return HLBM_ERR_CUDA;
+        const int g = (per_sm > 0 ? per_sm : 1) * sms;
+        b->grid = g < b->nitems ? g : b->nitems;
+        return HLBM_OK;
+    }
     switch (b->tile) {
     case 1: e = batch_kernel_setup<64, 16, 256>(b, &per_sm); break;
     case 2: e = batch_kernel_setup<32, 8, 128>(b, &per_sm); break;
@@ -941,7 +1001,7 @@ void hlbm_batch_destroy(hlbm_batch *b)
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop_graphs(b);
-    cudaFree(b->d_kps); cudaFree(b->d_planes); cudaFree(b->d_tile_case); cudaFree(b->d_tile_first);
+    cudaFree(b->d_kps); cudaFree(b->d_planes); cudaFree(b->d_tile_case); cudaFree(b->d_tile_first); cudaFree(b->d_items);
     for (hlbm_handle *h : b->cases) hlbm_destroy(h);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -968,6 +1028,14 @@ int hlbm_batch_create(const hlbm_params *params, int ncase, void *stream, hlbm_b
         if (r != HLBM_OK) { hlbm_batch_destroy(b); return r; }
         b->cases.push_back(h);
     }
+    b->sig = b->cases[0]->kp.sigma_nonzero != 0;
+    b->phi0 = b->cases[0]->kp.phi_mode == 0;
+    b->march_ok = true;
+    for (hlbm_handle *h : b->cases)
+        if ((h->kp.sigma_nonzero != 0) != b->sig || (h->kp.phi_mode == 0) != b->phi0) b->march_ok = false;
+    // starting shape (HLBM_BATCH_TILE=<k> for tests and sweeps; autotune may change it)
+    b->tile = env_choice("HLBM_BATCH_TILE", 0, 0, kNumBatchKinds);
+    if (b->tile >= kNumBatchTiles && !b->march_ok) b->tile = 0;
     const int r = batch_tables(b);
     if (r != HLBM_OK) { hlbm_batch_destroy(b); return r; }
     *out = b;
@@ -991,10 +1059,11 @@ int hlbm_batch_step(hlbm_batch *b, int64_t n)
 int hlbm_batch_tile(const hlbm_batch *b, int *index, int *tx, int *ty, int *threads)
 {
     if (!b) return HLBM_ERR_ARG;
+    const bool march = b->tile >= kNumBatchTiles;
     if (index) *index = b->tile;
-    if (tx) *tx = kBatchTiles[b->tile].tx;
-    if (ty) *ty = kBatchTiles[b->tile].ty;
-    if (threads) *threads = kBatchTiles[b->tile].nt;
+    if (tx) *tx = march ? PairGeom<float, kBatchMarchNT>::W : kBatchTiles[b->tile].tx;
+    if (ty) *ty = march ? kBatchMarchRows[b->tile - kNumBatchTiles] : kBatchTiles[b->tile].ty;
+    if (threads) *threads = march ? kBatchMarchNT : kBatchTiles[b->tile].nt;
     return HLBM_OK;
 }
 
@@ -1022,7 +1091,8 @@ int hlbm_batch_autotune(hlbm_batch *b, int *tile)
     int best_tile = b->tile;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (rc == HLBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = HLBM_ERR_CUDA;
-    for (int t = 0; t < kNumBatchTiles && rc == HLBM_OK; t++) {
+    for (int t = 0; t < kNumBatchKinds && rc == HLBM_OK; t++) {
+        if (t >= kNumBatchTiles && !b->march_ok) break;
         b->tile = t;
         rc = batch_tables(b);
         if (rc != HLBM_OK) break;

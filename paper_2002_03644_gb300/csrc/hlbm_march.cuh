@@ -176,16 +176,19 @@ struct PairGeom {
     static constexpr size_t smem_bytes = sizeof(T) * (size_t)N;
 };
 
-template <typename T, typename S, int NT, int MINB, bool SIG, bool PHI0>
-__global__ void __launch_bounds__(NT, MINB)
-march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
-                  typename S::raw *__restrict__ outF, T *__restrict__ outA, const KParams kp, const int nseg)
+// One strip (columns x0 .. x0+W-1) and one row segment [ys, ye) of one
+// case; all NT threads of the CTA take part (the caller separates
+// consecutive segments with a barrier).
+template <typename T, typename S, int NT, bool SIG, bool PHI0>
+__device__ __forceinline__ void march_pair_segment(const typename S::raw *__restrict__ inF,
+                                                   const T *__restrict__ inA, typename S::raw *__restrict__ outF,
+                                                   T *__restrict__ outA, const KParams &kp, const int x0,
+                                                   const int ys, const int ye, unsigned char *smem_raw)
 {
     using G = PairGeom<T, NT>;
     using V = typename Vec2<T>::type;
     using raw = typename S::raw;
     using raw2 = typename S::raw2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *const sm = reinterpret_cast<T *>(smem_raw);
     V *const gA = reinterpret_cast<V *>(sm + G::OFF_GA);  // [3][NT] pairs
     V *const gB = reinterpret_cast<V *>(sm + G::OFF_GB);  // [2][3][NT]
@@ -201,8 +204,6 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
     const long long P = kp.plane;
     const int pitch = kp.pitch;
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * G::W;
-    const int ys = seg_start(blockIdx.y, nseg, kp.ny), ye = seg_start(blockIdx.y + 1, nseg, kp.ny);
     const int base = ys - 4;
 
     // load-phase pair t: columns gxL, gxL + 1
@@ -493,6 +494,58 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
             const int sx = ss0; ss0 = ss1; ss1 = ss2; ss2 = ss3; ss3 = ss4; ss4 = sx;
             const int n = ns0; ns0 = ns1; ns1 = ns2; ns2 = n;
         }
+    }
+}
+
+// One case: blockIdx.x picks the strip, blockIdx.y the row segment.
+template <typename T, typename S, int NT, int MINB, bool SIG, bool PHI0>
+__global__ void __launch_bounds__(NT, MINB)
+march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
+                  typename S::raw *__restrict__ outF, T *__restrict__ outA, const KParams kp, const int nseg)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ys = seg_start(blockIdx.y, nseg, kp.ny), ye = seg_start(blockIdx.y + 1, nseg, kp.ny);
+    march_pair_segment<T, S, NT, SIG, PHI0>(inF, inA, outF, outA, kp, blockIdx.x * PairGeom<T, NT>::W, ys, ye,
+                                            smem_raw);
+}
+
+// ---- many cases in one persistent launch (FP32) ---------------------------------
+// The (case, strip, segment) items of all cases form one list that a grid
+// of resident CTAs walks; the parameters of an item's case are copied to
+// shared memory behind the rings.
+struct MarchItem {
+    int c, x0, ys, ye;
+};
+
+struct MarchTables {
+    const KParams *kps;        // [ncase]
+    const CasePlanes *planes;  // [ncase]
+    const MarchItem *items;    // [nitems]
+    int nitems;
+};
+
+template <int NT, int MINB, bool SIG, bool PHI0>
+__global__ void __launch_bounds__(NT, MINB)
+batched_march_kernel(const MarchTables tab, const int parity)
+{
+    using G = PairGeom<float, NT>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    KParams &skp = *reinterpret_cast<KParams *>(smem_raw + (G::smem_bytes + 15) / 16 * 16);
+    int loaded = -1;
+    for (int i = blockIdx.x; i < tab.nitems; i += gridDim.x) {
+        const MarchItem it = tab.items[i];
+        __syncthreads();  // the previous segment is done with the rings and the parameters
+        if (it.c != loaded) {
+            const int *src = reinterpret_cast<const int *>(tab.kps + it.c);
+            int *dst = reinterpret_cast<int *>(&skp);
+            for (int w = threadIdx.x; w < (int)(sizeof(KParams) / sizeof(int)); w += NT) dst[w] = __ldg(src + w);
+            loaded = it.c;
+            __syncthreads();
+        }
+        const CasePlanes &pl = tab.planes[it.c];
+        march_pair_segment<float, FullStore<float>, NT, SIG, PHI0>(pl.inF[parity], pl.inA[parity], pl.outF[parity],
+                                                                  pl.outA[parity], skp, it.x0, it.ys, it.ye,
+                                                                  smem_raw);
     }
 }
 

@@ -1,7 +1,11 @@
 """Batched form: many FP32 cases of uneven size and parameters advanced by one
-persistent launch per step (replayed from a CUDA graph).  Each case must come
-out bitwise equal to the same case stepped alone with the plain tiled kernel
-of the same tile shape (the per-tile arithmetic is the same code)."""
+persistent launch per step (replayed from a CUDA graph).  Each case is
+compared with the same case stepped alone by the single-case kernel of the
+same work shape: a tile of the tiled kernel (kinds 0-4) must agree bitwise;
+the row-marching kernel with the same segment height (kinds 5, 6) runs the
+same per-segment source, but inlined into a different kernel the compiler
+may fuse a different set of multiply-adds, so it must agree to 1e-5 of each
+field's scale (ten times inside the FP32 parity bound)."""
 import numpy as np
 import pytest
 
@@ -9,7 +13,23 @@ from paper_2002_03644_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TILE_ENV = {0: "0", 1: "1", 2: "2", 3: "3", 4: "4"}  # batch tile index -> plain tile variant
+# batch work shape -> environment of the single-case kernel that computes the same way
+KIND_ENV = {k: dict(HLBM_MARCH="-1", HLBM_FP32_TMA="-1", HLBM_FP32_TILE=str(k)) for k in range(5)}
+KIND_ENV[5] = dict(HLBM_MARCH="0", HLBM_MARCH_ROWS="16")
+KIND_ENV[6] = dict(HLBM_MARCH="0", HLBM_MARCH_ROWS="32")
+
+
+def close(g, m, k):
+    """|g - m| within 1e-5 of the field's scale (a1, a stress: of max p)."""
+    scale = (m["rho"] * m["theta"] / 3.0).max() if k == "a1" else max(np.abs(m[k]).max(), 1e-30)
+    return np.abs(g[k] - m[k]).max() <= 1e-5 * scale
+
+
+def set_kind_env(monkeypatch, kind):
+    for k in ("HLBM_MARCH", "HLBM_FP32_TMA", "HLBM_FP32_TILE", "HLBM_MARCH_ROWS"):
+        monkeypatch.delenv(k, raising=False)
+    for k, v in KIND_ENV[kind].items():
+        monkeypatch.setenv(k, v)
 
 
 @pytest.fixture(scope="module")
@@ -35,25 +55,29 @@ def make_cases():
     return cases
 
 
-def test_batch_equals_separate_runs_bitwise(hl, monkeypatch):
+@pytest.mark.parametrize("kind", [0, 5, 6])
+def test_batch_equals_separate_runs_bitwise(hl, monkeypatch, kind):
     cases = make_cases()
     spec = [dict(nx=c.nx, ny=c.ny, precision=1, **c.params()) for c in cases]
+    monkeypatch.setenv("HLBM_BATCH_TILE", str(kind))
     b = hl.Batch(spec)
     tile = b.tile()[0]
+    assert tile == kind
     for view, c in zip(b.cases, cases):
         view.init(*c.fields())
     b.step(37)  # two graph replays of 16 steps and 5 single steps
     got = [v.macros() for v in b.cases]
-    monkeypatch.setenv("HLBM_MARCH", "-1")  # the single-case runs use the batch's tiled kernel
-    monkeypatch.setenv("HLBM_FP32_TMA", "-1")
-    monkeypatch.setenv("HLBM_FP32_TILE", TILE_ENV[tile])
+    set_kind_env(monkeypatch, tile)
     for g, c in zip(got, cases):
         s = hl.Solver(c.nx, c.ny, precision=1, **c.params())
         s.init(*c.fields())
         s.step(37)
         m = s.macros()
         for k in m:
-            assert np.array_equal(g[k], m[k]), (c.name, c.nx, k)
+            if kind < 5:
+                assert np.array_equal(g[k], m[k]), (c.name, c.nx, k)
+            else:
+                assert close(g, m, k), (c.name, c.nx, k)
     for v in b.cases:
         assert v.step_count == 37
     b.close()
@@ -68,7 +92,7 @@ def test_autotune_keeps_results_and_picks_a_tile(hl, monkeypatch):
     b.step(3)
     before = [v.macros() for v in b.cases]
     t = b.autotune()
-    assert 0 <= t < 5 and b.tile()[0] == t
+    assert 0 <= t < 7 and b.tile()[0] == t
     after = [v.macros() for v in b.cases]
     for x, y in zip(before, after):
         for k in x:
@@ -77,22 +101,23 @@ def test_autotune_keeps_results_and_picks_a_tile(hl, monkeypatch):
     # the same history case by case: 3 steps with the batch's first tile,
     # then 20 with the tuned one (different tile instantiations may round
     # differently, so the reference follows the same tiles)
-    first = "0"
+    first = 0
     for v, c in zip(b.cases, cases):
-        monkeypatch.setenv("HLBM_MARCH", "-1")
-        monkeypatch.setenv("HLBM_FP32_TMA", "-1")
-        monkeypatch.setenv("HLBM_FP32_TILE", first)
+        set_kind_env(monkeypatch, first)
         s1 = hl.Solver(c.nx, c.ny, precision=1, **c.params())
         s1.init(*c.fields())
         s1.step(3)
         blob = s1.state()
-        monkeypatch.setenv("HLBM_FP32_TILE", TILE_ENV[t])
+        set_kind_env(monkeypatch, t)
         s2 = hl.Solver(c.nx, c.ny, precision=1, **c.params())
         s2.set_state(blob)
         s2.step(20)
         m, g = s2.macros(), v.macros()
         for k in m:
-            assert np.array_equal(g[k], m[k]), k
+            if t < 5:
+                assert np.array_equal(g[k], m[k]), k
+            else:
+                assert close(g, m, k), k
     b.close()
 
 
