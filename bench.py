@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # 9 populations + s + 3 a1 read and written once per cell-update
-BYTES_PER_CELL = {"fp32": 104, "fp64": 208, "fp16pop": 68, "bf16pop": 68}
+BYTES_PER_CELL = {"fp32": 104, "fp64": 208, "fp16pop": 68, "bf16pop": 68, "moments": 56}
 METRIC, UNIT = "MLUPS", "MLUPS"
 
 
@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16pop", "bf16pop"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16pop", "bf16pop", "moments"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--e2e-inner", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -187,6 +187,8 @@ def kernel_name(precision, cells, sigma=0.0, phi_mode=0):
     768^2 cells unless HLBM_MARCH=-1 (then the tiled kernels, chosen by
     HLBM_FP32_TMA / HLBM_FP32_TILE), the tiled kernel for FP64 and small
     grids unless HLBM_MARCH selects a marching variant."""
+    if precision == "moments":
+        return "march_moment_kernel<64,8,%s,%s>" % (str(sigma > 0).lower(), str(phi_mode == 0).lower())
     march = int(os.environ.get("HLBM_MARCH", "-1" if precision == "fp64" or cells <= 768 * 768 else "0"))
     if 0 <= march < 4:
         t = {"fp64": "double,FullStore<double>", "fp16pop": "float,HalfStore", "bf16pop": "float,BF16Store"}
@@ -295,7 +297,7 @@ def run_ours(args):
     from paper_2002_03644_gb300 import hlbm
 
     prec = {"fp32": hlbm.HLBM_FP32, "fp64": hlbm.HLBM_FP64, "fp16pop": hlbm.HLBM_FP32_F16POP,
-            "bf16pop": hlbm.HLBM_FP32_BF16POP}[args.precision]
+            "bf16pop": hlbm.HLBM_FP32_BF16POP, "moments": hlbm.HLBM_FP32_MOMENTS}[args.precision]
     case = workload(args.n)
     cells = case.nx * case.ny
     # a dedicated stream: torch's default stream has handle 0, which the C ABI

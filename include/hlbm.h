@@ -46,8 +46,13 @@ extern "C" {
  * all arithmetic in FP32 and keep s and a1 in FP32, but store each
  * population as F_i - f_ref_i in FP16 or BF16, where f_ref is the
  * equilibrium of the mean initial state (mass-weighted velocity, mean rho
- * and theta), fixed at hlbm_init_fields / hlbm_set_state. */
-enum { HLBM_FP64 = 0, HLBM_FP32 = 1, HLBM_FP32_F16POP = 2, HLBM_FP32_BF16POP = 3 };
+ * and theta), fixed at hlbm_init_fields / hlbm_set_state.
+ * HLBM_FP32_MOMENTS keeps no populations: the state is rho, u_x, u_y, s and
+ * a1 in FP32 (7 values per cell instead of 13), and each step rebuilds the
+ * post-collision populations from them (in the regularised scheme they are
+ * a function of the level's macros and a1, Sec. 3.4).  It supports every
+ * call but hlbm_get_populations (HLBM_ERR_UNSUPPORTED) and batches. */
+enum { HLBM_FP64 = 0, HLBM_FP32 = 1, HLBM_FP32_F16POP = 2, HLBM_FP32_BF16POP = 3, HLBM_FP32_MOMENTS = 4 };
 
 /* boundary kind per side (Sec. 4-5 use periodic, zero-gradient and imposed
  * states; the paper refers their exact form to an earlier work) */
@@ -78,7 +83,7 @@ enum {
  * Dirichlet y side takes precedence, then a Dirichlet x side. */
 typedef struct {
     int32_t nx, ny;        /* interior cells, >= 1 each */
-    int32_t precision;     /* HLBM_FP64, HLBM_FP32, HLBM_FP32_F16POP or HLBM_FP32_BF16POP */
+    int32_t precision;     /* HLBM_FP64, HLBM_FP32, HLBM_FP32_F16POP, HLBM_FP32_BF16POP or HLBM_FP32_MOMENTS */
     int32_t phi_mode;      /* 0: Phi = -(tau/tau_bar) a1 : grad u (eq. viscous
                               heat discret, default); 1: finite-difference
                               Phi of eq. (viscous heat) */
@@ -133,7 +138,8 @@ int hlbm_get_macros(hlbm_handle *h, double *rho, double *ux, double *uy, double 
 
 /* The 9 post-collision populations of the current level (eq. streamalgo,
  * before propagation), as 9 FP64 planes in D2Q9 order c_x = [0,1,0,-1,0,1,
- * -1,-1,1], c_y = [0,0,1,0,-1,1,1,-1,-1].  Synchronises. */
+ * -1,-1,1], c_y = [0,0,1,0,-1,1,1,-1,-1].  Synchronises.  HLBM_ERR_UNSUPPORTED
+ * for HLBM_FP32_MOMENTS, which stores no populations. */
 int hlbm_get_populations(hlbm_handle *h, double *F, int mem_kind);
 
 /* Diagnostics of the current level, FP64 sums over interior cells:

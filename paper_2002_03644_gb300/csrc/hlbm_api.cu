@@ -65,6 +65,7 @@ struct hlbm_handle {
     int tma_variant = 0;        // FP32 kernel choice, fixed at create
     int tile_variant = 0;
     int march_variant = -1;     // row-marching kernel variant, -1: tiled / TMA kernels
+    bool moments = false;       // HLBM_FP32_MOMENTS: 7 FP32 planes, moment-state kernel
     int march_nseg = 1;         // row segments per strip
     int *d_err = nullptr;       // device-side timeout flag of the TMA kernel
     int64_t step = 0;
@@ -102,6 +103,12 @@ template <typename T, typename S>
 static T *aux_planes(const hlbm_handle *h, int idx)
 {
     return reinterpret_cast<T *>(static_cast<char *>(h->state[idx]) + 9 * h->plane * sizeof(typename S::raw));
+}
+
+// Bytes of one state copy.
+static size_t payload_bytes(const hlbm_handle *h)
+{
+    return h->moments ? h->plane * MS_NPLANE * sizeof(float) : h->plane * (9 * h->fsize + 4 * h->asize);
 }
 
 // Call fn(Types<T, S>{}) for the handle's precision.
@@ -337,8 +344,63 @@ static cudaError_t setup_march(hlbm_handle *h)
     });
 }
 
+// Moment-state kernel: 64 threads at <= 128 registers (strips of 116
+// columns), row segments as for the marching kernel; the instantiation
+// matches the handle's sigma > 0 and Phi choice.
+constexpr int kMomNT = 64, kMomMinB = 8;
+
+static const void *moment_kernel_ptr(const hlbm_handle *h)
+{
+    const bool sig = h->kp.sigma_nonzero != 0, phi0 = h->kp.phi_mode == 0;
+    if (sig) return phi0 ? (const void *)march_moment_kernel<kMomNT, kMomMinB, true, true>
+                         : (const void *)march_moment_kernel<kMomNT, kMomMinB, true, false>;
+    return phi0 ? (const void *)march_moment_kernel<kMomNT, kMomMinB, false, true>
+                : (const void *)march_moment_kernel<kMomNT, kMomMinB, false, false>;
+}
+
+static cudaError_t setup_moments(hlbm_handle *h)
+{
+    using G = MomGeom<kMomNT>;
+    const void *fn = moment_kernel_ptr(h);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMomNT, G::smem_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return e;
+    const long long strips = (h->p.nx + G::W - 1) / G::W;
+    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+    long long nseg = (cap + strips - 1) / strips;
+    const long long least = (h->p.ny + kMarchMaxRows - 1) / kMarchMaxRows;
+    if (nseg < least) nseg = least;
+    const long long most = h->p.ny / kMarchMinRows > 0 ? h->p.ny / kMarchMinRows : 1;
+    if (nseg > most) nseg = most;
+    const int rows = env_choice("HLBM_MARCH_ROWS", 0, 1, 1 << 20);
+    if (rows > 0) nseg = (h->p.ny + rows - 1) / rows;
+    if (nseg > 65535) nseg = 65535;
+    h->march_nseg = (int)(nseg > 0 ? nseg : 1);
+    return cudaSuccess;
+}
+
+static cudaError_t launch_moments(hlbm_handle *h)
+{
+    using G = MomGeom<kMomNT>;
+    dim3 grid((h->p.nx + G::W - 1) / G::W, h->march_nseg);
+    const float *in = static_cast<const float *>(h->state[h->cur]);
+    float *out = static_cast<float *>(h->state[h->cur ^ 1]);
+    const bool sig = h->kp.sigma_nonzero != 0, phi0 = h->kp.phi_mode == 0;
+    const size_t sm = G::smem_bytes;
+    if (sig && phi0) march_moment_kernel<kMomNT, kMomMinB, true, true><<<grid, kMomNT, sm, h->stream>>>(in, out, h->kp, h->march_nseg);
+    else if (sig) march_moment_kernel<kMomNT, kMomMinB, true, false><<<grid, kMomNT, sm, h->stream>>>(in, out, h->kp, h->march_nseg);
+    else if (phi0) march_moment_kernel<kMomNT, kMomMinB, false, true><<<grid, kMomNT, sm, h->stream>>>(in, out, h->kp, h->march_nseg);
+    else march_moment_kernel<kMomNT, kMomMinB, false, false><<<grid, kMomNT, sm, h->stream>>>(in, out, h->kp, h->march_nseg);
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_one_step(hlbm_handle *h)
 {
+    if (h->moments) return launch_moments(h);
     using F32 = FullStore<float>;
     if (h->march_variant >= 0) {
         return with_types(h, [&](auto ty) {
@@ -397,7 +459,7 @@ static int validate(const hlbm_params *p)
     if (!p) return HLBM_ERR_ARG;
     if (p->nx < 1 || p->ny < 1) return HLBM_ERR_ARG;
     if ((long long)p->nx * p->ny > (1ll << 28)) return HLBM_ERR_ARG;
-    if (p->precision < HLBM_FP64 || p->precision > HLBM_FP32_BF16POP) return HLBM_ERR_UNSUPPORTED;
+    if (p->precision < HLBM_FP64 || p->precision > HLBM_FP32_MOMENTS) return HLBM_ERR_UNSUPPORTED;
     if (p->phi_mode != 0 && p->phi_mode != 1) return HLBM_ERR_ARG;
     if (!(p->gamma > 1.0) || !(p->Pr > 0.0) || !(p->mu >= 0.0) || !(p->sigma >= 0.0 && p->sigma <= 1.0))
         return HLBM_ERR_ARG;
@@ -514,11 +576,12 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         if (e != cudaSuccess) { delete h; return HLBM_ERR_CUDA; }
         h->own_stream = true;
     }
+    h->moments = params->precision == HLBM_FP32_MOMENTS;
     h->asize = params->precision == HLBM_FP64 ? sizeof(double) : sizeof(float);
-    h->fsize = params->precision >= HLBM_FP32_F16POP ? 2 : h->asize;
+    h->fsize = (params->precision == HLBM_FP32_F16POP || params->precision == HLBM_FP32_BF16POP) ? 2 : h->asize;
     h->pitch = (params->nx + 31) / 32 * 32;
     h->plane = (size_t)h->pitch * params->ny;
-    const size_t bytes = h->plane * (9 * h->fsize + 4 * h->asize);
+    const size_t bytes = payload_bytes(h);
     const size_t ncell = (size_t)params->nx * params->ny;
     if (cudaMalloc(&h->state[0], bytes) != cudaSuccess || cudaMalloc(&h->state[1], bytes) != cudaSuccess ||
         cudaMalloc(&h->staging, 9 * ncell * sizeof(double)) != cudaSuccess ||
@@ -540,6 +603,15 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         return HLBM_ERR_CUDA;
     }
     fill_kparams(h);
+    if (h->moments) {
+        if (setup_moments(h) != cudaSuccess) {
+            cudaGetLastError();
+            hlbm_destroy(h);
+            return HLBM_ERR_CUDA;
+        }
+        *out = h;
+        return HLBM_OK;
+    }
     if (setup_march(h) != cudaSuccess ||
         (h->march_variant < 0 && params->precision == HLBM_FP32 && setup_fp32_kernel(h) != cudaSuccess)) {
         cudaGetLastError();
@@ -552,7 +624,11 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
 
 static int run_diagnostics(hlbm_handle *h, double out[8])
 {
-    CK(with_types(h, [&](auto ty) {
+    if (h->moments) {
+        moments_diag_partial_kernel<<<DIAG_BLOCKS, DIAG_NT, 0, h->stream>>>(static_cast<const float *>(h->state[h->cur]),
+                                                                            h->diag_partial, h->kp);
+        CK(cudaGetLastError(), "moments_diag_partial_kernel");
+    } else CK(with_types(h, [&](auto ty) {
            using T = typename decltype(ty)::t;
            using S = typename decltype(ty)::s;
            diag_partial_kernel<T, S><<<DIAG_BLOCKS, DIAG_NT, 0, h->stream>>>(
@@ -588,7 +664,7 @@ int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const 
     } else {
         for (int k = 0; k < 5; k++) dev[k] = src[k];
     }
-    if (h->p.precision >= HLBM_FP32_F16POP) {
+    if (h->p.precision == HLBM_FP32_F16POP || h->p.precision == HLBM_FP32_BF16POP) {
         // reference equilibrium of the mean state for the 16-bit forms
         field_sums_partial_kernel<<<DIAG_BLOCKS, DIAG_NT, 0, h->stream>>>(dev[0], dev[1], dev[2], dev[3],
                                                                           (long long)n, h->diag_partial);
@@ -606,7 +682,11 @@ int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const 
         for (int i = 0; i < 9; i++) h->kp.f_ref[i] = (float)fr[i];
     }
     dim3 blk(32, 8);
-    CK(with_types(h, [&](auto ty) {
+    if (h->moments) {
+        init_moments_kernel<<<cell_grid(h, blk), blk, 0, h->stream>>>(dev[0], dev[1], dev[2], dev[3], dev[4],
+                                                                      static_cast<float *>(h->state[0]), h->kp);
+        CK(cudaGetLastError(), "init_moments_kernel");
+    } else CK(with_types(h, [&](auto ty) {
            using T = typename decltype(ty)::t;
            using S = typename decltype(ty)::s;
            init_kernel<T, S><<<cell_grid(h, blk), blk, 0, h->stream>>>(dev[0], dev[1], dev[2], dev[3], dev[4],
@@ -676,7 +756,13 @@ static int extract(hlbm_handle *h, double *rho, double *ux, double *uy, double *
         for (int k = 0; k < 7; k++) dev[k] = dst[k];
     }
     dim3 blk(32, 8);
-    CK(with_types(h, [&](auto ty) {
+    if (h->moments) {
+        if (F) return fail(h, HLBM_ERR_UNSUPPORTED, "the moment state stores no populations");
+        moments_macros_kernel<<<cell_grid(h, blk), blk, 0, h->stream>>>(static_cast<const float *>(h->state[h->cur]),
+                                                                        dev[0], dev[1], dev[2], dev[3], dev[4], dev[5],
+                                                                        h->kp);
+        CK(cudaGetLastError(), "moments_macros_kernel");
+    } else CK(with_types(h, [&](auto ty) {
            using T = typename decltype(ty)::t;
            using S = typename decltype(ty)::s;
            macros_kernel<T, S><<<cell_grid(h, blk), blk, 0, h->stream>>>(pop_planes<T, S>(h, h->cur),
@@ -726,7 +812,7 @@ int hlbm_synchronize(hlbm_handle *h)
 int hlbm_state_bytes(const hlbm_handle *h, size_t *bytes)
 {
     if (!h || !bytes) return HLBM_ERR_ARG;
-    *bytes = sizeof(StateHeader) + h->plane * (9 * h->fsize + 4 * h->asize);
+    *bytes = sizeof(StateHeader) + payload_bytes(h);
     return HLBM_OK;
 }
 
@@ -741,7 +827,8 @@ int hlbm_get_state(hlbm_handle *h, void *buf, size_t bytes)
     StateHeader hd;
     memset(&hd, 0, sizeof(hd));
     hd.magic = STATE_MAGIC; hd.abi = HLBM_ABI_VERSION; hd.precision = h->p.precision;
-    hd.nx = h->p.nx; hd.ny = h->p.ny; hd.pitch = h->pitch; hd.nplane = NPLANE; hd.step = h->step;
+    hd.nx = h->p.nx; hd.ny = h->p.ny; hd.pitch = h->pitch; hd.nplane = h->moments ? MS_NPLANE : NPLANE;
+    hd.step = h->step;
     hd.payload_bytes = (int64_t)(need - sizeof(StateHeader));
     for (int i = 0; i < 9; i++) hd.ref[i] = h->kp.f_ref[i];
     memcpy(buf, &hd, sizeof(hd));
@@ -760,7 +847,7 @@ int hlbm_set_state(hlbm_handle *h, const void *buf, size_t bytes)
     StateHeader hd;
     memcpy(&hd, buf, sizeof(hd));
     if (hd.magic != STATE_MAGIC || hd.abi != HLBM_ABI_VERSION || hd.precision != h->p.precision || hd.nx != h->p.nx ||
-        hd.ny != h->p.ny || hd.pitch != h->pitch || hd.nplane != NPLANE || hd.step < 0 ||
+        hd.ny != h->p.ny || hd.pitch != h->pitch || hd.nplane != (h->moments ? MS_NPLANE : NPLANE) || hd.step < 0 ||
         hd.payload_bytes != (int64_t)(need - sizeof(StateHeader)))
         return fail(h, HLBM_ERR_STATE, "state header mismatch");
     CK(cudaSetDevice(h->device), "cudaSetDevice");
@@ -1080,7 +1167,7 @@ int hlbm_batch_autotune(hlbm_batch *b, int *tile)
     int rc = HLBM_OK;
     for (size_t c = 0; c < b->cases.size() && rc == HLBM_OK; c++) {
         hlbm_handle *h = b->cases[c];
-        sizes[c] = h->plane * (9 * h->fsize + 4 * h->asize);
+        sizes[c] = payload_bytes(h);
         cur[c] = h->cur;
         steps[c] = h->step;
         if (cudaMalloc(&saved[c], sizes[c]) != cudaSuccess) rc = HLBM_ERR_NOMEM;

@@ -549,4 +549,530 @@ batched_march_kernel(const MarchTables tab, const int parity)
     }
 }
 
+// ---- moment-state form (HLBM_FP32_MOMENTS) -------------------------------------------
+// The state holds 7 FP32 planes per cell instead of 13: rho, u_x, u_y, s,
+// a1_xx, a1_xy, a1_yy (56 B read + written per cell-update instead of 104).
+// In the regularised scheme the post-collision populations are a function
+// of the level's macros and a1 (Sec. 3.4: only a1 needs keeping), so each
+// step rebuilds F(n) once per cell from the stored moments -- the arithmetic
+// of the collision that ended the previous step -- and ends with a1(n+1)
+// instead of a collision.  Per row r of the segment, three barriers apart:
+//   load:    rho, u, s, a1 of row r+3 (prefetched one iteration earlier);
+//            theta; the level-n macros of row r+3
+//   rebuild: F(n) of row r+2 from the level-n macros of rows r+1 .. r+3
+//            (E1, E2, omega) and its own a1; a Dirichlet position holds
+//            the side's equilibrium
+//   phase 2: level n+1 of row r+1 (as in the population form); a pull
+//            from beyond a zero-gradient side reads the edge cell, which is
+//            where the population form's index map takes the populations
+//   phase 3: a1(n+1) of row r (a1^FD, blended with a1^PR when sigma > 0),
+//            written with rho, u and s of level n+1.
+// Ring columns x0-6 .. x0+2NT-7: load on pairs 0 .. NT-1, rebuild on
+// 1 .. NT-2, phase 2 on 2 .. NT-3, phase 3 on the W = 2 (NT - 6) columns of
+// pairs 3 .. NT-4.
+constexpr int MS_RHO = 0, MS_UX = 1, MS_UY = 2, MS_S = 3, MS_AXX = 4, MS_AXY = 5, MS_AYY = 6, MS_NPLANE = 7;
+
+template <int NT>
+struct MomGeom {
+    static constexpr int NP = NT - 6;
+    static constexpr int W = 2 * NP;
+    static constexpr int CW = 2 * NT;
+    static constexpr int OFF_GA = 0;                  // [2][3][CW]  F_4, F_7, F_8 of rows r+1, r+2
+    static constexpr int OFF_GB = OFF_GA + 6 * CW;    // [2][3][CW]  F_0, F_1, F_3 of rows r+1, r+2
+    static constexpr int OFF_GC = OFF_GB + 6 * CW;    // [3][3][CW]  F_2, F_5, F_6 of rows r .. r+2
+    static constexpr int OFF_M = OFF_GC + 9 * CW;     // [4][4][CW]  rho, u_x, u_y, theta of rows r .. r+3
+    static constexpr int OFF_S = OFF_M + 16 * CW;     // [5][CW]     s of rows r-1 .. r+3
+    static constexpr int OFF_N = OFF_S + 5 * CW;      // [3][4][CW]  level n+1 of rows r-1 .. r+1
+    static constexpr int N = OFF_N + 12 * CW;
+    static constexpr size_t smem_bytes = sizeof(float) * (size_t)N;
+};
+
+// E_x, E_y (E1 upwind or centred, plus E2) and omega of one cell from its
+// macros and those of its four neighbours (the collision's first half).
+template <typename T>
+__device__ __forceinline__ void closure_terms(const Consts<T> &cs, bool cen, T rho, T ux, T uy, T th, T rW, T uxW,
+                                              T thW, T rE, T uxE, T thE, T rS, T uyS, T thS, T rN, T uyN, T thN,
+                                              T &ex, T &ey, T &omega)
+{
+    const T third = T(1) / T(3);
+    const T dxux = T(0.5) * (uxE - uxW);
+    const T dyuy = T(0.5) * (uyN - uyS);
+    const T p = rho * th * third;
+    const T gxc = gamma_defect(rho, ux, th), gyc = gamma_defect(rho, uy, th);
+    const T gxm = gamma_defect(rW, uxW, thW), gxp = gamma_defect(rE, uxE, thE);
+    const T gym = gamma_defect(rS, uyS, thS), gyp = gamma_defect(rN, uyN, thN);
+    const T e1xx = (ux > T(0) && !cen) ? gxc - gxm : ((ux < T(0) && !cen) ? gxp - gxc : T(0.5) * (gxp - gxm));
+    const T e1yy = (uy > T(0) && !cen) ? gyc - gym : ((uy < T(0) && !cen) ? gyp - gyc : T(0.5) * (gyp - gym));
+    const T e2 = p * cs.two_m_gamma * (dxux + dyuy);
+    ex = e1xx + e2;
+    ey = e1yy + e2;
+    omega = fdiv(cs.two_mu - p, cs.two_mu + p);
+}
+
+template <int NT, bool SIG, bool PHI0>
+__device__ __forceinline__ void moment_segment(const float *__restrict__ in, float *__restrict__ out,
+                                               const KParams &kp, const int x0, const int ys, const int ye,
+                                               unsigned char *smem_raw)
+{
+    using G = MomGeom<NT>;
+    using V = float2;
+    float *const sm = reinterpret_cast<float *>(smem_raw);
+    V *const gA = reinterpret_cast<V *>(sm + G::OFF_GA);  // [2][3][NT]
+    V *const gB = reinterpret_cast<V *>(sm + G::OFF_GB);  // [2][3][NT]
+    V *const gC = reinterpret_cast<V *>(sm + G::OFF_GC);  // [3][3][NT]
+    V *const rM = reinterpret_cast<V *>(sm + G::OFF_M);   // [4][4][NT]
+    V *const rS = reinterpret_cast<V *>(sm + G::OFF_S);   // [5][NT]
+    V *const rN = reinterpret_cast<V *>(sm + G::OFF_N);   // [3][4][NT]
+
+    Consts<float> cs;
+    cs.load(kp);
+    const Side<float> side{kp};
+    const bool cen = kp.e1_centred != 0;
+    const long long P = kp.plane;
+    const int pitch = kp.pitch;
+    const int t = threadIdx.x;
+    const int base = ys - 6;
+
+    // load / rebuild pair t: columns gxL, gxL + 1
+    const int gxL = x0 - 6 + 2 * t;
+    const int mcLa = map_col(gxL, kp), mcLb = map_col(gxL + 1, kp);
+    const bool vecL = gxL >= 0 && gxL + 1 < kp.nx;
+    const bool doR = t >= 1 && t <= NT - 2;
+    // phase-2 / phase-3 pair q = t + 2: columns gx2, gx2 + 1
+    const int q = t + 2;
+    const int gx2 = gxL + 4;
+    const bool do2 = t <= NT - 5;
+    const int mc2a = map_col(gx2, kp), mc2b = map_col(gx2 + 1, kp);
+    const bool vec2 = gx2 >= 0 && gx2 + 1 < kp.nx;
+    bool dir2[2];
+    int side2[2];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const int gx = gx2 + c;
+        side2[c] = gx < 0 ? 0 : 1;
+        dir2[c] = (gx < 0 || gx >= kp.nx) && kp.bc[side2[c]] == BC_DIRICHLET;
+    }
+    const bool do3 = t >= 1 && t <= G::NP;
+    const bool v3a = do3 && gx2 < kp.nx, v3b = do3 && gx2 + 1 < kp.nx;
+    // zero-gradient x sides: a neighbour (phase 3) or a pull source (phase 2)
+    // beyond the edge is the edge cell itself
+    const bool zgW = gx2 == 0 && kp.bc[0] == BC_ZEROGRAD;             // west of cell a
+    const bool zgEa = gx2 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD;    // east of cell a
+    const bool zgEb = gx2 + 1 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD; // east of cell b
+
+    // prefetch registers: moments of row r+4 (load pair), a1 of row r+2 (phase-2 pair)
+    float pM[2][4], pA[2][3], pA2[2][3];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) pM[c][k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; k++) { pA[c][k] = 0.0f; pA2[c][k] = 0.0f; }
+    }
+    // moments of row y at the load pair; a Dirichlet position gives the side's
+    // state with a1 = 0
+    auto load_row = [&](int y) {
+        const int mr = map_row(y, kp);
+        if (mr >= 0 && vecL) {
+            const float *src = in + ((long long)mr * pitch + gxL);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const V v = *reinterpret_cast<const V *>(src + k * P);
+                pM[0][k] = v.x; pM[1][k] = v.y;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const V v = *reinterpret_cast<const V *>(src + (MS_AXX + k) * P);
+                pA[0][k] = v.x; pA[1][k] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const int o = join_map(mr, c ? mcLb : mcLa, pitch);
+                if (o >= 0) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) pM[c][k] = in[k * P + o];
+#pragma unroll
+                    for (int k = 0; k < 3; k++) pA[c][k] = in[(MS_AXX + k) * P + o];
+                } else {
+                    const int sd = -o - 1;
+                    pM[c][0] = side.rho(sd); pM[c][1] = side.ux(sd); pM[c][2] = side.uy(sd); pM[c][3] = side.s_(sd);
+                    pA[c][0] = pA[c][1] = pA[c][2] = 0.0f;
+                }
+            }
+        }
+    };
+    // a1(n) of row y at the phase-2 pair (for Phi)
+    auto load_a2 = [&](int y) {
+        if (!PHI0 || !do2) return;
+        const int mr = map_row(y, kp);
+        if (mr >= 0 && vec2) {
+            const float *src = in + ((long long)mr * pitch + gx2);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const V v = *reinterpret_cast<const V *>(src + (MS_AXX + k) * P);
+                pA2[0][k] = v.x; pA2[1][k] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const int o = join_map(mr, c ? mc2b : mc2a, pitch);
+#pragma unroll
+                for (int k = 0; k < 3; k++) pA2[c][k] = o >= 0 ? in[(MS_AXX + k) * P + o] : 0.0f;
+            }
+        }
+    };
+    load_row(base + 3);
+    load_a2(base + 1);
+
+    float aCur[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};  // a1(n) of the rebuild row
+    CellN1<float> cur[2], nxt[2];
+#pragma unroll
+    for (int c = 0; c < 2; c++) cur[c] = nxt[c] = CellN1<float>{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+
+    for (int r = base; r < ye; r++) {
+        const int rel = r - base;
+        // ---- load: level-n macros and s of row r+3
+        float mv[2][4], an[2][3], a2[2][3];
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) mv[c][k] = pM[c][k];
+#pragma unroll
+            for (int k = 0; k < 3; k++) { an[c][k] = pA[c][k]; a2[c][k] = pA2[c][k]; }
+        }
+        if (r + 1 < ye) {
+            load_row(r + 4);
+            load_a2(r + 2);
+        }
+        {
+            const int mr = map_row(r + 3, kp);
+            float th[2];
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const int o = join_map(mr, c ? mcLb : mcLa, pitch);
+                th[c] = o >= 0 ? cs.theta(mv[c][0], mv[c][3]) : side.th(-o - 1);
+            }
+            const int m3 = (rel + 3) & 3;
+            rM[(m3 * 4 + 0) * NT + t] = V{mv[0][0], mv[1][0]};
+            rM[(m3 * 4 + 1) * NT + t] = V{mv[0][1], mv[1][1]};
+            rM[(m3 * 4 + 2) * NT + t] = V{mv[0][2], mv[1][2]};
+            rM[(m3 * 4 + 3) * NT + t] = V{th[0], th[1]};
+            rS[((rel + 3) % 5) * NT + t] = V{mv[0][3], mv[1][3]};
+        }
+        __syncthreads();
+
+        // ---- rebuild: F(n) of row r+2 on pair t
+        if (rel >= 2 && doR) {
+            const int m1 = (rel + 1) & 3, m2 = (rel + 2) & 3, m3 = (rel + 3) & 3;
+            const V *M2 = rM + m2 * 4 * NT, *M1 = rM + m1 * 4 * NT, *M3 = rM + m3 * 4 * NT;
+            V c0[4], cw[4], ce[4], cS[4], cN[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                c0[k] = M2[k * NT + t];
+                cw[k] = M2[k * NT + t - 1];
+                ce[k] = M2[k * NT + t + 1];
+                cS[k] = M1[k * NT + t];
+                cN[k] = M3[k * NT + t];
+            }
+            const int mr = map_row(r + 2, kp);
+            float fa[9], fb[9];
+            {
+                float ex, ey, om;
+                closure_terms<float>(cs, cen, c0[0].x, c0[1].x, c0[2].x, c0[3].x, cw[0].y, cw[1].y, cw[3].y,
+                                     c0[0].y, c0[1].y, c0[3].y, cS[0].x, cS[2].x, cS[3].x, cN[0].x, cN[2].x,
+                                     cN[3].x, ex, ey, om);
+                build_populations(c0[0].x, c0[1].x, c0[2].x, c0[3].x, aCur[0][0], aCur[0][1], aCur[0][2], ex, ey,
+                                  om, fa);
+                closure_terms<float>(cs, cen, c0[0].y, c0[1].y, c0[2].y, c0[3].y, c0[0].x, c0[1].x, c0[3].x,
+                                     ce[0].x, ce[1].x, ce[3].x, cS[0].y, cS[2].y, cS[3].y, cN[0].y, cN[2].y,
+                                     cN[3].y, ex, ey, om);
+                build_populations(c0[0].y, c0[1].y, c0[2].y, c0[3].y, aCur[1][0], aCur[1][1], aCur[1][2], ex, ey,
+                                  om, fb);
+            }
+            const int oa = join_map(mr, mcLa, pitch), ob = join_map(mr, mcLb, pitch);
+            if (oa < 0) {
+#pragma unroll
+                for (int i = 0; i < 9; i++) fa[i] = side.F(-oa - 1, i);
+            }
+            if (ob < 0) {
+#pragma unroll
+                for (int i = 0; i < 9; i++) fb[i] = side.F(-ob - 1, i);
+            }
+            const int a2s = (rel + 2) & 1, c2s = (rel + 2) % 3;
+            gA[(a2s * 3 + 0) * NT + t] = V{fa[4], fb[4]};
+            gA[(a2s * 3 + 1) * NT + t] = V{fa[7], fb[7]};
+            gA[(a2s * 3 + 2) * NT + t] = V{fa[8], fb[8]};
+            gB[(a2s * 3 + 0) * NT + t] = V{fa[0], fb[0]};
+            gB[(a2s * 3 + 1) * NT + t] = V{fa[1], fb[1]};
+            gB[(a2s * 3 + 2) * NT + t] = V{fa[3], fb[3]};
+            gC[(c2s * 3 + 0) * NT + t] = V{fa[2], fb[2]};
+            gC[(c2s * 3 + 1) * NT + t] = V{fa[5], fb[5]};
+            gC[(c2s * 3 + 2) * NT + t] = V{fa[6], fb[6]};
+        }
+        __syncthreads();
+
+        // ---- phase 2: level n+1 of row r+1 on pair q
+        const int y2 = r + 1;
+        if (rel >= 4 && do2) {
+            const int m0 = rel & 3, m1 = (rel + 1) & 3, m2 = (rel + 2) & 3;
+            const V rho0 = rM[(m1 * 4 + 0) * NT + q];
+            V mc[3][3], ms[3], mn[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                mc[k][0] = rM[(m1 * 4 + 1 + k) * NT + q - 1];
+                mc[k][1] = rM[(m1 * 4 + 1 + k) * NT + q];
+                mc[k][2] = rM[(m1 * 4 + 1 + k) * NT + q + 1];
+                ms[k] = rM[(m0 * 4 + 1 + k) * NT + q];
+                mn[k] = rM[(m2 * 4 + 1 + k) * NT + q];
+            }
+            const int s0 = (rel - 1) % 5, s1 = rel % 5, s2 = (rel + 1) % 5, s3 = (rel + 2) % 5, s4 = (rel + 3) % 5;
+            const V sc0 = rS[s2 * NT + q - 1], sc1 = rS[s2 * NT + q], sc2 = rS[s2 * NT + q + 1];
+            const V sS2 = rS[s0 * NT + q], sS1 = rS[s1 * NT + q], sN1 = rS[s3 * NT + q], sN2 = rS[s4 * NT + q];
+            // pull sources: F_0,1,3 of row y2, F_2,5,6 of row y2-1, F_4,7,8 of row y2+1;
+            // beyond a zero-gradient side, the edge row / column itself
+            const bool zS = y2 == 0 && kp.bc[2] == BC_ZEROGRAD;
+            const bool zN = y2 == kp.ny - 1 && kp.bc[3] == BC_ZEROGRAD;
+            const int bsl = (rel + 1) & 1;                               // row y2 in gB
+            const int csl = zS ? (rel + 1) % 3 : rel % 3;                // row y2-1 (or y2) in gC
+            const int asl = zN ? (rel + 1) & 1 : (rel + 2) & 1;          // row y2+1 (or y2) in gA
+            const V *GB = gB + bsl * 3 * NT, *GC = gC + csl * 3 * NT, *GA = gA + asl * 3 * NT;
+            float ga[9], gb[9];
+            {
+                const V f0 = GB[0 * NT + q], f2 = GC[0 * NT + q], f4 = GA[0 * NT + q];
+                ga[0] = f0.x; gb[0] = f0.y;
+                ga[2] = f2.x; gb[2] = f2.y;
+                ga[4] = f4.x; gb[4] = f4.y;
+                // c_x = +1 (1, 5, 8): from x-1 (cell a: pair q-1, or itself at a zero-gradient edge)
+                const V f1l = GB[1 * NT + q - 1], f1c = GB[1 * NT + q];
+                const V f5l = GC[1 * NT + q - 1], f5c = GC[1 * NT + q];
+                const V f8l = GA[2 * NT + q - 1], f8c = GA[2 * NT + q];
+                ga[1] = zgW ? f1c.x : f1l.y; gb[1] = f1c.x;
+                ga[5] = zgW ? f5c.x : f5l.y; gb[5] = f5c.x;
+                ga[8] = zgW ? f8c.x : f8l.y; gb[8] = f8c.x;
+                // c_x = -1 (3, 6, 7): from x+1
+                const V f3c = GB[2 * NT + q], f3r = GB[2 * NT + q + 1];
+                const V f6c = GC[2 * NT + q], f6r = GC[2 * NT + q + 1];
+                const V f7c = GA[1 * NT + q], f7r = GA[1 * NT + q + 1];
+                ga[3] = zgEa ? f3c.x : f3c.y; gb[3] = zgEb ? f3c.y : f3r.x;
+                ga[6] = zgEa ? f6c.x : f6c.y; gb[6] = zgEb ? f6c.y : f6r.x;
+                ga[7] = zgEa ? f7c.x : f7c.y; gb[7] = zgEb ? f7c.y : f7r.x;
+            }
+            nxt[0] = level_np1<float, SIG, PHI0>(cs, rho0.x, mc[0][1].x, mc[1][1].x, mc[2][1].x,
+                                                 mc[0][0].y, mc[0][1].y, ms[0].x, mn[0].x,
+                                                 mc[1][0].y, mc[1][1].y, ms[1].x, mn[1].x,
+                                                 mc[2][0].y, mc[2][1].y, ms[2].x, mn[2].x,
+                                                 sc0.x, sc0.y, sc1.x, sc1.y, sc2.x, sS2.x, sS1.x, sN1.x, sN2.x,
+                                                 a2[0][0], a2[0][1], a2[0][2], ga);
+            nxt[1] = level_np1<float, SIG, PHI0>(cs, rho0.y, mc[0][1].y, mc[1][1].y, mc[2][1].y,
+                                                 mc[0][1].x, mc[0][2].x, ms[0].y, mn[0].y,
+                                                 mc[1][1].x, mc[1][2].x, ms[1].y, mn[1].y,
+                                                 mc[2][1].x, mc[2][2].x, ms[2].y, mn[2].y,
+                                                 sc0.y, sc1.x, sc1.y, sc2.x, sc2.y, sS2.y, sS1.y, sN1.y, sN2.y,
+                                                 a2[1][0], a2[1][1], a2[1][2], gb);
+            const bool out2y = y2 < 0 || y2 >= kp.ny;
+            const int side2y = y2 < 0 ? 2 : 3;
+            const bool dir2y = out2y && kp.bc[side2y] == BC_DIRICHLET;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                if (dir2y || dir2[c]) {
+                    const int sd = dir2y ? side2y : side2[c];
+                    nxt[c].rho = side.rho(sd); nxt[c].ux = side.ux(sd); nxt[c].uy = side.uy(sd);
+                    nxt[c].th = side.th(sd); nxt[c].s = side.s_(sd);
+                }
+            }
+            const int ns2 = (rel + 1) % 3;
+            rN[(ns2 * 4 + 0) * NT + q] = V{nxt[0].rho, nxt[1].rho};
+            rN[(ns2 * 4 + 1) * NT + q] = V{nxt[0].ux, nxt[1].ux};
+            rN[(ns2 * 4 + 2) * NT + q] = V{nxt[0].uy, nxt[1].uy};
+            rN[(ns2 * 4 + 3) * NT + q] = V{nxt[0].th, nxt[1].th};
+        }
+        __syncthreads();
+
+        // ---- phase 3: a1(n+1) of row r; write the level-(n+1) moments
+        if (r >= ys && do3) {
+            const int ns0 = (rel + 2) % 3, ns1 = rel % 3, ns2 = (rel + 1) % 3;  // rows r-1, r, r+1
+            const bool zS = r == 0 && kp.bc[2] == BC_ZEROGRAD;
+            const bool zN = r == kp.ny - 1 && kp.bc[3] == BC_ZEROGRAD;
+            V nW[4], nE[4], nS[4], nN[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                nW[k] = rN[(ns1 * 4 + k) * NT + q - 1];
+                nE[k] = rN[(ns1 * 4 + k) * NT + q + 1];
+                nS[k] = rN[(ns0 * 4 + k) * NT + q];
+                nN[k] = rN[(ns2 * 4 + k) * NT + q];
+            }
+            const CellN1<float> &A = cur[0], &B = cur[1];
+            const float aWr = zgW ? A.rho : nW[0].y, aWux = zgW ? A.ux : nW[1].y, aWuy = zgW ? A.uy : nW[2].y,
+                        aWth = zgW ? A.th : nW[3].y;
+            const float aEr = zgEa ? A.rho : B.rho, aEux = zgEa ? A.ux : B.ux, aEuy = zgEa ? A.uy : B.uy,
+                        aEth = zgEa ? A.th : B.th;
+            const float bEr = zgEb ? B.rho : nE[0].x, bEux = zgEb ? B.ux : nE[1].x, bEuy = zgEb ? B.uy : nE[2].x,
+                        bEth = zgEb ? B.th : nE[3].x;
+            float aa[3], ab[3];
+            auto a1_of = [&](const CellN1<float> &c, float rW, float uxW, float uyW, float thW, float rE, float uxE,
+                             float uyE, float thE, float rS, float uxS, float uyS, float thS, float rN, float uxN,
+                             float uyN, float thN, float *a) {
+                const float dxux = 0.5f * (uxE - uxW), dyux = 0.5f * (uxN - uxS);
+                const float dxuy = 0.5f * (uyE - uyW), dyuy = 0.5f * (uyN - uyS);
+                const float p = c.rho * c.th * (1.0f / 3.0f);
+                const float cfd = -(cs.mu + 0.5f * p);
+                const float fdxx = cfd * (dxux - dyuy), fdxy = cfd * (dyux + dxuy);
+                if (SIG) {
+                    float ex, ey, om;
+                    closure_terms<float>(cs, cen, c.rho, c.ux, c.uy, c.th, rW, uxW, thW, rE, uxE, thE, rS, uyS, thS,
+                                         rN, uyN, thN, ex, ey, om);
+                    const float prxx = c.mxx - c.rho * c.ux * c.ux - p + 0.5f * ex;
+                    const float pryy = c.myy - c.rho * c.uy * c.uy - p + 0.5f * ey;
+                    const float prxy = c.mxy - c.rho * c.ux * c.uy;
+                    a[0] = cs.sigma * prxx + cs.one_m_sigma * fdxx;
+                    a[2] = cs.sigma * pryy - cs.one_m_sigma * fdxx;
+                    a[1] = cs.sigma * prxy + cs.one_m_sigma * fdxy;
+                } else {
+                    a[0] = fdxx; a[2] = -fdxx; a[1] = fdxy;
+                }
+            };
+            a1_of(A, aWr, aWux, aWuy, aWth, aEr, aEux, aEuy, aEth,
+                  zS ? A.rho : nS[0].x, zS ? A.ux : nS[1].x, zS ? A.uy : nS[2].x, zS ? A.th : nS[3].x,
+                  zN ? A.rho : nN[0].x, zN ? A.ux : nN[1].x, zN ? A.uy : nN[2].x, zN ? A.th : nN[3].x, aa);
+            a1_of(B, A.rho, A.ux, A.uy, A.th, bEr, bEux, bEuy, bEth,
+                  zS ? B.rho : nS[0].y, zS ? B.ux : nS[1].y, zS ? B.uy : nS[2].y, zS ? B.th : nS[3].y,
+                  zN ? B.rho : nN[0].y, zN ? B.ux : nN[1].y, zN ? B.uy : nN[2].y, zN ? B.th : nN[3].y, ab);
+            const long long o = (long long)r * pitch + gx2;
+            float *d = out + o;
+            if (v3a && v3b) {
+                *reinterpret_cast<V *>(d + MS_RHO * P) = V{A.rho, B.rho};
+                *reinterpret_cast<V *>(d + MS_UX * P) = V{A.ux, B.ux};
+                *reinterpret_cast<V *>(d + MS_UY * P) = V{A.uy, B.uy};
+                *reinterpret_cast<V *>(d + MS_S * P) = V{A.s, B.s};
+#pragma unroll
+                for (int k = 0; k < 3; k++) *reinterpret_cast<V *>(d + (MS_AXX + k) * P) = V{aa[k], ab[k]};
+            } else if (v3a) {
+                d[MS_RHO * P] = A.rho; d[MS_UX * P] = A.ux; d[MS_UY * P] = A.uy; d[MS_S * P] = A.s;
+#pragma unroll
+                for (int k = 0; k < 3; k++) d[(MS_AXX + k) * P] = aa[k];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            cur[c] = nxt[c];
+#pragma unroll
+            for (int k = 0; k < 3; k++) aCur[c][k] = an[c][k];
+        }
+    }
+}
+
+template <int NT, int MINB, bool SIG, bool PHI0>
+__global__ void __launch_bounds__(NT, MINB)
+march_moment_kernel(const float *__restrict__ in, float *__restrict__ out, const KParams kp, const int nseg)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ys = seg_start(blockIdx.y, nseg, kp.ny), ye = seg_start(blockIdx.y + 1, nseg, kp.ny);
+    moment_segment<NT, SIG, PHI0>(in, out, kp, blockIdx.x * MomGeom<NT>::W, ys, ye, smem_raw);
+}
+
+// Moment state from FP64 caller fields (Algorithm 1, steps 1-4): rho, u, s
+// and a1 (given, or a1^FD of the initial fields as in init_kernel).
+__global__ void init_moments_kernel(const double *__restrict__ rho, const double *__restrict__ ux,
+                                    const double *__restrict__ uy, const double *__restrict__ th,
+                                    const double *__restrict__ a1, float *__restrict__ out, const KParams kp)
+{
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= kp.nx || gy >= kp.ny) return;
+    const int n = kp.nx * kp.ny;
+    const int c = gy * kp.nx + gx;
+    const long long P = kp.plane;
+    const int o = gy * kp.pitch + gx;
+    double axx, axy, ayy;
+    if (a1) {
+        axx = a1[c]; axy = a1[n + c]; ayy = a1[2 * n + c];
+    } else {
+        auto vel = [&](int dx, int dy, double &u, double &v) {
+            const int q = locate(gx + dx, gy + dy, kp, kp.nx);
+            if (q >= 0) { u = ux[q]; v = uy[q]; } else { u = kp.d_ux[-q - 1]; v = kp.d_uy[-q - 1]; }
+        };
+        double uxm, vxm, uxp, vxp, uym, vym, uyp, vyp;
+        vel(-1, 0, uxm, vxm); vel(1, 0, uxp, vxp); vel(0, -1, uym, vym); vel(0, 1, uyp, vyp);
+        const double p = rho[c] * th[c] / 3.0;
+        const double cfd = -(kp.mu + 0.5 * p);
+        axx = cfd * (0.5 * (uxp - uxm) - 0.5 * (vyp - vym));
+        axy = cfd * (0.5 * (uyp - uym) + 0.5 * (vxp - vxm));
+        ayy = -axx;
+    }
+    out[MS_RHO * P + o] = (float)rho[c];
+    out[MS_UX * P + o] = (float)ux[c];
+    out[MS_UY * P + o] = (float)uy[c];
+    out[MS_S * P + o] = (float)(kp.cv * (log(th[c]) - kp.gm1 * log(rho[c])));
+    out[MS_AXX * P + o] = (float)axx;
+    out[MS_AXY * P + o] = (float)axy;
+    out[MS_AYY * P + o] = (float)ayy;
+}
+
+// Caller fields from the moment state (theta recomputed from rho and s).
+__global__ void moments_macros_kernel(const float *__restrict__ in, double *rho, double *ux, double *uy,
+                                      double *th, double *s, double *a1, const KParams kp)
+{
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= kp.nx || gy >= kp.ny) return;
+    Consts<float> cs;
+    cs.load(kp);
+    const long long P = kp.plane;
+    const int o = gy * kp.pitch + gx;
+    const int c = gy * kp.nx + gx;
+    const size_t n = (size_t)kp.nx * kp.ny;
+    const float r = in[MS_RHO * P + o], sv = in[MS_S * P + o];
+    if (rho) rho[c] = (double)r;
+    if (ux) ux[c] = (double)in[MS_UX * P + o];
+    if (uy) uy[c] = (double)in[MS_UY * P + o];
+    if (th) th[c] = (double)cs.theta(r, sv);
+    if (s) s[c] = (double)sv;
+    if (a1) {
+        a1[c] = (double)in[MS_AXX * P + o];
+        a1[n + c] = (double)in[MS_AXY * P + o];
+        a1[2 * n + c] = (double)in[MS_AYY * P + o];
+    }
+}
+
+// Diagnostics of the moment state: the same 8 values as diag_partial_kernel.
+__global__ void __launch_bounds__(DIAG_NT)
+moments_diag_partial_kernel(const float *__restrict__ in, double *__restrict__ partial, const KParams kp)
+{
+    Consts<float> cs;
+    cs.load(kp);
+    const long long P = kp.plane;
+    const long long ncell = (long long)kp.nx * kp.ny;
+    double acc[DIAG_NV] = {0.0, 0.0, 0.0, 0.0, 1e300, 1e300, 0.0, 0.0};
+    for (long long c = (long long)blockIdx.x * DIAG_NT + threadIdx.x; c < ncell; c += (long long)gridDim.x * DIAG_NT) {
+        const int gy = (int)(c / kp.nx), gx = (int)(c - (long long)gy * kp.nx);
+        const int o = gy * kp.pitch + gx;
+        const float r = in[MS_RHO * P + o];
+        const double rho = (double)r;
+        const double u = (double)in[MS_UX * P + o], v = (double)in[MS_UY * P + o];
+        const double th = (double)cs.theta(r, in[MS_S * P + o]);
+        const bool bad = !(rho > 0.0) || !(th > 0.0) || !isfinite(rho) || !isfinite(th) || !isfinite(u) || !isfinite(v);
+        if (bad) { acc[7] += 1.0; continue; }
+        acc[0] += rho; acc[1] += rho * u; acc[2] += rho * v;
+        acc[3] += rho * kp.cv * th + 0.5 * rho * (u * u + v * v);
+        acc[4] = fmin(acc[4], rho); acc[5] = fmin(acc[5], th);
+        acc[6] = fmax(acc[6], sqrt(u * u + v * v) + sqrt(kp.gamma * th / 3.0));
+    }
+    __shared__ double red[DIAG_NV][DIAG_NT];
+#pragma unroll
+    for (int k = 0; k < DIAG_NV; k++) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = DIAG_NT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+#pragma unroll
+            for (int k = 0; k < DIAG_NV; k++) {
+                const double a = red[k][threadIdx.x], b = red[k][threadIdx.x + w];
+                red[k][threadIdx.x] = (k == 4 || k == 5) ? fmin(a, b) : (k == 6 ? fmax(a, b) : a + b);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < DIAG_NV) partial[blockIdx.x * DIAG_NV + threadIdx.x] = red[threadIdx.x][0];
+}
+
 }  // namespace hlbm

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-HLBM_FP64, HLBM_FP32, HLBM_FP32_F16POP, HLBM_FP32_BF16POP = 0, 1, 2, 3
+HLBM_FP64, HLBM_FP32, HLBM_FP32_F16POP, HLBM_FP32_BF16POP, HLBM_FP32_MOMENTS = 0, 1, 2, 3, 4
 HLBM_BC_PERIODIC, HLBM_BC_ZEROGRAD, HLBM_BC_DIRICHLET = 0, 1, 2
 HLBM_MEM_HOST, HLBM_MEM_DEVICE = 0, 1
 HLBM_OK, HLBM_ERR_ARG, HLBM_ERR_CFL, HLBM_ERR_NONFINITE = 0, -1, -2, -3
