@@ -23,7 +23,10 @@
 // from the edge cell itself in phase 3.
 #pragma once
 
+#include <type_traits>
+
 #include "hlbm_device.cuh"
+#include "hlbm_pack.cuh"
 
 namespace hlbm {
 
@@ -349,8 +352,24 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
                     mm[0] = side.rho(sd); mm[1] = side.ux(sd); mm[2] = side.uy(sd); mm[3] = side.th(sd);
                 }
             };
-            macros(fa, sPa, join_map(mr, mcLa, pitch), m[0]);
-            macros(fb, sPb, join_map(mr, mcLb, pitch), m[1]);
+            if constexpr (std::is_same<T, float>::value) {
+                // both cells at once (packed FP32)
+                f2 g[9];
+#pragma unroll
+                for (int i = 0; i < 9; i++) g[i] = mk2(fa[i], fb[i]);
+                f2 rho, jx, jy;
+                moments2(g, rho, jx, jy);
+                const f2 ir = rcp2(rho);
+                const f2 ux = jx * ir, uy = jy * ir, th = theta2(cs, rho, mk2(sPa, sPb));
+                m[0][0] = rho.x; m[0][1] = ux.x; m[0][2] = uy.x; m[0][3] = th.x;
+                m[1][0] = rho.y; m[1][1] = ux.y; m[1][2] = uy.y; m[1][3] = th.y;
+                const int oa = join_map(mr, mcLa, pitch), ob = join_map(mr, mcLb, pitch);
+                if (oa < 0) { const int sd = -oa - 1; m[0][0] = side.rho(sd); m[0][1] = side.ux(sd); m[0][2] = side.uy(sd); m[0][3] = side.th(sd); }
+                if (ob < 0) { const int sd = -ob - 1; m[1][0] = side.rho(sd); m[1][1] = side.ux(sd); m[1][2] = side.uy(sd); m[1][3] = side.th(sd); }
+            } else {
+                macros(fa, sPa, join_map(mr, mcLa, pitch), m[0]);
+                macros(fb, sPb, join_map(mr, mcLb, pitch), m[1]);
+            }
 #pragma unroll
             for (int k = 0; k < 4; k++) rM[(fs2 * 4 + k) * NT + t] = Vec2<T>::make(m[0][k], m[1][k]);
             rS[ss4 * NT + t] = Vec2<T>::make(sna, snb);
@@ -399,6 +418,28 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
                     ga[6] = f6c.y; gb[6] = f6r.x;
                     ga[7] = f7c.y; gb[7] = f7r.x;
                 }
+                if constexpr (std::is_same<T, float>::value) {
+                    // both cells at once (packed FP32): lane x = cell a, lane y = cell b
+                    f2 C[3], Wv[3], Ev[3], Sv[3], Nv[3];
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        C[k] = from2(mc[k][1]);
+                        Wv[k] = mk2(mc[k][0].y, mc[k][1].x);
+                        Ev[k] = mk2(mc[k][1].y, mc[k][2].x);
+                        Sv[k] = from2(ms[k]);
+                        Nv[k] = from2(mn[k]);
+                    }
+                    f2 g2[9];
+#pragma unroll
+                    for (int i = 0; i < 9; i++) g2[i] = mk2(ga[i], gb[i]);
+                    const CellN1x2 n2 = level_np1_2<SIG, PHI0>(
+                        cs, from2(rho0), C[0], C[1], C[2], Wv[0], Ev[0], Sv[0], Nv[0], Wv[1], Ev[1], Sv[1], Nv[1], Wv[2],
+                        Ev[2], Sv[2], Nv[2], from2(sc0), mk2(sc0.y, sc1.x), from2(sc1), mk2(sc1.y, sc2.x), from2(sc2),
+                        from2(sS2), from2(sS1), from2(sN1), from2(sN2), mk2(a2[0][0], a2[1][0]), mk2(a2[0][1], a2[1][1]),
+                        mk2(a2[0][2], a2[1][2]), g2);
+                    nxt[0] = CellN1<T>{n2.rho.x, n2.ux.x, n2.uy.x, n2.th.x, n2.s.x, n2.mxx.x, n2.myy.x, n2.mxy.x};
+                    nxt[1] = CellN1<T>{n2.rho.y, n2.ux.y, n2.uy.y, n2.th.y, n2.s.y, n2.mxx.y, n2.myy.y, n2.mxy.y};
+                } else {
                 nxt[0] = level_np1<T, SIG, PHI0>(cs, rho0.x, mc[0][1].x, mc[1][1].x, mc[2][1].x,
                                                  mc[0][0].y, mc[0][1].y, ms[0].x, mn[0].x,
                                                  mc[1][0].y, mc[1][1].y, ms[1].x, mn[1].x,
@@ -411,6 +452,7 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
                                                  mc[2][1].x, mc[2][2].x, ms[2].y, mn[2].y,
                                                  sc0.y, sc1.x, sc1.y, sc2.x, sc2.y, sS2.y, sS1.y, sN1.y, sN2.y,
                                                  a2[1][0], a2[1][1], a2[1][2], gb);
+                }
                 // Dirichlet cells hold the side's constants
                 const bool out2y = y2 < 0 || y2 >= kp.ny;
                 const int side2y = y2 < 0 ? 2 : 3;
@@ -453,6 +495,32 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
             const T bEr = zgEb ? B.rho : nE[0].x, bEux = zgEb ? B.ux : nE[1].x, bEuy = zgEb ? B.uy : nE[2].x,
                     bEth = zgEb ? B.th : nE[3].x;
             T fa[9], fb[9], aa[3], ab[3];
+            if constexpr (std::is_same<T, float>::value) {
+                // both cells at once (packed FP32); the neighbours of cell a are (W, E) =
+                // (west pair or a, b) and of cell b (a, east pair or b)
+                const f2 cr = mk2(A.rho, B.rho), cux = mk2(A.ux, B.ux), cuy = mk2(A.uy, B.uy), cth = mk2(A.th, B.th);
+                const f2 wr = mk2(aWr, A.rho), wux = mk2(aWux, A.ux), wuy = mk2(aWuy, A.uy), wth = mk2(aWth, A.th);
+                const f2 er = mk2(aEr, bEr), eux = mk2(aEux, bEux), euy = mk2(aEuy, bEuy), eth = mk2(aEth, bEth);
+                const f2 sr = zS ? cr : from2(nS[0]), sux = zS ? cux : from2(nS[1]), suy = zS ? cuy : from2(nS[2]),
+                         sth = zS ? cth : from2(nS[3]);
+                const f2 nr = zN ? cr : from2(nN[0]), nux = zN ? cux : from2(nN[1]), nuy = zN ? cuy : from2(nN[2]),
+                         nth = zN ? cth : from2(nN[3]);
+                const f2 half = bc2(0.5f);
+                const f2 dxux = half * (eux - wux), dyux = half * (nux - sux);
+                const f2 dxuy = half * (euy - wuy), dyuy = half * (nuy - suy);
+                f2 ex, ey, om;
+                closure_terms2(cs, cen, cr, cux, cuy, cth, wr, wux, wth, er, eux, eth, sr, suy, sth, nr, nuy, nth, ex, ey,
+                               om);
+                const CellN1x2 c2{cr, cux, cuy, cth, mk2(A.s, B.s), mk2(A.mxx, B.mxx), mk2(A.myy, B.myy),
+                                  mk2(A.mxy, B.mxy)};
+                f2 axx, axy, ayy, fo[9];
+                a1_next2<SIG>(cs, c2, dxux, dyux, dxuy, dyuy, ex, ey, axx, axy, ayy);
+                build_populations2(cr, cux, cuy, cth, axx, axy, ayy, ex, ey, om, fo);
+#pragma unroll
+                for (int i = 0; i < 9; i++) { fa[i] = fo[i].x; fb[i] = fo[i].y; }
+                aa[0] = axx.x; aa[1] = axy.x; aa[2] = ayy.x;
+                ab[0] = axx.y; ab[1] = axy.y; ab[2] = ayy.y;
+            } else {
             if (v3a) {
                 collide_cell<T, SIG>(cs, cen, A, aWr, aWux, aWuy, aWth, aEr, aEux, aEuy, aEth,
                                      zS ? A.rho : nS[0].x, zS ? A.ux : nS[1].x, zS ? A.uy : nS[2].x, zS ? A.th : nS[3].x,
@@ -464,6 +532,7 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
                                      zS ? B.rho : nS[0].y, zS ? B.ux : nS[1].y, zS ? B.uy : nS[2].y, zS ? B.th : nS[3].y,
                                      zN ? B.rho : nN[0].y, zN ? B.ux : nN[1].y, zN ? B.uy : nN[2].y, zN ? B.th : nN[3].y,
                                      fb, ab[0], ab[1], ab[2]);
+            }
             }
             const long long o = (long long)r * pitch + gx2;
             if (v3a && v3b) {
