@@ -847,17 +847,17 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
             const int mr = map_row(r + 2, kp);
             float fa[9], fb[9];
             {
-                float ex, ey, om;
-                closure_terms<float>(cs, cen, c0[0].x, c0[1].x, c0[2].x, c0[3].x, cw[0].y, cw[1].y, cw[3].y,
-                                     c0[0].y, c0[1].y, c0[3].y, cS[0].x, cS[2].x, cS[3].x, cN[0].x, cN[2].x,
-                                     cN[3].x, ex, ey, om);
-                build_populations(c0[0].x, c0[1].x, c0[2].x, c0[3].x, aCur[0][0], aCur[0][1], aCur[0][2], ex, ey,
-                                  om, fa);
-                closure_terms<float>(cs, cen, c0[0].y, c0[1].y, c0[2].y, c0[3].y, c0[0].x, c0[1].x, c0[3].x,
-                                     ce[0].x, ce[1].x, ce[3].x, cS[0].y, cS[2].y, cS[3].y, cN[0].y, cN[2].y,
-                                     cN[3].y, ex, ey, om);
-                build_populations(c0[0].y, c0[1].y, c0[2].y, c0[3].y, aCur[1][0], aCur[1][1], aCur[1][2], ex, ey,
-                                  om, fb);
+                // both cells at once (packed FP32): west of a is pair t-1, east of b pair t+1
+                f2 ex, ey, om, fo[9];
+                closure_terms2(cs, cen, from2(c0[0]), from2(c0[1]), from2(c0[2]), from2(c0[3]),
+                               mk2(cw[0].y, c0[0].x), mk2(cw[1].y, c0[1].x), mk2(cw[3].y, c0[3].x),
+                               mk2(c0[0].y, ce[0].x), mk2(c0[1].y, ce[1].x), mk2(c0[3].y, ce[3].x),
+                               from2(cS[0]), from2(cS[2]), from2(cS[3]), from2(cN[0]), from2(cN[2]), from2(cN[3]),
+                               ex, ey, om);
+                build_populations2(from2(c0[0]), from2(c0[1]), from2(c0[2]), from2(c0[3]), mk2(aCur[0][0], aCur[1][0]),
+                                   mk2(aCur[0][1], aCur[1][1]), mk2(aCur[0][2], aCur[1][2]), ex, ey, om, fo);
+#pragma unroll
+                for (int i = 0; i < 9; i++) { fa[i] = fo[i].x; fb[i] = fo[i].y; }
             }
             const int oa = join_map(mr, mcLa, pitch), ob = join_map(mr, mcLb, pitch);
             if (oa < 0) {
@@ -927,18 +927,27 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
                 ga[6] = zgEa ? f6c.x : f6c.y; gb[6] = zgEb ? f6c.y : f6r.x;
                 ga[7] = zgEa ? f7c.x : f7c.y; gb[7] = zgEb ? f7c.y : f7r.x;
             }
-            nxt[0] = level_np1<float, SIG, PHI0>(cs, rho0.x, mc[0][1].x, mc[1][1].x, mc[2][1].x,
-                                                 mc[0][0].y, mc[0][1].y, ms[0].x, mn[0].x,
-                                                 mc[1][0].y, mc[1][1].y, ms[1].x, mn[1].x,
-                                                 mc[2][0].y, mc[2][1].y, ms[2].x, mn[2].x,
-                                                 sc0.x, sc0.y, sc1.x, sc1.y, sc2.x, sS2.x, sS1.x, sN1.x, sN2.x,
-                                                 a2[0][0], a2[0][1], a2[0][2], ga);
-            nxt[1] = level_np1<float, SIG, PHI0>(cs, rho0.y, mc[0][1].y, mc[1][1].y, mc[2][1].y,
-                                                 mc[0][1].x, mc[0][2].x, ms[0].y, mn[0].y,
-                                                 mc[1][1].x, mc[1][2].x, ms[1].y, mn[1].y,
-                                                 mc[2][1].x, mc[2][2].x, ms[2].y, mn[2].y,
-                                                 sc0.y, sc1.x, sc1.y, sc2.x, sc2.y, sS2.y, sS1.y, sN1.y, sN2.y,
-                                                 a2[1][0], a2[1][1], a2[1][2], gb);
+            {
+                f2 C[3], Wv[3], Ev[3], Sv[3], Nv[3];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    C[k] = from2(mc[k][1]);
+                    Wv[k] = mk2(mc[k][0].y, mc[k][1].x);
+                    Ev[k] = mk2(mc[k][1].y, mc[k][2].x);
+                    Sv[k] = from2(ms[k]);
+                    Nv[k] = from2(mn[k]);
+                }
+                f2 g2[9];
+#pragma unroll
+                for (int i = 0; i < 9; i++) g2[i] = mk2(ga[i], gb[i]);
+                const CellN1x2 n2 = level_np1_2<SIG, PHI0>(
+                    cs, from2(rho0), C[0], C[1], C[2], Wv[0], Ev[0], Sv[0], Nv[0], Wv[1], Ev[1], Sv[1], Nv[1], Wv[2], Ev[2],
+                    Sv[2], Nv[2], from2(sc0), mk2(sc0.y, sc1.x), from2(sc1), mk2(sc1.y, sc2.x), from2(sc2), from2(sS2),
+                    from2(sS1), from2(sN1), from2(sN2), mk2(a2[0][0], a2[1][0]), mk2(a2[0][1], a2[1][1]),
+                    mk2(a2[0][2], a2[1][2]), g2);
+                nxt[0] = CellN1<float>{n2.rho.x, n2.ux.x, n2.uy.x, n2.th.x, n2.s.x, n2.mxx.x, n2.myy.x, n2.mxy.x};
+                nxt[1] = CellN1<float>{n2.rho.y, n2.ux.y, n2.uy.y, n2.th.y, n2.s.y, n2.mxx.y, n2.myy.y, n2.mxy.y};
+            }
             const bool out2y = y2 < 0 || y2 >= kp.ny;
             const int side2y = y2 < 0 ? 2 : 3;
             const bool dir2y = out2y && kp.bc[side2y] == BC_DIRICHLET;
@@ -979,34 +988,29 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
             const float bEr = zgEb ? B.rho : nE[0].x, bEux = zgEb ? B.ux : nE[1].x, bEuy = zgEb ? B.uy : nE[2].x,
                         bEth = zgEb ? B.th : nE[3].x;
             float aa[3], ab[3];
-            auto a1_of = [&](const CellN1<float> &c, float rW, float uxW, float uyW, float thW, float rE, float uxE,
-                             float uyE, float thE, float rS, float uxS, float uyS, float thS, float rN, float uxN,
-                             float uyN, float thN, float *a) {
-                const float dxux = 0.5f * (uxE - uxW), dyux = 0.5f * (uxN - uxS);
-                const float dxuy = 0.5f * (uyE - uyW), dyuy = 0.5f * (uyN - uyS);
-                const float p = c.rho * c.th * (1.0f / 3.0f);
-                const float cfd = -(cs.mu + 0.5f * p);
-                const float fdxx = cfd * (dxux - dyuy), fdxy = cfd * (dyux + dxuy);
-                if (SIG) {
-                    float ex, ey, om;
-                    closure_terms<float>(cs, cen, c.rho, c.ux, c.uy, c.th, rW, uxW, thW, rE, uxE, thE, rS, uyS, thS,
-                                         rN, uyN, thN, ex, ey, om);
-                    const float prxx = c.mxx - c.rho * c.ux * c.ux - p + 0.5f * ex;
-                    const float pryy = c.myy - c.rho * c.uy * c.uy - p + 0.5f * ey;
-                    const float prxy = c.mxy - c.rho * c.ux * c.uy;
-                    a[0] = cs.sigma * prxx + cs.one_m_sigma * fdxx;
-                    a[2] = cs.sigma * pryy - cs.one_m_sigma * fdxx;
-                    a[1] = cs.sigma * prxy + cs.one_m_sigma * fdxy;
-                } else {
-                    a[0] = fdxx; a[2] = -fdxx; a[1] = fdxy;
-                }
-            };
-            a1_of(A, aWr, aWux, aWuy, aWth, aEr, aEux, aEuy, aEth,
-                  zS ? A.rho : nS[0].x, zS ? A.ux : nS[1].x, zS ? A.uy : nS[2].x, zS ? A.th : nS[3].x,
-                  zN ? A.rho : nN[0].x, zN ? A.ux : nN[1].x, zN ? A.uy : nN[2].x, zN ? A.th : nN[3].x, aa);
-            a1_of(B, A.rho, A.ux, A.uy, A.th, bEr, bEux, bEuy, bEth,
-                  zS ? B.rho : nS[0].y, zS ? B.ux : nS[1].y, zS ? B.uy : nS[2].y, zS ? B.th : nS[3].y,
-                  zN ? B.rho : nN[0].y, zN ? B.ux : nN[1].y, zN ? B.uy : nN[2].y, zN ? B.th : nN[3].y, ab);
+            {
+                // both cells at once (packed FP32)
+                const f2 cr = mk2(A.rho, B.rho), cux = mk2(A.ux, B.ux), cuy = mk2(A.uy, B.uy), cth = mk2(A.th, B.th);
+                const f2 wr = mk2(aWr, A.rho), wux = mk2(aWux, A.ux), wuy = mk2(aWuy, A.uy), wth = mk2(aWth, A.th);
+                const f2 er = mk2(aEr, bEr), eux = mk2(aEux, bEux), euy = mk2(aEuy, bEuy), eth = mk2(aEth, bEth);
+                const f2 sr = zS ? cr : from2(nS[0]), sux = zS ? cux : from2(nS[1]), suy = zS ? cuy : from2(nS[2]),
+                         sth = zS ? cth : from2(nS[3]);
+                const f2 nr = zN ? cr : from2(nN[0]), nux = zN ? cux : from2(nN[1]), nuy = zN ? cuy : from2(nN[2]),
+                         nth = zN ? cth : from2(nN[3]);
+                const f2 half = bc2(0.5f);
+                const f2 dxux = half * (eux - wux), dyux = half * (nux - sux);
+                const f2 dxuy = half * (euy - wuy), dyuy = half * (nuy - suy);
+                f2 ex = bc2(0.0f), ey = bc2(0.0f), om;
+                if (SIG)
+                    closure_terms2(cs, cen, cr, cux, cuy, cth, wr, wux, wth, er, eux, eth, sr, suy, sth, nr, nuy, nth, ex,
+                                   ey, om);
+                const CellN1x2 c2{cr, cux, cuy, cth, mk2(A.s, B.s), mk2(A.mxx, B.mxx), mk2(A.myy, B.myy),
+                                  mk2(A.mxy, B.mxy)};
+                f2 axx, axy, ayy;
+                a1_next2<SIG>(cs, c2, dxux, dyux, dxuy, dyuy, ex, ey, axx, axy, ayy);
+                aa[0] = axx.x; aa[1] = axy.x; aa[2] = ayy.x;
+                ab[0] = axx.y; ab[1] = axy.y; ab[2] = ayy.y;
+            }
             const long long o = (long long)r * pitch + gx2;
             float *d = out + o;
             if (v3a && v3b) {
