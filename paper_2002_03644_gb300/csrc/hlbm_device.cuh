@@ -13,6 +13,11 @@
 // moments of F (collision invariants, eqs. rhoalgo, ualgo); theta follows
 // from s and rho.
 //
+// This file holds the tiled form of the step (FP64, and FP32 grids of up to
+// 768^2 cells) with the scalar cell arithmetic; hlbm_march.cuh holds the
+// row-marching form (the FP32 default on larger grids, the batched form's
+// marching shapes, and the moment-state form).
+//
 // One launch of fused_step_kernel performs Algorithm 1 steps 5-11 for a tile
 // of TX x TY cells:
 //   phase 0: s(n) on the tile plus a 3-cell halo -> shared memory
