@@ -15,7 +15,8 @@
 // keeps the pre-activation for the backward pass.
 //
 // Weight gradient: dW[co][ci][tap] = sum_pixels dz[pixel, co] *
-// h[pixel + offset(tap), ci], reduced in FP32 per block and added with
+// h[pixel + offset(tap), ci], a GEMM over pixels on the tensor cores
+// (BF16 operands, FP32 accumulators), added to the FP32 gradient with
 // atomics.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -204,67 +205,143 @@ conv_mma_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
     }
 }
 
-// dW[co][ci][tap] += sum over a chunk of pixels of dz[p, co] h[p + off(tap), ci]
-// in FP32 (real channels co < cout, ci < cin; arrays strided by the padded
-// counts), and db[co] += sum dz[p, co].  One block per (chunk, tap).
-__global__ void __launch_bounds__(256)
-wgrad_kernel(const __nv_bfloat16 *__restrict__ h, int cin_pad, int cin, const float *__restrict__ dz, int cout_pad,
-             int cout, int npix, int H, int W, int chunk, float *__restrict__ dW, float *__restrict__ db)
+__device__ __forceinline__ void ldsm_x4_t(uint32_t b[4], const void *p)
 {
-    constexpr int PER = MAXC * MAXC / 256;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]) : "r"(a));
+}
+
+// Weight gradient on the tensor cores: for one tap, dW[co][ci] += sum over
+// pixels p of dz[p, co] h[p + off(tap), ci], a GEMM with the pixels as its
+// K dimension (M = output channels, N = input channels).  BF16 tiles of dz
+// and of the shifted activations ([pixel][channel], rows padded by 8 for
+// conflict-free ldmatrix) are staged in shared memory and read transposed
+// into the A and B fragments of mma.sync m16n8k16; each of the 4 warps
+// accumulates a 32 x 32 block of the (at most) 64 x 64 result in FP32 over
+// its CTA's pixel chunk, then adds it to the FP32 gradient (real channels
+// only).  The bias gradient (tap 4 CTAs) sums the FP32 dz.  One CTA per
+// (chunk, tap).
+constexpr int WG_THREADS = 128, WG_KC = 64;
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(WG_THREADS)
+wgrad_mma_kernel(const __nv_bfloat16 *__restrict__ h, const __nv_bfloat16 *__restrict__ dzb,
+                 const float *__restrict__ dzf, int cin, int cout, int npix, int H, int W, int chunk,
+                 float *__restrict__ dW, float *__restrict__ db)
+{
+    constexpr int LDA = COUT + 8, LDB = CIN + 8;
+    constexpr int MT = COUT / 16, NTT = CIN / 8;
+    constexpr int CA = COUT / 8, CB = CIN / 8;  // 16-byte chunks per staged row
+    __shared__ __align__(16) __nv_bfloat16 sA[WG_KC * LDA];
+    __shared__ __align__(16) __nv_bfloat16 sB[WG_KC * LDB];
     const int tap = blockIdx.y;
+    const int dp = tap / 3 - 1, dq = tap % 3 - 1;
     const int p0 = blockIdx.x * chunk;
     const int p1 = min(p0 + chunk, npix);
-    const int dp = tap / 3 - 1, dq = tap % 3 - 1;
     const int HW = H * W;
-    __shared__ float sz[32][MAXC];
-    __shared__ float sh[32][MAXC + 1];
-    const int npair = cout * cin;
-    float acc[PER];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t4 = lane & 3, lj = lane >> 3, lr = lane & 7;
+    const int mt0 = 2 * (warp >> 1), nt0 = 4 * (warp & 1);
+    float acc[2][4][4];
 #pragma unroll
-    for (int k = 0; k < PER; k++) acc[k] = 0.0f;
-    float bacc = 0.0f;
-    for (int q0 = p0; q0 < p1; q0 += 32) {
-        const int nq = min(32, p1 - q0);
-        for (int e = threadIdx.x; e < 32 * MAXC; e += 256) {
-            const int r = e / MAXC, c = e - r * MAXC;
-            float vz = 0.0f, vh = 0.0f;
-            if (r < nq) {
-                const int p = q0 + r;
-                if (c < cout) vz = dz[(size_t)p * cout_pad + c];
-                if (c < cin) {
-                    const int n = p / HW, rem = p - n * HW, i = rem / W, j = rem - i * W;
-                    const int ii = wrap(i + dp, H), jj = wrap(j + dq, W);
-                    vh = __bfloat162float(h[((size_t)n * HW + (size_t)ii * W + jj) * cin_pad + c]);
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc[i][j][k] = 0.0f;
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    for (int q0 = p0; q0 < p1; q0 += WG_KC) {
+        __syncthreads();  // the previous sub-chunk's fragments are read
+        for (int e = threadIdx.x; e < WG_KC * CA; e += WG_THREADS) {
+            const int r = e / CA, c8 = e - r * CA;
+            const int p = q0 + r;
+            *reinterpret_cast<uint4 *>(sA + r * LDA + c8 * 8) =
+                p < p1 ? *reinterpret_cast<const uint4 *>(dzb + (size_t)p * COUT + c8 * 8) : zero;
+        }
+        for (int e = threadIdx.x; e < WG_KC * CB; e += WG_THREADS) {
+            const int r = e / CB, c8 = e - r * CB;
+            const int p = q0 + r;
+            uint4 v = zero;
+            if (p < p1) {
+                const int n = p / HW, rem = p - n * HW, i = rem / W, j = rem - i * W;
+                const int src = n * HW + wrap(i + dp, H) * W + wrap(j + dq, W);
+                v = *reinterpret_cast<const uint4 *>(h + (size_t)src * CIN + c8 * 8);
+            }
+            *reinterpret_cast<uint4 *>(sB + r * LDB + c8 * 8) = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k0 = 0; k0 < WG_KC; k0 += 16) {
+            uint32_t a[2][4];
+#pragma unroll
+            for (int mi = 0; mi < 2; mi++)
+                if (mt0 + mi < MT)
+                    ldsm_x4_t(a[mi], sA + (k0 + (lj >> 1) * 8 + lr) * LDA + (mt0 + mi) * 16 + (lj & 1) * 8);
+#pragma unroll
+            for (int ni = 0; ni < 4; ni += 2) {
+                if (nt0 + ni + 1 < NTT) {
+                    uint32_t b[4];
+                    ldsm_x4_t(b, sB + (k0 + (lj & 1) * 8 + lr) * LDB + (nt0 + ni) * 8 + (lj >> 1) * 8);
+#pragma unroll
+                    for (int mi = 0; mi < 2; mi++) {
+                        if (mt0 + mi < MT) {
+                            mma_bf16(acc[mi][ni], a[mi], b);
+                            mma_bf16(acc[mi][ni + 1], a[mi], b + 2);
+                        }
+                    }
                 }
             }
-            sz[r][c] = vz;
-            sh[r][c] = vh;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < PER; k++) {
-            const int pair = threadIdx.x + k * 256;
-            if (pair < npair) {
-                const int co = pair / cin, ci = pair - co * cin;
-                float sacc = 0.0f;
-                for (int r = 0; r < nq; r++) sacc += sz[r][co] * sh[r][ci];
-                acc[k] += sacc;
-            }
-        }
-        if (tap == 4 && (int)threadIdx.x < cout)
-            for (int r = 0; r < nq; r++) bacc += sz[r][threadIdx.x];
-        __syncthreads();
-    }
-#pragma unroll
-    for (int k = 0; k < PER; k++) {
-        const int pair = threadIdx.x + k * 256;
-        if (pair < npair) {
-            const int co = pair / cin, ci = pair - co * cin;
-            atomicAdd(&dW[((size_t)co * cin + ci) * 9 + tap], acc[k]);
         }
     }
-    if (tap == 4 && (int)threadIdx.x < cout) atomicAdd(&db[threadIdx.x], bacc);
+#pragma unroll
+    for (int mi = 0; mi < 2; mi++) {
+#pragma unroll
+        for (int ni = 0; ni < 4; ni++) {
+            if (mt0 + mi >= MT || nt0 + ni >= NTT) continue;
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const int co = (mt0 + mi) * 16 + g + 8 * r, ci = (nt0 + ni) * 8 + 2 * t4 + e;
+                    if (co < cout && ci < cin) atomicAdd(&dW[((size_t)co * cin + ci) * 9 + tap], acc[mi][ni][2 * r + e]);
+                }
+        }
+    }
+    if (tap == 4 && (int)threadIdx.x < cout) {
+        float bacc = 0.0f;
+        for (int p = p0; p < p1; p++) bacc += dzf[(size_t)p * COUT + threadIdx.x];
+        atomicAdd(&db[threadIdx.x], bacc);
+    }
+}
+
+template <int CIN>
+cudaError_t launch_wgrad_cin(int cout_pad, const __nv_bfloat16 *h, const __nv_bfloat16 *dzb, const float *dzf, int cin,
+                             int cout, int npix, int H, int W, float *dW, float *db, cudaStream_t st)
+{
+    const int chunk = 16384;
+    dim3 grid((npix + chunk - 1) / chunk, 9);
+    switch (cout_pad) {
+    case 16: wgrad_mma_kernel<CIN, 16><<<grid, WG_THREADS, 0, st>>>(h, dzb, dzf, cin, cout, npix, H, W, chunk, dW, db); break;
+    case 32: wgrad_mma_kernel<CIN, 32><<<grid, WG_THREADS, 0, st>>>(h, dzb, dzf, cin, cout, npix, H, W, chunk, dW, db); break;
+    case 48: wgrad_mma_kernel<CIN, 48><<<grid, WG_THREADS, 0, st>>>(h, dzb, dzf, cin, cout, npix, H, W, chunk, dW, db); break;
+    case 64: wgrad_mma_kernel<CIN, 64><<<grid, WG_THREADS, 0, st>>>(h, dzb, dzf, cin, cout, npix, H, W, chunk, dW, db); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// cin_pad, cout_pad: padded channel counts (multiples of 16)
+cudaError_t launch_wgrad(int cin_pad, int cout_pad, const __nv_bfloat16 *h, const __nv_bfloat16 *dzb, const float *dzf,
+                         int cin, int cout, int npix, int H, int W, float *dW, float *db, cudaStream_t st)
+{
+    switch (cin_pad) {
+    case 16: return launch_wgrad_cin<16>(cout_pad, h, dzb, dzf, cin, cout, npix, H, W, dW, db, st);
+    case 32: return launch_wgrad_cin<32>(cout_pad, h, dzb, dzf, cin, cout, npix, H, W, dW, db, st);
+    case 48: return launch_wgrad_cin<48>(cout_pad, h, dzb, dzf, cin, cout, npix, H, W, dW, db, st);
+    case 64: return launch_wgrad_cin<64>(cout_pad, h, dzb, dzf, cin, cout, npix, H, W, dW, db, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // y = x + net(x) with the FP32 input x, loss = mean((y - t)^2),
@@ -582,12 +659,10 @@ int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss_out)
     if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
     int gb = 0;
     for (int l = L - 1; l >= 0; l--) {
-        const int chunk = 4096;
-        dim3 grid((npix + chunk - 1) / chunk, 9);
-        wgrad_kernel<<<grid, 256, 0, s->stream>>>(s->act[l], s->cpad_in[l], s->width[l], dzf[cur], s->cpad_out[l],
-                                                  s->width[l + 1], npix, s->H, s->W, chunk, s->g + s->woff[l],
-                                                  s->g + s->boff[l]);
-        if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+        // weight gradient on the tensor cores from the BF16 copy of dz_l
+        if (launch_wgrad(s->cpad_in[l], s->cpad_out[l], s->act[l], s->gbuf[gb], dzf[cur], s->width[l], s->width[l + 1],
+                         npix, s->H, s->W, s->g + s->woff[l], s->g + s->boff[l], s->stream) != cudaSuccess)
+            return HLBM_ERR_CUDA;
         if (l == 0) break;
         // dz_{l-1} = (W_l^T * dz_l) . GELU'(z_{l-1}): the transposed
         // convolution on the tensor cores (dz read at p - offset(tap)),

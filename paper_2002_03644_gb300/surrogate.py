@@ -81,9 +81,11 @@ def make_dataset_device(nsamples, n=256, K=16, pairs_per_run=4, seed=0, mu=1e-4,
         for q in range(4):
             dst[..., q] = f64[q]
 
+    s = None
     while filled < nsamples:
         case = inputs.random_fourier(n=n, seed=seed * 100003 + run, mu=mu)
-        s = hlbm.Solver(n, n, stream=stream, precision=hlbm.HLBM_FP32, **case.params())
+        if s is None:  # every run shares the parameters: one handle, re-initialised per run
+            s = hlbm.Solver(n, n, stream=stream, precision=hlbm.HLBM_FP32, **case.params())
         s.init(*case.fields())
         grab(s, X[filled])
         for k in range(pairs_per_run):
@@ -94,8 +96,9 @@ def make_dataset_device(nsamples, n=256, K=16, pairs_per_run=4, seed=0, mu=1e-4,
                 break
             if k + 1 < pairs_per_run:
                 X[filled].copy_(Y[filled - 1])
-        s.close()
         run += 1
+    if s is not None:
+        s.close()
     return X, Y
 
 
