@@ -46,10 +46,13 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+@pytest.mark.parametrize("shape", [(2, 12, 20), (2, 9, 256)], ids=["12x20", "9x256"])
 @pytest.mark.parametrize("widths", [(4, 16, 16, 4), (4, 32, 64, 32, 4)])
-def test_forward_and_gradients_match_reference(env, widths):
+def test_forward_and_gradients_match_reference(env, widths, shape):
+    """Forward outputs and gradients against the FP64 reference on a small
+    image and on one as wide as the surrogate's 256^2 grid."""
     torch, hlbm, surrogate = env
-    B, H, W = 2, 12, 20
+    B, H, W = shape
     sur = surrogate.Surrogate(widths, H, W, batch_max=B, seed=3)
     p = sur.params()
     rng = np.random.default_rng(5)
