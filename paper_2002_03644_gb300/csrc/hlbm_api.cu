@@ -241,14 +241,31 @@ static cudaError_t launch_tma(hlbm_handle *h)
     return cudaGetLastError();
 }
 
-// Row-marching kernel (paired columns, see hlbm_march.cuh).  Its row
-// segments are cut so that the grid fills the GPU once (resident CTAs per
-// SM x SMs, from the occupancy calculator), at most kMarchMaxRows and at
-// least kMarchMinRows rows high.  HLBM_MARCH_ROWS=<n> fixes the height.
+// Row-marching kernel (paired columns, see hlbm_march.cuh); its row
+// segments come from march_segments().
 constexpr int kNumMarch = 4;
 constexpr int kMarchMinRows = 8;
 constexpr int kMarchMaxRows = 32;
 constexpr long long kMarchMinCells = 768ll * 768ll;  // GB300 sweep: tiled faster up to 768^2, marching at 1024^2
+
+// Row segments per strip: the fewest whole waves of resident CTAs (per_sm x
+// SMs) whose segments are at most kMarchMaxRows high, cut as finely as that
+// number of waves allows, so that no wave runs part-empty; at least
+// kMarchMinRows rows per segment.  HLBM_MARCH_ROWS=<n> fixes the height.
+static int march_segments(const hlbm_handle *h, long long strips, int per_sm, int sms)
+{
+    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    const long long least = (h->p.ny + kMarchMaxRows - 1) / kMarchMaxRows;
+    const long long waves = (strips * least + cap - 1) / cap;
+    long long nseg = (waves > 0 ? waves : 1) * cap / strips;
+    if (nseg < least) nseg = least;
+    const long long most = h->p.ny / kMarchMinRows > 0 ? h->p.ny / kMarchMinRows : 1;
+    if (nseg > most) nseg = most;
+    const int rows = env_choice("HLBM_MARCH_ROWS", 0, 1, 1 << 20);
+    if (rows > 0) nseg = (h->p.ny + rows - 1) / rows;
+    if (nseg > 65535) nseg = 65535;
+    return (int)(nseg > 0 ? nseg : 1);
+}
 
 // Paired-column marching kernel with NT threads (strips of 2 (NT - 4)
 // columns), register budget set by MINB resident CTAs per SM; the
@@ -275,17 +292,7 @@ static cudaError_t pair_setup(hlbm_handle *h)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
-    const long long strips = (h->p.nx + G::W - 1) / G::W;
-    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * sms;
-    long long nseg = (cap + strips - 1) / strips;
-    const long long least = (h->p.ny + kMarchMaxRows - 1) / kMarchMaxRows;
-    if (nseg < least) nseg = least;
-    const long long most = h->p.ny / kMarchMinRows > 0 ? h->p.ny / kMarchMinRows : 1;
-    if (nseg > most) nseg = most;
-    const int rows = env_choice("HLBM_MARCH_ROWS", 0, 1, 1 << 20);
-    if (rows > 0) nseg = (h->p.ny + rows - 1) / rows;
-    if (nseg > 65535) nseg = 65535;
-    h->march_nseg = (int)(nseg > 0 ? nseg : 1);
+    h->march_nseg = march_segments(h, (h->p.nx + G::W - 1) / G::W, per_sm, sms);
     return cudaSuccess;
 }
 
@@ -369,17 +376,7 @@ static cudaError_t setup_moments(hlbm_handle *h)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
-    const long long strips = (h->p.nx + G::W - 1) / G::W;
-    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * sms;
-    long long nseg = (cap + strips - 1) / strips;
-    const long long least = (h->p.ny + kMarchMaxRows - 1) / kMarchMaxRows;
-    if (nseg < least) nseg = least;
-    const long long most = h->p.ny / kMarchMinRows > 0 ? h->p.ny / kMarchMinRows : 1;
-    if (nseg > most) nseg = most;
-    const int rows = env_choice("HLBM_MARCH_ROWS", 0, 1, 1 << 20);
-    if (rows > 0) nseg = (h->p.ny + rows - 1) / rows;
-    if (nseg > 65535) nseg = 65535;
-    h->march_nseg = (int)(nseg > 0 ? nseg : 1);
+    h->march_nseg = march_segments(h, (h->p.nx + G::W - 1) / G::W, per_sm, sms);
     return cudaSuccess;
 }
 
