@@ -435,6 +435,134 @@ struct ConvArgs {
     int npix, H, W, mode, flip;
 };
 
+// Staged form for images whose width is a multiple of STG_TW: a CTA of 4
+// warps computes one 128-pixel segment of one image row.  It copies the
+// three input rows a 3x3 tap reaches (periodic wrap, one pixel of halo on
+// each side) into shared memory once with cp.async, and streams the
+// weights one tap at a time through a double buffer (the copy of tap t+1
+// overlaps the MMAs of tap t); both operands are read by ldmatrix.  Each
+// warp computes 32 pixels x NOUT outputs.
+constexpr int STG_TW = 128, STG_THREADS = 128;
+
+template <int CIN, int NOUT>
+struct StagedConvGeom {
+    static constexpr int LDI = CIN + 8, LDB = CIN + 8, RW = STG_TW + 2;
+    static constexpr size_t in_elems = (size_t)3 * RW * LDI;
+    static constexpr size_t w_elems = (size_t)NOUT * LDB;  // one tap
+    static constexpr size_t smem_bytes = (in_elems + 2 * w_elems) * sizeof(__nv_bfloat16);
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int CIN, int NOUT>
+__global__ void __launch_bounds__(STG_THREADS)
+conv_staged_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ B,
+                   const float *__restrict__ bias, int nbias, __nv_bfloat16 *__restrict__ out_bf,
+                   float *__restrict__ z_f32, const float *__restrict__ zprev, int H, int W, int mode, int flip)
+{
+    using G = StagedConvGeom<CIN, NOUT>;
+    constexpr int NT = NOUT / 8, LDI = G::LDI, LDB = G::LDB, RW = G::RW, CH = CIN / 8;
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    __nv_bfloat16 *Is = reinterpret_cast<__nv_bfloat16 *>(conv_smem);  // [3][RW][LDI]
+    __nv_bfloat16 *Ws = Is + G::in_elems;                               // [2][NOUT][LDB]
+    const int nseg = W / STG_TW;
+    const int seg = blockIdx.x % nseg, row = blockIdx.x / nseg;  // row = n H + i
+    const int n = row / H, i = row - n * H;
+    const int j0 = seg * STG_TW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t4 = lane & 3, lj = lane >> 3, lr = lane & 7;
+    // input rows i-1 .. i+1, columns j0-1 .. j0+STG_TW (wrapped)
+    for (int e = threadIdx.x; e < 3 * RW * CH; e += STG_THREADS) {
+        const int rr = e / (RW * CH), rem = e - rr * RW * CH;
+        const int cc = rem / CH, c8 = rem - cc * CH;
+        const int ii = wrap(i + rr - 1, H), jj = wrap(j0 + cc - 1, W);
+        cp_async16(Is + (rr * RW + cc) * LDI + c8 * 8, in + (((size_t)n * H + ii) * W + jj) * CIN + c8 * 8);
+    }
+    auto load_w = [&](int tap, int buf) {
+        for (int e = threadIdx.x; e < NOUT * CH; e += STG_THREADS) {
+            const int r = e / CH, c8 = e - r * CH;
+            cp_async16(Ws + buf * G::w_elems + r * LDB + c8 * 8, B + ((size_t)tap * NOUT + r) * CIN + c8 * 8);
+        }
+    };
+    load_w(0, 0);
+    cp_async_commit();
+    float acc[2][NT][4];
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int q = 0; q < NT; q++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc[m][q][k] = 0.0f;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; tap++) {
+        cp_async_wait0();
+        __syncthreads();  // tap's weights (and the input rows) are in; tap-1's buffer is free
+        if (tap + 1 < 9) {
+            load_w(tap + 1, (tap + 1) & 1);
+            cp_async_commit();
+        }
+        int dp = tap / 3 - 1, dq = tap % 3 - 1;
+        if (flip) { dp = -dp; dq = -dq; }
+        const __nv_bfloat16 *rowp = Is + (1 + dp) * RW * LDI;
+        const __nv_bfloat16 *Bt = Ws + (tap & 1) * G::w_elems;
+#pragma unroll
+        for (int k0 = 0; k0 < CIN; k0 += 16) {
+            uint32_t a[2][4];
+#pragma unroll
+            for (int m = 0; m < 2; m++)
+                ldsm_x4(a[m], rowp + (32 * warp + 16 * m + (lj & 1) * 8 + lr + 1 + dq) * LDI + k0 + (lj >> 1) * 8);
+#pragma unroll
+            for (int q = 0; q < NT; q += 2) {
+                if (q + 1 < NT) {
+                    uint32_t b[4];
+                    ldsm_x4(b, Bt + (q * 8 + (lj >> 1) * 8 + lr) * LDB + k0 + (lj & 1) * 8);
+#pragma unroll
+                    for (int m = 0; m < 2; m++) {
+                        mma_bf16(acc[m][q], a[m], b);
+                        mma_bf16(acc[m][q + 1], a[m], b + 2);
+                    }
+                } else {
+                    uint32_t b[2];
+                    ldsm_x2(b, Bt + (q * 8 + lr) * LDB + k0 + (lj & 1) * 8);
+#pragma unroll
+                    for (int m = 0; m < 2; m++) mma_bf16(acc[m][q], a[m], b);
+                }
+            }
+        }
+    }
+    const size_t rowpix = (size_t)row * W + j0 + 32 * warp;
+#pragma unroll
+    for (int m = 0; m < 2; m++) {
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const size_t p = rowpix + 16 * m + g + 8 * r;
+#pragma unroll
+            for (int q = 0; q < NT; q++) {
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const int col = q * 8 + 2 * t4 + e;
+                    float z = acc[m][q][2 * r + e] + ((bias && col < nbias) ? bias[col] : 0.0f);
+                    const size_t idx = p * NOUT + col;
+                    if (mode == 2) {
+                        if (zprev) z *= gelu_grad_f(zprev[idx]);
+                        out_bf[idx] = __float2bfloat16_rn(z);
+                        if (z_f32) z_f32[idx] = z;
+                    } else {
+                        if (z_f32) z_f32[idx] = z;
+                        out_bf[idx] = __float2bfloat16_rn(mode == 1 ? gelu_f(z) : z);
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Persistent grid: two CTAs per SM (the weights of a 64 x 64 layer take
 // 81 KB of shared memory), at most one CTA per 256-pixel tile.
 template <int CIN, int NOUT>
@@ -450,6 +578,19 @@ cudaError_t launch_conv_t(const ConvArgs &a, cudaStream_t st)
             e = cudaFuncSetAttribute(conv_mma_kernel<CIN, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)G::smem_bytes);
         if (e != cudaSuccess) { sms = 0; return e; }
+    }
+    if (a.W % STG_TW == 0 && a.npix % (a.H * a.W) == 0) {
+        using S = StagedConvGeom<CIN, NOUT>;
+        static bool staged_ready = false;
+        if (!staged_ready) {
+            const cudaError_t e = cudaFuncSetAttribute(conv_staged_kernel<CIN, NOUT>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
+            if (e != cudaSuccess) return e;
+            staged_ready = true;
+        }
+        conv_staged_kernel<CIN, NOUT><<<a.npix / STG_TW, STG_THREADS, S::smem_bytes, st>>>(
+            a.in, a.B, a.bias, a.nbias, a.out, a.z, a.zprev, a.H, a.W, a.mode, a.flip);
+        return cudaGetLastError();
     }
     const int tiles = (a.npix + CONV_THREADS - 1) / CONV_THREADS;
     const int blocks = tiles < 2 * sms ? tiles : 2 * sms;
