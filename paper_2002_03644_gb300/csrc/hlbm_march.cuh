@@ -656,28 +656,6 @@ struct MomGeom {
     static constexpr size_t smem_bytes = sizeof(float) * (size_t)N;
 };
 
-// E_x, E_y (E1 upwind or centred, plus E2) and omega of one cell from its
-// macros and those of its four neighbours (the collision's first half).
-template <typename T>
-__device__ __forceinline__ void closure_terms(const Consts<T> &cs, bool cen, T rho, T ux, T uy, T th, T rW, T uxW,
-                                              T thW, T rE, T uxE, T thE, T rS, T uyS, T thS, T rN, T uyN, T thN,
-                                              T &ex, T &ey, T &omega)
-{
-    const T third = T(1) / T(3);
-    const T dxux = T(0.5) * (uxE - uxW);
-    const T dyuy = T(0.5) * (uyN - uyS);
-    const T p = rho * th * third;
-    const T gxc = gamma_defect(rho, ux, th), gyc = gamma_defect(rho, uy, th);
-    const T gxm = gamma_defect(rW, uxW, thW), gxp = gamma_defect(rE, uxE, thE);
-    const T gym = gamma_defect(rS, uyS, thS), gyp = gamma_defect(rN, uyN, thN);
-    const T e1xx = (ux > T(0) && !cen) ? gxc - gxm : ((ux < T(0) && !cen) ? gxp - gxc : T(0.5) * (gxp - gxm));
-    const T e1yy = (uy > T(0) && !cen) ? gyc - gym : ((uy < T(0) && !cen) ? gyp - gyc : T(0.5) * (gyp - gym));
-    const T e2 = p * cs.two_m_gamma * (dxux + dyuy);
-    ex = e1xx + e2;
-    ey = e1yy + e2;
-    omega = fdiv(cs.two_mu - p, cs.two_mu + p);
-}
-
 template <int NT, bool SIG, bool PHI0>
 __device__ __forceinline__ void moment_segment(const float *__restrict__ in, float *__restrict__ out,
                                                const KParams &kp, const int x0, const int ys, const int ye,

@@ -189,7 +189,8 @@ __device__ __forceinline__ CellN1x2 level_np1_2(const Consts<float> &cs, f2 rho0
     return o;
 }
 
-// E_x, E_y and omega of two cells (closure_terms).
+// E_x, E_y (E1 upwind or centred, plus E2) and omega of two cells from their
+// macros and those of their four neighbours (the first half of collide_cell).
 __device__ __forceinline__ void closure_terms2(const Consts<float> &cs, bool cen, f2 rho, f2 ux, f2 uy, f2 th, f2 rW,
                                                f2 uxW, f2 thW, f2 rE, f2 uxE, f2 thE, f2 rS, f2 uyS, f2 thS, f2 rN,
                                                f2 uyN, f2 thN, f2 &ex, f2 &ey, f2 &omega)
