@@ -519,7 +519,7 @@ def run_surrogate(args):
     # held-out error (normalised fields) of the surrogate and of y = x
     errs, errs_id, mse, mse_id = [], [], [], []
     for b0 in range(ntrain, Xn.shape[0] - batch + 1, batch):
-        pred = sur.forward(Xn[b0:b0 + batch].contiguous())
+        pred = sur.predict(Xn[b0:b0 + batch].contiguous())
         d, d0 = pred - Yn[b0:b0 + batch], Xn[b0:b0 + batch] - Yn[b0:b0 + batch]
         errs.append(float(d.abs().max())); errs_id.append(float(d0.abs().max()))
         mse.append(float((d * d).mean())); mse_id.append(float((d0 * d0).mean()))
@@ -527,13 +527,13 @@ def run_surrogate(args):
     x = Xn[:batch].contiguous()
     y = torch.empty_like(x)
     for _ in range(3):
-        sur.forward(x, y)
+        sur.predict(x, y)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 10
     e0.record(stream)
     for _ in range(reps):
-        sur.forward(x, y)
+        sur.predict(x, y)
     e1.record(stream)
     torch.cuda.synchronize()
     t_sur = e0.elapsed_time(e1) / 1e3 / (reps * batch)

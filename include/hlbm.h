@@ -231,6 +231,10 @@ int hlbm_sur_set_params(hlbm_sur *s, const float *params, int mem_kind);  /* res
 int hlbm_sur_get_params(hlbm_sur *s, float *params, float *grads, int mem_kind);
 /* y = x + net(x) for B samples (B <= batch_max); y may be NULL */
 int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B);
+/* Inference: y = x + net(x) like hlbm_sur_forward, keeping no FP32
+ * pre-activations of the hidden layers (they only serve the backward pass),
+ * so hlbm_sur_backward cannot follow it (HLBM_ERR_ARG).  y may be NULL. */
+int hlbm_sur_predict(hlbm_sur *s, const float *x, float *y, int B);
 /* after hlbm_sur_forward: gradients of mean((y - target)^2); *loss if non-NULL */
 int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss);
 int hlbm_sur_adam(hlbm_sur *s, float lr, float beta1, float beta2, float eps);

@@ -755,7 +755,9 @@ int hlbm_sur_get_params(hlbm_sur *s, float *params, float *grads, int mem_kind)
 }
 
 // x: device FP32 [B, H, W, C0] (NHWC); y: device FP32 [B, H, W, C0] or NULL.
-int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B)
+// keep_z: store every layer's FP32 pre-activation (for the backward pass);
+// otherwise only the last layer's, which the residual output needs.
+static int sur_run(hlbm_sur *s, const float *x, float *y, int B, bool keep_z)
 {
     if (!s || !x || B < 1 || B > s->bmax) return HLBM_ERR_ARG;
     const int npix = B * s->H * s->W;
@@ -765,8 +767,8 @@ int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B)
     if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
     for (int l = 0; l < s->L; l++) {
         const bool last = l == s->L - 1;
-        const ConvArgs a{s->act[l], s->Wb[l], s->p + s->boff[l], s->width[l + 1], s->act[l + 1], s->z[l], nullptr,
-                         npix, s->H, s->W, last ? 0 : 1, 0};
+        const ConvArgs a{s->act[l], s->Wb[l], s->p + s->boff[l], s->width[l + 1], s->act[l + 1],
+                         (keep_z || last) ? s->z[l] : nullptr, nullptr, npix, s->H, s->W, last ? 0 : 1, 0};
         if (launch_conv(s->cpad_in[l], s->cpad_out[l], a, s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
     }
     residual_loss_kernel<<<1024, 256, 0, s->stream>>>(s->xin, s->z[s->L - 1], s->cpad_out[s->L - 1], nullptr,
@@ -774,9 +776,14 @@ int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B)
     if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
     if (y && cudaMemcpyAsync(y, s->y, (size_t)npix * s->width[0] * 4, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
         return HLBM_ERR_CUDA;
-    s->last_batch = B;
+    s->last_batch = keep_z ? B : 0;
     return HLBM_OK;
 }
+
+int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B) { return sur_run(s, x, y, B, true); }
+
+// Inference only: the hidden layers' pre-activations are not stored.
+int hlbm_sur_predict(hlbm_sur *s, const float *x, float *y, int B) { return sur_run(s, x, y, B, false); }
 
 // After hlbm_sur_forward on the same batch: loss = mean((y - target)^2)
 // (target FP32 NHWC [B, H, W, C0] on the device) and the gradient of every

@@ -33,6 +33,7 @@ ENTRY_POINTS = (
     "hlbm_batch_create", "hlbm_batch_case", "hlbm_batch_step", "hlbm_batch_autotune", "hlbm_batch_tile",
     "hlbm_batch_destroy",
     "hlbm_sur_create", "hlbm_sur_param_count", "hlbm_sur_set_params", "hlbm_sur_get_params", "hlbm_sur_forward",
+    "hlbm_sur_predict",
     "hlbm_sur_backward", "hlbm_sur_adam", "hlbm_sur_synchronize", "hlbm_sur_destroy",
 )
 HLBM_NOALLOC_MAX_CELLS = 16777216
@@ -145,6 +146,8 @@ def _lib():
         lib.hlbm_sur_get_params.argtypes = [_P, _PD, _PD, ctypes.c_int]
         lib.hlbm_sur_forward.restype = ctypes.c_int
         lib.hlbm_sur_forward.argtypes = [_P, _PD, _PD, ctypes.c_int]
+        lib.hlbm_sur_predict.restype = ctypes.c_int
+        lib.hlbm_sur_predict.argtypes = [_P, _PD, _PD, ctypes.c_int]
         lib.hlbm_sur_backward.restype = ctypes.c_int
         lib.hlbm_sur_backward.argtypes = [_P, _PD, ctypes.POINTER(ctypes.c_double)]
         lib.hlbm_sur_adam.restype = ctypes.c_int
@@ -397,6 +400,11 @@ def hlbm_sur_get_params(s, params=None, grads=None):
 def hlbm_sur_forward(s, x, y, batch):
     """x, y: CUDA float32 tensors [B, H, W, C] (y may be None)."""
     _check(_lib().hlbm_sur_forward(s, x.data_ptr(), None if y is None else y.data_ptr(), int(batch)))
+
+
+def hlbm_sur_predict(s, x, y, batch):
+    """Inference (no pre-activations kept): x, y CUDA float32 tensors [B, H, W, C]."""
+    _check(_lib().hlbm_sur_predict(s, x.data_ptr(), None if y is None else y.data_ptr(), int(batch)))
 
 
 def hlbm_sur_backward(s, target):

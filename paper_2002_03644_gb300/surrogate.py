@@ -177,6 +177,15 @@ class Surrogate:
         hlbm.hlbm_sur_forward(self.s, x, y, x.shape[0])
         return y
 
+    def predict(self, x, y=None):
+        """Inference only: like forward, without keeping the pre-activations
+        a backward pass needs."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        hlbm.hlbm_sur_predict(self.s, x, y, x.shape[0])
+        return y
+
     def train_step(self, x, target, lr):
         hlbm.hlbm_sur_forward(self.s, x, None, x.shape[0])
         loss = hlbm.hlbm_sur_backward(self.s, target)
@@ -215,7 +224,7 @@ def hybrid_rollout(sur, norm, case, calls, K=16, judge_every=8, tol=None, stream
     log = []
     for k in range(calls):
         x = torch.from_numpy(norm.fwd(state)[None].astype(np.float32)).cuda()
-        y = norm.inv(sur.forward(x)[0].double().cpu().numpy())
+        y = norm.inv(sur.predict(x)[0].double().cpu().numpy())
         if (k + 1) % judge_every == 0:
             s = hlbm.Solver(n, n, stream=stream, precision=hlbm.HLBM_FP32, **case.params())
             s.init(*[np.ascontiguousarray(state[..., q]) for q in range(4)])

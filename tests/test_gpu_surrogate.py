@@ -127,3 +127,20 @@ def test_training_beats_persistence_and_hybrid_rollout(env):
     assert len(log) == 2 and all(back for _, _, back in log)  # tol so small that the HLBM always takes over
     assert np.isfinite(state).all()
     sur.close()
+
+
+@pytest.mark.parametrize("shape", [(2, 12, 20), (2, 9, 256)], ids=["12x20", "9x256"])
+def test_predict_equals_forward_and_blocks_backward(env, shape):
+    """Inference keeps no hidden pre-activations but computes the same
+    outputs; a backward pass after it is refused."""
+    torch, hlbm, surrogate = env
+    B, H, W = shape
+    sur = surrogate.Surrogate((4, 32, 64, 32, 4), H, W, batch_max=B, seed=5)
+    x = torch.from_numpy(np.random.default_rng(6).normal(size=(B, H, W, 4)).astype(np.float32)).cuda()
+    yf = sur.forward(x).cpu().numpy()
+    yp = sur.predict(x).cpu().numpy()
+    assert np.array_equal(yf, yp)
+    with pytest.raises(hlbm.HlbmError) as e:
+        hlbm.hlbm_sur_backward(sur.s, x)
+    assert e.value.code == hlbm.HLBM_ERR_ARG
+    sur.close()
