@@ -29,6 +29,13 @@
  *    (rho, u, theta) with a1 = 0 and populations at equilibrium.  Ghosts of a
  *    level are refilled from the interior of the same level.  At corners a
  *    Dirichlet y side wins, then a Dirichlet x side, else both axes are mapped.
+ *    Wall sides (y sides only) are no-slip, fixed-temperature walls half-way
+ *    between the first ghost row and the first interior row: ghost row g
+ *    mirrors interior row g - 1 with rho equal, u reflected about the wall
+ *    velocity (u_g = 2 u_w - u) and theta about the wall temperature
+ *    (theta_g = 2 theta_w - theta), s from that rho and theta, and ghost
+ *    populations rebuilt by the regularised formula of the collision from
+ *    the ghost macros and the mirrored cell's a1, without psi.
  *    Parity unpinned for the boundary forms: the paper defers them to an
  *    earlier work that is not available.
  */
@@ -41,7 +48,7 @@
 #define CS2 (1.0 / 3.0)          /* c_s^2, Sec. 2.1 */
 #define DIM 2
 
-enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_DIRICHLET = 2 };
+enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_DIRICHLET = 2, BC_WALL = 3 };
 
 /* D2Q9 velocities and weights, Sec. 2.1 */
 static const int CX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -259,7 +266,7 @@ typedef struct {
     int nx, ny, px, py;
     double gamma, Pr, mu, sigma;
     int bc[4];              /* x-, x+, y-, y+ */
-    double bcs[4][4];       /* Dirichlet (rho, ux, uy, theta) per side */
+    double bcs[4][4];       /* Dirichlet (rho, ux, uy, theta) or wall (-, ux, uy, theta) per side */
     int phi_mode;           /* 0: Phi from a1 (eq viscous heat discret), 1: finite differences */
     int ablation;           /* bit 1: centred E1, bit 2: no E2 (parts of the original model) */
     double cv, cp, lambda;
@@ -305,11 +312,13 @@ static void fill_ghosts(const hlbmo *o, double *a, const double dv[4])
             switch (o->bc[2]) {
             case BC_PERIODIC: a[IX(o, x, yl)] = a[IX(o, x, wrap(yl, o->ny))]; break;
             case BC_ZEROGRAD: a[IX(o, x, yl)] = a[IX(o, x, 0)]; break;
+            case BC_WALL: break;  /* fill_wall_macros / wall_populations */
             default: a[IX(o, x, yl)] = dv[2];
             }
             switch (o->bc[3]) {
             case BC_PERIODIC: a[IX(o, x, yr)] = a[IX(o, x, wrap(yr, o->ny))]; break;
             case BC_ZEROGRAD: a[IX(o, x, yr)] = a[IX(o, x, o->ny - 1)]; break;
+            case BC_WALL: break;
             default: a[IX(o, x, yr)] = dv[3];
             }
         }
@@ -327,6 +336,35 @@ static void fill_macros(hlbmo *o, double *rho, double *ux, double *uy, double *t
     side_values(o, 1, dv); fill_ghosts(o, ux, dv);
     side_values(o, 2, dv); fill_ghosts(o, uy, dv);
     side_values(o, 3, dv); fill_ghosts(o, th, dv);
+}
+
+/* Wall side k (2: y-, 3: y+): ghost row g (1 or 2) and the interior row it
+ * mirrors about the wall, which lies half-way between row -1 and row 0 (or
+ * between rows ny - 1 and ny). */
+static int wall_ghost_row(const hlbmo *o, int k, int g) { return k == 2 ? -g : o->ny - 1 + g; }
+static int wall_mirror_row(const hlbmo *o, int k, int g) { return k == 2 ? g - 1 : o->ny - g; }
+
+static double entropy_of(const hlbmo *o, double rho, double th);
+
+/* Ghost macros of the wall sides over the full padded width (the x ghosts
+ * of the mirrored rows are filled first, so a wall wins at a corner): rho
+ * mirrored, u reflected about the wall velocity, theta about the wall
+ * temperature, s of the ghost rho and theta. */
+static void fill_wall_macros(hlbmo *o, double *rho, double *ux, double *uy, double *th, double *s)
+{
+    for (int k = 2; k < 4; k++) {
+        if (o->bc[k] != BC_WALL) continue;
+        const double uw = o->bcs[k][1], vw = o->bcs[k][2], tw = o->bcs[k][3];
+        for (int g = 1; g <= G; g++)
+            for (int x = -G; x < o->nx + G; x++) {
+                const int kg = IX(o, x, wall_ghost_row(o, k, g)), km = IX(o, x, wall_mirror_row(o, k, g));
+                ux[kg] = 2.0 * uw - ux[km];
+                uy[kg] = 2.0 * vw - uy[km];
+                th[kg] = 2.0 * tw - th[km];
+                rho[kg] = rho[km] * th[km] / th[kg];
+                s[kg] = entropy_of(o, rho[kg], th[kg]);
+            }
+    }
 }
 
 static double *alloc_field(const hlbmo *o)
@@ -361,6 +399,10 @@ hlbmo *hlbmo_create(int nx, int ny, double gamma, double Pr, double mu, double s
     for (int k = 0; k < 4; k++) {
         o->bc[k] = bc[k];
         for (int q = 0; q < 4; q++) o->bcs[k][q] = bc_state ? bc_state[4 * k + q] : 0.0;
+        if (bc[k] < BC_PERIODIC || bc[k] > BC_WALL) { free(o); return NULL; }
+        /* walls on the y sides only, with a positive temperature and two
+         * interior rows to mirror */
+        if (bc[k] == BC_WALL && (k < 2 || ny < 2 || !(o->bcs[k][3] > 0.0))) { free(o); return NULL; }
     }
     /* c_v = c_s^2/(gamma-1), c_p = gamma c_s^2/(gamma-1) (Sec. 2.4).
      * Heat conductivity lambda = mu c_p / Pr, the definition of the Prandtl
@@ -484,6 +526,7 @@ int hlbmo_init(hlbmo *o, const double *rho0, const double *ux0, const double *uy
         }
     fill_macros(o, o->rho, o->ux, o->uy, o->th);
     fill_ghosts(o, o->s, o->b_s);
+    fill_wall_macros(o, o->rho, o->ux, o->uy, o->th, o->s);
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             const int c = y * o->nx + x, k = IX(o, x, y);
@@ -507,6 +550,30 @@ int hlbmo_init(hlbmo *o, const double *rho0, const double *ux0, const double *uy
     return 0;
 }
 
+/* Post-collision populations of the wall ghost rows: the regularised
+ * formula of eq streamalgo from the ghost macros of level n and the a1 of
+ * the mirrored cell (a Dirichlet x ghost has a1 = 0), without psi. */
+static void wall_populations(hlbmo *o)
+{
+    const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+    fill_ghosts(o, o->axx, zero);
+    fill_ghosts(o, o->axy, zero);
+    fill_ghosts(o, o->ayy, zero);
+    for (int k = 2; k < 4; k++) {
+        if (o->bc[k] != BC_WALL) continue;
+        for (int g = 1; g <= G; g++)
+            for (int x = -G; x < o->nx + G; x++) {
+                const int kg = IX(o, x, wall_ghost_row(o, k, g)), km = IX(o, x, wall_mirror_row(o, k, g));
+                const double p = o->rho[kg] * CS2 * o->th[kg];
+                const double taub = o->mu / p + 0.5;
+                double feq[Q], f1[Q];
+                hlbmo_feq_cell(o->rho[kg], o->ux[kg], o->uy[kg], o->th[kg], feq);
+                hlbmo_f1_cell(o->axx[km], o->axy[km], o->ayy[km], o->ux[kg], o->uy[kg], o->th[kg], f1);
+                for (int i = 0; i < Q; i++) o->F[i][kg] = feq[i] + (1.0 - 1.0 / taub) * f1[i];
+            }
+    }
+}
+
 /* Algorithm 1, step 5 for every interior cell: F_i = f^eq_i + (1 - 1/tau_bar)
  * f1_i + psi_i / 2 (eq streamalgo), the post-collision populations of level n. */
 static void collide(hlbmo *o)
@@ -526,6 +593,7 @@ static void collide(hlbmo *o)
         for (int s = 0; s < 4; s++) dv[s] = o->b_feq[s][i];
         fill_ghosts(o, o->F[i], dv);
     }
+    if (o->bc[2] == BC_WALL || o->bc[3] == BC_WALL) wall_populations(o);
 }
 
 /* Entropy right-hand side of eq (sequaalgo) at level n (Algorithm 1, step 7):
@@ -610,6 +678,7 @@ int hlbmo_step(hlbmo *o, long nsteps)
             }
         fill_macros(o, o->rho1, o->ux1, o->uy1, o->th1);
         fill_ghosts(o, o->s1, o->b_s);
+        fill_wall_macros(o, o->rho1, o->ux1, o->uy1, o->th1, o->s1);
         /* step 9: psi at n+1 */
         compute_psi(o, o->rho1, o->ux1, o->uy1, o->th1, o->psi1);
         /* step 10: f^eq at n+1 */

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "hlbm_oracle.c")
 LIB = os.path.join(HERE, "libhlbm_oracle.so")
 
-BC_PERIODIC, BC_ZEROGRAD, BC_DIRICHLET = 0, 1, 2
+BC_PERIODIC, BC_ZEROGRAD, BC_DIRICHLET, BC_WALL = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None

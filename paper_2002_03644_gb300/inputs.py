@@ -193,21 +193,31 @@ def acoustic_wave(nx=200, ny=2, dp_rel=5.0 / 101325.0, theta0=300.0 / 1478.75, g
                 sigma=sigma, steps=steps, meta=dict(k=2.0 * math.pi / nx, c=c, dp=dp_rel * p_inf))
 
 
-def couette(ny=100, nx=2, Ma=0.8, gamma=1.4, Pr=0.71, mu=0.1, sigma=0.9, theta_w=300.0 / 1500.0, steps=70000):
+def couette(ny=100, nx=2, Ma=0.8, gamma=1.4, Pr=0.71, mu=0.1, sigma=0.9, theta_w=300.0 / 1500.0, steps=70000,
+            walls="wall"):
     """Thermal Couette flow (Sec. 4.4): gas at rest and at the wall
     temperature between a wall at rest (the y- side) and a wall moving along
-    x at U = Ma c (the y+ side), both held at theta_w as Dirichlet sides;
-    periodic in x.  T_r = 1500 K and T_w = 300 K give theta_w = 0.2; sigma =
-    0.9 as in the paper.  The walls sit at the centres of the Dirichlet ghost
-    rows, so the plates are H = ny + 1 apart and cell j lies at y = j + 1."""
+    x at U = Ma c (the y+ side), both at theta_w; periodic in x.  T_r = 1500 K
+    and T_w = 300 K give theta_w = 0.2; sigma = 0.9 as in the paper.
+
+    walls="wall": wall sides, half-way between the ghost and the first
+    interior row, so the plates are H = ny apart and cell j lies at
+    y = j + 1/2.  walls="dirichlet": Dirichlet sides whose ghost-row centres
+    are the plates, H = ny + 1 and cell j at y = j + 1."""
     c = math.sqrt(gamma * theta_w * CS2)
     U = Ma * c
     shape = (ny, nx)
     bc_state = np.array([[1.0, 0.0, 0.0, theta_w], [1.0, 0.0, 0.0, theta_w],
                          [1.0, 0.0, 0.0, theta_w], [1.0, U, 0.0, theta_w]])
+    if walls == "wall":
+        side, H, y0 = BC_WALL, float(ny), 0.5
+    elif walls == "dirichlet":
+        side, H, y0 = BC_DIRICHLET, ny + 1.0, 1.0
+    else:
+        raise ValueError(walls)
     return Case("couette", nx, ny, np.ones(shape), np.zeros(shape), np.zeros(shape), np.full(shape, theta_w),
-                gamma=gamma, Pr=Pr, mu=mu, sigma=sigma, bc=(BC_PERIODIC, BC_PERIODIC, BC_DIRICHLET, BC_DIRICHLET),
-                bc_state=bc_state, steps=steps, meta=dict(U=U, H=ny + 1.0, Ma=Ma, theta_w=theta_w))
+                gamma=gamma, Pr=Pr, mu=mu, sigma=sigma, bc=(BC_PERIODIC, BC_PERIODIC, side, side),
+                bc_state=bc_state, steps=steps, meta=dict(U=U, H=H, y0=y0, Ma=Ma, theta_w=theta_w))
 
 
 def gaussian_pulse_1d(nx=200, ny=2, width=20.0, dp_rel=1e-4, theta0=300.0 / 1478.75, gamma=1.4,

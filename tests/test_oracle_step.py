@@ -8,7 +8,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle.oracle import BC_DIRICHLET, BC_PERIODIC, BC_ZEROGRAD, Oracle
+from oracle.oracle import BC_DIRICHLET, BC_PERIODIC, BC_WALL, BC_ZEROGRAD, Oracle
 from paper_2002_03644_gb300 import inputs
 
 CS2 = 1.0 / 3.0
@@ -35,6 +35,54 @@ def test_uniform_state_is_fixed_point(bc):
     assert np.abs(m["uy"] + 0.1).max() < 1e-14
     assert np.abs(m["theta"] - 0.3).max() < 1e-14
     assert np.abs(m["a1"]).max() < 1e-15
+
+
+@pytest.mark.parametrize("xbc", [BC_PERIODIC, BC_ZEROGRAD])
+@pytest.mark.parametrize("U", [0.0, 0.15])
+def test_walls_keep_a_uniform_flow_along_them(xbc, U):
+    """Gas at the wall temperature moving with both walls: every ghost row
+    equals the interior state, so the state is a fixed point."""
+    bs = np.array([[1.0, 0.0, 0.0, 0.25]] * 4)
+    bs[2:, 1] = U
+    c = inputs.uniform(6, 5, rho=1.1, ux=U, uy=0.0, theta=0.25, mu=2e-3, sigma=0.6,
+                       bc=(xbc, xbc, BC_WALL, BC_WALL), bc_state=bs)
+    m = run(c, 30).macros()
+    assert np.abs(m["rho"] - 1.1).max() < 1e-13
+    assert np.abs(m["ux"] - U).max() < 1e-14
+    assert np.abs(m["uy"]).max() < 1e-14
+    assert np.abs(m["theta"] - 0.25).max() < 1e-14
+
+
+@pytest.mark.parametrize("xbc", [(BC_PERIODIC, BC_PERIODIC), (BC_ZEROGRAD, BC_DIRICHLET)])
+def test_wall_sides_are_mirror_symmetric(xbc):
+    """Flipping the grid in y (v negated) and swapping the two walls gives
+    the flipped solution: a wrong mirror row or ghost depth on one side
+    breaks it."""
+    bs = np.array([[1.05, 0.03, 0.01, 0.21], [0.97, -0.02, 0.0, 0.2],
+                   [1.0, 0.04, 0.0, 0.19], [1.0, -0.06, 0.0, 0.22]])
+    c = inputs.random_smooth(9, 8, seed=17, amp=0.05, u0=(0.05, 0.02), theta0=0.2, mu=3e-3, sigma=0.5,
+                             bc=xbc + (BC_WALL, BC_WALL), bc_state=bs)
+    a = run(c, 25).macros()
+    f = inputs.Case("flip", c.nx, c.ny, c.rho[::-1].copy(), c.ux[::-1].copy(), -c.uy[::-1], c.theta[::-1].copy(),
+                    gamma=c.gamma, Pr=c.Pr, mu=c.mu, sigma=c.sigma, bc=c.bc,
+                    bc_state=bs[[0, 1, 3, 2]] * np.array([1.0, 1.0, -1.0, 1.0]))
+    f.bc_state[:2] = bs[:2] * np.array([1.0, 1.0, -1.0, 1.0])
+    b = run(f, 25).macros()
+    for k, sgn in (("rho", 1), ("ux", 1), ("uy", -1), ("theta", 1), ("s", 1)):
+        assert np.abs(a[k] - sgn * b[k][::-1]).max() < 1e-12, k
+    for q, sgn in ((0, 1), (1, -1), (2, 1)):
+        assert np.abs(a["a1"][q] - sgn * b["a1"][q][::-1]).max() < 1e-12, q
+
+
+def test_wall_sides_are_checked():
+    bs = np.array([[1.0, 0.0, 0.0, 0.2]] * 4)
+    with pytest.raises(ValueError):
+        Oracle(5, 4, bc=(BC_WALL, BC_WALL, BC_PERIODIC, BC_PERIODIC), bc_state=bs)  # x walls
+    with pytest.raises(ValueError):
+        Oracle(5, 1, bc=(BC_PERIODIC, BC_PERIODIC, BC_WALL, BC_WALL), bc_state=bs)  # one row
+    bs[2, 3] = 0.0
+    with pytest.raises(ValueError):
+        Oracle(5, 4, bc=(BC_PERIODIC, BC_PERIODIC, BC_WALL, BC_WALL), bc_state=bs)  # theta_w = 0
 
 
 def test_dirichlet_sides_holding_the_same_state_keep_a_uniform_flow():
