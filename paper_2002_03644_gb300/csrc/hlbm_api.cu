@@ -66,6 +66,8 @@ struct hlbm_handle {
     int tile_variant = 0;
     int march_variant = -1;     // row-marching kernel variant, -1: tiled / TMA kernels
     bool moments = false;       // HLBM_FP32_MOMENTS: 7 FP32 planes, moment-state kernel
+    bool walls = false;         // a wall side: tiled kernel plus wall_ghost_kernel each step
+    void *wall_g = nullptr;     // wall ghost rows (KParams::wall_g)
     int march_nseg = 1;         // row segments per strip
     int *d_err = nullptr;       // device-side timeout flag of the TMA kernel
     int64_t step = 0;
@@ -395,9 +397,26 @@ static cudaError_t launch_moments(hlbm_handle *h)
     return cudaGetLastError();
 }
 
+// Level-n ghost rows of the wall sides, from the current state.
+static cudaError_t launch_wall_ghosts(hlbm_handle *h)
+{
+    return with_types(h, [&](auto ty) {
+        using T = typename decltype(ty)::t;
+        using S = typename decltype(ty)::s;
+        dim3 grid((h->kp.wall_p + 127) / 128, 4);
+        wall_ghost_kernel<T, S><<<grid, 128, 0, h->stream>>>(pop_planes<T, S>(h, h->cur), aux_planes<T, S>(h, h->cur),
+                                                             h->kp);
+        return cudaGetLastError();
+    });
+}
+
 static cudaError_t launch_one_step(hlbm_handle *h)
 {
     if (h->moments) return launch_moments(h);
+    if (h->walls) {
+        const cudaError_t e = launch_wall_ghosts(h);
+        if (e != cudaSuccess) return e;
+    }
     using F32 = FullStore<float>;
     if (h->march_variant >= 0) {
         return with_types(h, [&](auto ty) {
@@ -462,9 +481,16 @@ static int validate(const hlbm_params *p)
         return HLBM_ERR_ARG;
     if (!std::isfinite(p->gamma) || !std::isfinite(p->Pr) || !std::isfinite(p->mu)) return HLBM_ERR_ARG;
     for (int k = 0; k < 4; k++) {
-        if (p->bc[k] < HLBM_BC_PERIODIC || p->bc[k] > HLBM_BC_DIRICHLET) return HLBM_ERR_UNSUPPORTED;
+        if (p->bc[k] < HLBM_BC_PERIODIC || p->bc[k] > HLBM_BC_WALL) return HLBM_ERR_UNSUPPORTED;
         if (p->bc[k] == HLBM_BC_DIRICHLET && (!(p->bc_state[k][0] > 0.0) || !(p->bc_state[k][3] > 0.0)))
             return HLBM_ERR_ARG;
+        if (p->bc[k] == HLBM_BC_WALL) {
+            // y sides only, two interior rows to mirror, a positive temperature
+            if (k < 2) return HLBM_ERR_UNSUPPORTED;
+            if (p->ny < 2 || !(p->bc_state[k][3] > 0.0)) return HLBM_ERR_ARG;
+            if (!std::isfinite(p->bc_state[k][1]) || !std::isfinite(p->bc_state[k][2])) return HLBM_ERR_ARG;
+            if (p->precision == HLBM_FP32_MOMENTS) return HLBM_ERR_UNSUPPORTED;
+        }
     }
     // a periodic side needs a periodic partner
     if ((p->bc[0] == HLBM_BC_PERIODIC) != (p->bc[1] == HLBM_BC_PERIODIC)) return HLBM_ERR_ARG;
@@ -496,6 +522,11 @@ static void fill_kparams(hlbm_handle *h)
     k.e1_centred = (p.ablation & HLBM_ABL_CENTRED_E1) ? 1 : 0;
     k.gamma = p.gamma;
     for (int s = 0; s < 4; s++) {
+        if (p.bc[s] == HLBM_BC_WALL) {
+            // wall velocity and temperature (the density is not imposed)
+            k.d_ux[s] = p.bc_state[s][1]; k.d_uy[s] = p.bc_state[s][2]; k.d_th[s] = p.bc_state[s][3];
+            continue;
+        }
         if (p.bc[s] != HLBM_BC_DIRICHLET) continue;
         const double r = p.bc_state[s][0], u = p.bc_state[s][1], v = p.bc_state[s][2], t = p.bc_state[s][3];
         k.d_rho[s] = r; k.d_ux[s] = u; k.d_uy[s] = v; k.d_th[s] = t;
@@ -551,6 +582,7 @@ void hlbm_destroy(hlbm_handle *h)
     cudaFree(h->diag_partial);
     cudaFree(h->diag_out);
     cudaFree(h->d_err);
+    cudaFree(h->wall_g);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -600,6 +632,22 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         return HLBM_ERR_CUDA;
     }
     fill_kparams(h);
+    h->walls = params->bc[2] == HLBM_BC_WALL || params->bc[3] == HLBM_BC_WALL;
+    if (h->walls) {
+        // ghost rows for the tiled kernel; walls never take the marching or
+        // TMA kernels
+        const size_t wb = (size_t)kWallPlanes * 4 * (params->nx + 4) * h->asize;
+        if (cudaMalloc(&h->wall_g, wb) != cudaSuccess) {
+            cudaGetLastError();
+            hlbm_destroy(h);
+            return HLBM_ERR_NOMEM;
+        }
+        h->kp.wall_g = h->wall_g;
+        h->kp.wall_p = params->nx + 4;
+        h->tile_variant = env_choice("HLBM_FP32_TILE", 4, 0, kNumFp32Tiles);
+        *out = h;
+        return HLBM_OK;
+    }
     if (h->moments) {
         if (setup_moments(h) != cudaSuccess) {
             cudaGetLastError();
@@ -1095,8 +1143,10 @@ int hlbm_batch_create(const hlbm_params *params, int ncase, void *stream, hlbm_b
 {
     if (!out || !params || ncase < 1) return HLBM_ERR_ARG;
     *out = nullptr;
-    for (int c = 0; c < ncase; c++)
+    for (int c = 0; c < ncase; c++) {
         if (params[c].precision != HLBM_FP32) return HLBM_ERR_UNSUPPORTED;
+        if (params[c].bc[2] == HLBM_BC_WALL || params[c].bc[3] == HLBM_BC_WALL) return HLBM_ERR_UNSUPPORTED;
+    }
     hlbm_batch *b = new (std::nothrow) hlbm_batch();
     if (!b) return HLBM_ERR_NOMEM;
     if (cudaGetDevice(&b->device) != cudaSuccess) { delete b; return HLBM_ERR_CUDA; }

@@ -41,6 +41,15 @@
 // the domain is the value at the mapped cell; for clamped sides it is copied
 // from the tile's own edge after phase 2.  A Dirichlet y side wins at a
 // corner, then a Dirichlet x side.
+// Wall sides (y only, tiled kernel): a no-slip, fixed-temperature wall
+// half-way between the first ghost row and the first interior row.  Ghost
+// row g mirrors interior row g - 1: u reflected about the wall velocity,
+// theta about the wall temperature, the pressure of the mirrored cell
+// (rho_g theta_g = rho theta), s of that rho and theta, and post-collision
+// populations rebuilt from them and the mirrored cell's a1 by the collision
+// formula without psi.  wall_ghost_kernel writes the level-n ghost rows to a
+// small buffer before each step; the level-(n+1) ghosts are mirrored inside
+// the tile after phase 2.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -52,7 +61,7 @@ namespace hlbm {
 
 constexpr int NPLANE = 13;
 constexpr int P_S = 9, P_AXX = 10, P_AXY = 11, P_AYY = 12;
-enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_DIRICHLET = 2 };
+enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_DIRICHLET = 2, BC_WALL = 3 };
 
 struct KParams {
     int nx, ny, pitch;
@@ -74,6 +83,11 @@ struct KParams {
     // reference populations subtracted before 16-bit storage (precision
     // forms HLBM_FP32_F16POP / HLBM_FP32_BF16POP; unused otherwise)
     float f_ref[9];
+    // wall ghost rows of level n (arithmetic type): 10 planes (F_0..F_8, s)
+    // of 4 rows (y- depth 1, 2; y+ depth 1, 2) of wall_p = nx + 4 columns
+    // (x = -2 .. nx + 1); null without wall sides
+    void *wall_g;
+    int wall_p;
 };
 
 // ---- population storage ----------------------------------------------------------
@@ -162,6 +176,32 @@ __device__ __forceinline__ int locate(int gx, int gy, const KParams &kp, int pit
         gx = (b == BC_PERIODIC) ? wrapi(gx, kp.nx) : (gx < 0 ? 0 : kp.nx - 1);
     }
     return gy * pitch + gx;
+}
+
+// locate() with wall sides: a coordinate beyond a wall maps to the wall
+// ghost buffer, returned as -(kWallCode + index) with index = row * wall_p +
+// x + 2 (row = (side - 2) * 2 + depth - 1; the depth is clamped to 2 and x
+// to [-2, nx + 1], which covers every ghost value a tile reads).
+constexpr int kWallCode = 8;
+constexpr int kWallPlanes = 10;
+__device__ __forceinline__ int locate_w(int gx, int gy, const KParams &kp, int pitch)
+{
+    if (gy < 0 || gy >= kp.ny) {
+        const int s = gy < 0 ? 2 : 3;
+        if (kp.bc[s] == BC_WALL) {
+            const int d = min(gy < 0 ? -gy : gy - kp.ny + 1, 2);
+            const int x = min(max(gx, -2), kp.nx + 1);
+            return -(kWallCode + ((s - 2) * 2 + d - 1) * kp.wall_p + x + 2);
+        }
+    }
+    return locate(gx, gy, kp, pitch);
+}
+
+// Plane q (0..8 populations, 9 entropy) of wall ghost index w.
+template <typename T>
+__device__ __forceinline__ T wall_val(const KParams &kp, int w, int q)
+{
+    return static_cast<const T *>(kp.wall_g)[(size_t)q * 4 * kp.wall_p + w];
 }
 
 // ---- FP32 hardware approximations ------------------------------------------
@@ -282,12 +322,14 @@ struct TileGeom {
 };
 
 // Classification of a tile + 1 cell for phase 2: 0 compute, 1 Dirichlet
-// constant (side in *side), 2 copy from the clamped cell.
+// constant (side in *side), 2 copy from the clamped cell, 3 mirror of the
+// interior cell across a wall.
 __device__ __forceinline__ int classify_r1(int gx, int gy, const KParams &kp, int *side)
 {
     const bool outx = gx < 0 || gx >= kp.nx, outy = gy < 0 || gy >= kp.ny;
     if (!outx && !outy) return 0;
-    const int o = locate(gx, gy, kp, kp.pitch);
+    const int o = locate_w(gx, gy, kp, kp.pitch);
+    if (o <= -kWallCode) return 3;
     if (o < 0) { *side = -o - 1; return 1; }
     const bool cx = outx && kp.bc[gx < 0 ? 0 : 1] == BC_ZEROGRAD;
     const bool cy = outy && kp.bc[gy < 0 ? 2 : 3] == BC_ZEROGRAD;
@@ -356,8 +398,9 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
     for (int c = threadIdx.x; c < N3; c += NT) {
         const int ly = c / R3X, lx = c - ly * R3X;
         const int gx = x0 - 3 + lx, gy = y0 - 3 + ly;
-        const int o = interior ? gy * pitch + gx : locate(gx, gy, kp, pitch);
-        sS[c] = o >= 0 ? __ldg(inA + A_S * P + o) : side.s_(-o - 1);
+        const int o = interior ? gy * pitch + gx : locate_w(gx, gy, kp, pitch);
+        sS[c] = o >= 0 ? __ldg(inA + A_S * P + o)
+                       : (o > -kWallCode ? side.s_(-o - 1) : wall_val<T>(kp, -o - kWallCode, 9));
     }
     {
         constexpr int ITER = (N2 + NT - 1) / NT;
@@ -370,14 +413,17 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
             if (c < N2) {
                 const int ly = c / R2X, lx = c - ly * R2X;
                 const int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
-                const int o = interior ? gy * pitch + gx : locate(gx, gy, kp, pitch);
+                const int o = interior ? gy * pitch + gx : locate_w(gx, gy, kp, pitch);
                 oc[it] = o;
                 if (o >= 0) {
 #pragma unroll
                     for (int i = 0; i < 9; i++) f[it][i] = S::get(inF[i * P + o], i, kp);
-                } else {
+                } else if (o > -kWallCode) {
 #pragma unroll
                     for (int i = 0; i < 9; i++) f[it][i] = side.F(-o - 1, i);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; i++) f[it][i] = wall_val<T>(kp, -o - kWallCode, i);
                 }
             }
         }
@@ -400,8 +446,9 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
         bool dirichlet = false;
         int sd = 0;
         if (!interior) {
-            const int o = locate(x0 - 2 + lx, y0 - 2 + ly, kp, pitch);
-            if (o < 0) { dirichlet = true; sd = -o - 1; }
+            // wall ghosts take their macros from their populations like cells
+            const int o = locate_w(x0 - 2 + lx, y0 - 2 + ly, kp, pitch);
+            if (o < 0 && o > -kWallCode) { dirichlet = true; sd = -o - 1; }
         }
         if (!dirichlet) {
             T f[9];
@@ -431,7 +478,7 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
                 nTh[c] = side.th(sd); nS[c] = side.s_(sd);
                 continue;
             }
-            if (kind == 2) continue;
+            if (kind >= 2) continue;
         }
         // a1(n) of this cell (phi_mode 0): issued first so the loads overlap
         // the stencil arithmetic below
@@ -492,6 +539,25 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
             nRho[c] = nRho[src]; nUx[c] = nUx[src]; nUy[c] = nUy[src]; nTh[c] = nTh[src]; nS[c] = nS[src];
         }
         __syncthreads();
+        if (kp.wall_g) {
+            // wall sides: mirror the first interior row (after the clamped
+            // copies, which the mirrored row may hold at a corner)
+            for (int c = threadIdx.x; c < N1; c += NT) {
+                const int ly = c / R1X, lx = c - ly * R1X;
+                const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+                int sd = 0;
+                if (classify_r1(gx, gy, kp, &sd) != 3) continue;
+                const int ws = gy < 0 ? 2 : 3;
+                const int src = c + (gy < 0 ? R1X : -R1X);  // rows 0 and ny - 1
+                const T th = T(2) * side.th(ws) - nTh[src];
+                nTh[c] = th;
+                nRho[c] = fdiv(nRho[src] * nTh[src], th);
+                nUx[c] = T(2) * side.ux(ws) - nUx[src];
+                nUy[c] = T(2) * side.uy(ws) - nUy[src];
+                nS[c] = T(0);  // not read: phase 3 uses the entropy of its own cell only
+            }
+            __syncthreads();
+        }
     }
 
     // phase 3: steps 9-11 and the collision of the next step on the tile
@@ -606,6 +672,57 @@ batched_step_kernel(const BatchTables tab, const int parity)
     }
 }
 
+// ---- wall ghost rows of level n --------------------------------------------------
+// One thread per ghost cell: x = -2 .. nx + 1 (blockIdx.x, threadIdx.x) and
+// row = (side - 2) * 2 + depth - 1 (blockIdx.y).  The mirrored cell's rho and
+// u are the moments of its F(n), theta follows from its s(n); an x ghost of
+// the mirrored row takes the x side's map (a Dirichlet x side gives its
+// constants and a1 = 0).
+template <typename T, typename S>
+__global__ void wall_ghost_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
+                                  const KParams kp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = blockIdx.y;
+    const int ws = 2 + row / 2, depth = row % 2 + 1;
+    if (i >= kp.wall_p || kp.bc[ws] != BC_WALL) return;
+    Consts<T> cs;
+    cs.load(kp);
+    const Side<T> side{kp};
+    const long long P = kp.plane;
+    const int o = locate(i - 2, ws == 2 ? depth - 1 : kp.ny - depth, kp, kp.pitch);
+    T rho, ux, uy, th, axx = T(0), axy = T(0), ayy = T(0);
+    if (o >= 0) {
+        T f[9];
+#pragma unroll
+        for (int q = 0; q < 9; q++) f[q] = S::get(inF[q * P + o], q, kp);
+        T jx, jy;
+        moments(f, rho, jx, jy);
+        const T ir = fdiv(T(1), rho);
+        ux = jx * ir;
+        uy = jy * ir;
+        th = cs.theta(rho, inA[A_S * P + o]);
+        axx = inA[A_XX * P + o];
+        axy = inA[A_XY * P + o];
+        ayy = inA[A_YY * P + o];
+    } else {
+        const int sd = -o - 1;
+        rho = side.rho(sd); ux = side.ux(sd); uy = side.uy(sd); th = side.th(sd);
+    }
+    const T tg = T(2) * side.th(ws) - th;
+    const T rg = fdiv(rho * th, tg);
+    const T ug = T(2) * side.ux(ws) - ux, vg = T(2) * side.uy(ws) - uy;
+    const T p = rho * th * (T(1) / T(3));
+    const T omega = fdiv(cs.two_mu - p, cs.two_mu + p);
+    T f[9];
+    build_populations(rg, ug, vg, tg, axx, axy, ayy, T(0), T(0), omega, f);
+    T *wg = static_cast<T *>(kp.wall_g);
+    const size_t w = (size_t)row * kp.wall_p + i, stride = (size_t)4 * kp.wall_p;
+#pragma unroll
+    for (int q = 0; q < 9; q++) wg[q * stride + w] = f[q];
+    wg[9 * stride + w] = (T)(kp.cv * (log((double)tg) - kp.gm1 * log((double)rg)));
+}
+
 // ---- initialisation (Algorithm 1, steps 1-4) -----------------------------------
 // In FP64 from FP64 caller fields (row-major [ny][nx]); writes the state in T.
 template <typename T, typename S>
@@ -619,9 +736,20 @@ __global__ void init_kernel(const double *__restrict__ rho, const double *__rest
     if (gx >= kp.nx || gy >= kp.ny) return;
     const int n = kp.nx * kp.ny;
     auto at = [&](int dx, int dy, double &r, double &u, double &v, double &t) {
-        const int o = locate(gx + dx, gy + dy, kp, kp.nx);
+        const int yy = gy + dy;
+        const bool wall = (yy < 0 || yy >= kp.ny) && kp.bc[yy < 0 ? 2 : 3] == BC_WALL;
+        // beyond a wall: the mirrored interior cell, reflected (see wall_ghost_kernel)
+        const int o = locate(gx + dx, wall ? (yy < 0 ? -yy - 1 : 2 * kp.ny - 1 - yy) : yy, kp, kp.nx);
         if (o >= 0) { r = rho[o]; u = ux[o]; v = uy[o]; t = th[o]; }
         else { const int s = -o - 1; r = kp.d_rho[s]; u = kp.d_ux[s]; v = kp.d_uy[s]; t = kp.d_th[s]; }
+        if (wall) {
+            const int ws = yy < 0 ? 2 : 3;
+            const double tg = 2.0 * kp.d_th[ws] - t;
+            r = r * t / tg;
+            t = tg;
+            u = 2.0 * kp.d_ux[ws] - u;
+            v = 2.0 * kp.d_uy[ws] - v;
+        }
     };
     double r0, u0, v0, t0, rxm, uxm, vxm, txm, rxp, uxp, vxp, txp, rym, uym, vym, tym, ryp, uyp, vyp, typ;
     at(0, 0, r0, u0, v0, t0);

@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 HLBM_FP64, HLBM_FP32, HLBM_FP32_F16POP, HLBM_FP32_BF16POP, HLBM_FP32_MOMENTS = 0, 1, 2, 3, 4
-HLBM_BC_PERIODIC, HLBM_BC_ZEROGRAD, HLBM_BC_DIRICHLET = 0, 1, 2
+HLBM_BC_PERIODIC, HLBM_BC_ZEROGRAD, HLBM_BC_DIRICHLET, HLBM_BC_WALL = 0, 1, 2, 3
 HLBM_MEM_HOST, HLBM_MEM_DEVICE = 0, 1
 HLBM_OK, HLBM_ERR_ARG, HLBM_ERR_CFL, HLBM_ERR_NONFINITE = 0, -1, -2, -3
 HLBM_ERR_CUDA, HLBM_ERR_STATE, HLBM_ERR_NOMEM, HLBM_ERR_UNSUPPORTED = -4, -5, -6, -7

@@ -89,6 +89,29 @@ def test_invalid_params_rejected_without_touching_the_gpu(lib):
         assert not h.value
 
 
+def test_wall_sides_validated_without_touching_the_gpu(lib):
+    """Walls: y sides only, ny >= 2, a positive wall temperature, no moment
+    state and no batches; each is refused before any CUDA call."""
+    from paper_2002_03644_gb300 import hlbm
+    W, P = hlbm.HLBM_BC_WALL, hlbm.HLBM_BC_PERIODIC
+    bs = [[1.0, 0.0, 0.0, 0.2]] * 4
+    cases = [(dict(bc=(W, W, P, P)), hlbm.HLBM_ERR_UNSUPPORTED),
+             (dict(bc=(P, P, W, W), ny=1), hlbm.HLBM_ERR_ARG),
+             (dict(bc=(P, P, W, W), bc_state=[[1.0, 0.0, 0.0, 0.2]] * 3 + [[1.0, 0.0, 0.0, 0.0]]), hlbm.HLBM_ERR_ARG),
+             (dict(bc=(P, P, W, W), precision=hlbm.HLBM_FP32_MOMENTS), hlbm.HLBM_ERR_UNSUPPORTED)]
+    for kw, want in cases:
+        args = dict(nx=8, ny=8, bc_state=bs)
+        args.update(kw)
+        p = hlbm.make_params(**args)
+        h = ctypes.c_void_p()
+        assert lib.hlbm_create(ctypes.byref(p), None, ctypes.byref(h)) == want, kw
+        assert not h.value
+    arr = (hlbm.hlbm_params * 1)(hlbm.make_params(8, 8, precision=hlbm.HLBM_FP32, bc=(P, P, W, W), bc_state=bs))
+    b = ctypes.c_void_p()
+    assert lib.hlbm_batch_create(arr, 1, None, ctypes.byref(b)) == hlbm.HLBM_ERR_UNSUPPORTED
+    assert not b.value
+
+
 def test_product_path_has_no_oracle_dependency():
     """The package never imports, links or runs anything under oracle/."""
     pkg = os.path.join(ROOT, "paper_2002_03644_gb300")
