@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -35,11 +36,57 @@ constexpr int MAXC = 64;  // widest layer (padded channels)
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU(x) = x Phi(x) = (x / 2) (1 + erf(x / sqrt 2)) and its derivative
+// Phi(x) + x phi(x), with erf from Abramowitz & Stegun, Handbook of
+// Mathematical Functions, formula 7.1.26: for z >= 0,
+//   erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2) + eps,
+//   t = 1 / (1 + p z), |eps| <= 1.5e-7,
+// extended to z < 0 by oddness.  With z = |x| / sqrt 2, exp(-z^2) is the
+// Gaussian factor phi(x) sqrt(2 pi) that the derivative needs as well.  The
+// reciprocal and the exponential are the PTX approximations (a few ulp); the
+// result is rounded to BF16 (8 bits) by every caller, far above these errors.
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_fast(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// r = (1 - erf(|x| / sqrt 2)) / 2 = Phi(-|x|) and e = exp(-x^2 / 2)
+__device__ __forceinline__ void normal_tail(float x, float &r, float &e)
+{
+    const float t = rcp_fast(fmaf(0.3275911f * 0.70710678118654752f, fabsf(x), 1.0f));
+    const float q = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                             0.254829592f);
+    e = ex2_fast(x * x * -0.72134752044448170f);  // exp(-x^2 / 2) = 2^(-x^2 / (2 ln 2))
+    r = 0.5f * q * e;
+}
+
+__device__ __forceinline__ float gelu_f(float x)
+{
+    float r, e;
+    normal_tail(x, r, e);
+    return x * (x >= 0.0f ? 1.0f - r : r);
+}
 
 __device__ __forceinline__ float gelu_grad_f(float x)
 {
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * __expf(-0.5f * x * x);
+    float r, e;
+    normal_tail(x, r, e);
+    return (x >= 0.0f ? 1.0f - r : r) + x * 0.3989422804014327f * e;
+}
+
+// Two floats rounded to BF16, low half first.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
 }
 
 __device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16 *p)
@@ -378,10 +425,20 @@ __global__ void residual_loss_kernel(const float *__restrict__ xin, const float 
 __global__ void pack_input_kernel(const float *__restrict__ x, int c_real, int cpad, int npix,
                                   __nv_bfloat16 *__restrict__ out)
 {
-    const long long n = (long long)npix * cpad;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int p = (int)(e / cpad), c = (int)(e - (long long)p * cpad);
-        out[e] = __float2bfloat16_rn(c < c_real ? x[(size_t)p * c_real + c] : 0.0f);
+    // one pixel per thread: c_real FP32 values in, cpad BF16 values out in
+    // 16-byte pieces (cpad is a multiple of 16)
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        const float *src = x + (size_t)p * c_real;
+        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)p * cpad);
+        for (int c0 = 0; c0 < cpad; c0 += 8) {
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int c = c0 + 2 * k;
+                w[k] = pack_bf16(c < c_real ? src[c] : 0.0f, c + 1 < c_real ? src[c + 1] : 0.0f);
+            }
+            dst[c0 / 8] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
     }
 }
 
@@ -544,27 +601,308 @@ conv_staged_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__
             const size_t p = rowpix + 16 * m + g + 8 * r;
 #pragma unroll
             for (int q = 0; q < NT; q++) {
-#pragma unroll
-                for (int e = 0; e < 2; e++) {
-                    const int col = q * 8 + 2 * t4 + e;
-                    float z = acc[m][q][2 * r + e] + ((bias && col < nbias) ? bias[col] : 0.0f);
-                    const size_t idx = p * NOUT + col;
-                    if (mode == 2) {
-                        if (zprev) z *= gelu_grad_f(zprev[idx]);
-                        out_bf[idx] = __float2bfloat16_rn(z);
-                        if (z_f32) z_f32[idx] = z;
-                    } else {
-                        if (z_f32) z_f32[idx] = z;
-                        out_bf[idx] = __float2bfloat16_rn(mode == 1 ? gelu_f(z) : z);
-                    }
+                // the two adjacent outputs of this thread, stored together
+                const int col = q * 8 + 2 * t4;
+                float z0 = acc[m][q][2 * r] + ((bias && col < nbias) ? bias[col] : 0.0f);
+                float z1 = acc[m][q][2 * r + 1] + ((bias && col + 1 < nbias) ? bias[col + 1] : 0.0f);
+                const size_t idx = p * NOUT + col;
+                if (mode == 2 && zprev) {
+                    const float2 zp = *reinterpret_cast<const float2 *>(zprev + idx);
+                    z0 *= gelu_grad_f(zp.x);
+                    z1 *= gelu_grad_f(zp.y);
                 }
+                if (z_f32) *reinterpret_cast<float2 *>(z_f32 + idx) = make_float2(z0, z1);
+                if (mode == 1) {
+                    z0 = gelu_f(z0);
+                    z1 = gelu_f(z1);
+                }
+                *reinterpret_cast<uint32_t *>(out_bf + idx) = pack_bf16(z0, z1);
             }
         }
     }
 }
 
+// ---- 5th-generation tensor cores (tcgen05, TMEM accumulators) ---------------------
+// The 64 -> 64 convolution on images whose width is a multiple of 128, as a
+// persistent kernel with one CTA of 16 warps per SM:
+//   - the nine taps' weights stay in shared memory for the whole launch;
+//   - each 128-pixel row segment is one M = 128 tile: the three input rows it
+//     reaches are copied into one of two shared-memory buffers, and one
+//     thread issues its 36 MMAs (9 taps x 4 K-slices of 16 channels,
+//     M = 128, N = 64, K = 16, BF16 operands) into one of two TMEM
+//     accumulators of 64 FP32 columns, with tcgen05.commit signalling an
+//     mbarrier when they are done;
+//   - while the MMAs of tile i run, all warps read tile i-1's accumulator
+//     (tcgen05.ld), apply bias / GELU and store, then copy tile i+1's input.
+// Operands use the canonical K-major layout without swizzle: 8-row x 16-byte
+// core matrices, rows 16 bytes apart, 8-row groups SBO = 128 bytes apart
+// (so consecutive pixels are consecutive 16-byte rows and a tap's pixel
+// shift is a plain 16-byte offset of the descriptor's start address), the
+// two 8-channel halves of a K-slice LBO bytes apart.
+constexpr int TC_THREADS = 512, TC_TW = 128, TC_CIN = 64, TC_NOUT = 64, TC_RW = TC_TW + 2;
+constexpr uint32_t TC_W_TAP = 8 * TC_NOUT * 16;          // one tap's weights: 8 channel chunks x 64 rows x 16 B
+constexpr uint32_t TC_W_BYTES = 9 * TC_W_TAP;            // 73728
+constexpr uint32_t TC_IN_LBO = TC_RW * 16;               // 2080: channel chunk stride of a staged row
+constexpr uint32_t TC_IN_ROW = 8 * TC_IN_LBO;            // 16640: one staged input row
+constexpr uint32_t TC_IN_BYTES = 3 * TC_IN_ROW;          // 49920
+constexpr uint32_t TC_BAR_OFF = TC_W_BYTES + 2 * TC_IN_BYTES;   // 173568: two mbarriers, then the TMEM address
+constexpr uint32_t TC_BIAS_OFF = TC_BAR_OFF + 32;                 // 64 FP32 bias values
+// Dynamic shared memory requested: the operands need 173.6 KB; the rest is
+// slack so that every address a descriptor can form stays inside the block.
+constexpr uint32_t TC_SMEM = 220 * 1024;
+constexpr uint32_t TC_TMEM_COLS = 2 * TC_NOUT;           // two accumulators
+constexpr long long TC_WAIT_CYCLES = 2000000000ll;       // about 1 s at 2 GHz
+
+// Set when an mbarrier wait of the tcgen05 kernel gave up (read by
+// hlbm_sur_synchronize).
+__device__ int g_tc_timeout = 0;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (all >> 4), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at
+// bit 24.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_NOUT >> 3) << 17) |
+                              ((uint32_t)(TC_TW >> 4) << 24);
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false (and the timeout flag set) after
+// about a second.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > TC_WAIT_CYCLES) {
+            atomicExch(&g_tc_timeout, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+// 16 TMEM columns of this warp's 32 lanes (one FP32 value per column).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+conv_tc_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ B,
+               const float *__restrict__ bias, int nbias, __nv_bfloat16 *__restrict__ out_bf,
+               float *__restrict__ z_f32, const float *__restrict__ zprev, int H, int W, int ntiles, int mode,
+               int flip)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    const uint32_t sbase = smem_addr(tc_smem);
+    const uint32_t w_s = sbase;
+    auto in_s = [&](int b) { return sbase + TC_W_BYTES + b * TC_IN_BYTES; };
+    auto bar = [&](int b) { return sbase + TC_BAR_OFF + 8 * b; };
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + TC_BAR_OFF + 16);
+    float *bias_s = reinterpret_cast<float *>(tc_smem + TC_BIAS_OFF);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nseg = W / TC_TW;
+    if (tid < TC_NOUT) bias_s[tid] = (bias && tid < nbias) ? bias[tid] : 0.0f;
+
+    // TMEM for the two accumulators (one warp allocates), the mbarriers
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(TC_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(0)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(1)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // weights of all taps: B[tap][n][k] -> [tap][k / 8][n][8]
+    for (int e = tid; e < 9 * TC_NOUT * 8; e += TC_THREADS) {
+        const int tap = e >> 9, rem = e & 511, nrow = rem >> 3, kc = rem & 7;
+        cp_async16(tc_smem + tap * TC_W_TAP + kc * (TC_NOUT * 16) + nrow * 16,
+                   B + ((size_t)tap * TC_NOUT + nrow) * TC_CIN + kc * 8);
+    }
+    // input rows i-1 .. i+1, columns j0-1 .. j0+128 of a tile -> [row][k / 8][column][8]:
+    // thread t copies channel chunk t % 8 of columns t / 8 + 64 m (m = 0, 1, 2)
+    const int s_kc = tid & 7, s_px = tid >> 3;
+    auto stage = [&](int tile, int buf) {
+        const int seg = tile % nseg, row = tile / nseg;
+        const int n = row / H, i = row - n * H, j0 = seg * TC_TW;
+        unsigned char *dst = tc_smem + TC_W_BYTES + buf * TC_IN_BYTES + s_kc * TC_IN_LBO;
+#pragma unroll
+        for (int rr = 0; rr < 3; rr++) {
+            const __nv_bfloat16 *src = in + ((size_t)n * H + wrap(i + rr - 1, H)) * W * TC_CIN + s_kc * 8;
+#pragma unroll
+            for (int m = 0; m < 3; m++) {
+                const int px = s_px + 64 * m;
+                if (px < TC_RW) cp_async16(dst + rr * TC_IN_ROW + px * 16, src + (size_t)wrap(j0 + px - 1, W) * TC_CIN);
+            }
+        }
+    };
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (my_tiles > 0) stage(blockIdx.x, 0);
+    cp_async_commit();
+    cp_async_wait0();
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    // epilogue of local tile k (accumulator k & 1): warp w reads TMEM lanes
+    // 32 (w % 4) .. +31 (pixels) and columns 16 (w / 4) .. +15 (outputs)
+    // Once tile k's MMAs are complete, its input buffer is free: tile k + 2's
+    // input is copied into it right away, overlapping the epilogue math.
+    auto epilogue = [&](int k) -> bool {
+        const int tile = blockIdx.x + k * gridDim.x;
+        // the warp-wide TMEM load below needs the whole warp: agree on the outcome
+        if (!__all_sync(0xffffffffu, mbar_wait(bar(k & 1), (k >> 1) & 1))) return false;
+        if (k + 2 < my_tiles) stage(blockIdx.x + (k + 2) * gridDim.x, k & 1);
+        cp_async_commit();
+        tc_fence_after();
+        const int q = warp & 3, h = warp >> 2;
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (k & 1) * TC_NOUT + 16 * h, v);
+        const size_t p = (size_t)tile * TC_TW + 32 * q + lane;  // tile = row * nseg + seg
+        const size_t o = p * TC_NOUT + 16 * h;                      // this thread's 16 outputs
+#pragma unroll
+        for (int c = 0; c < 16; c++) v[c] += bias_s[16 * h + c];
+        if (mode == 2 && zprev) {
+            const float4 *zp = reinterpret_cast<const float4 *>(zprev + o);
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float4 g = zp[c];
+                v[4 * c + 0] *= gelu_grad_f(g.x);
+                v[4 * c + 1] *= gelu_grad_f(g.y);
+                v[4 * c + 2] *= gelu_grad_f(g.z);
+                v[4 * c + 3] *= gelu_grad_f(g.w);
+            }
+        }
+        if (z_f32) {
+            float4 *zd = reinterpret_cast<float4 *>(z_f32 + o);
+#pragma unroll
+            for (int c = 0; c < 4; c++) zd[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        }
+        if (mode == 1) {
+#pragma unroll
+            for (int c = 0; c < 16; c++) v[c] = gelu_f(v[c]);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(out_bf + o);
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            uint4 u;
+            u.x = pack_bf16(v[8 * c + 0], v[8 * c + 1]);
+            u.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
+            u.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
+            u.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
+            dst[c] = u;
+        }
+        return true;
+    };
+
+    // descriptors of tap 0, K-slice 0; the others differ only in the start
+    // address field (low 14 bits, in 16-byte units), by compile-time offsets
+    const uint64_t adesc0[2] = {umma_desc(in_s(0), TC_IN_LBO, 128), umma_desc(in_s(1), TC_IN_LBO, 128)};
+    const uint64_t bdesc0 = umma_desc(w_s, TC_NOUT * 16, 128);
+    auto issue = [&](int b, bool flipped) {
+        const uint32_t d = tmem + b * TC_NOUT;
+        const uint64_t a0 = b ? adesc0[1] : adesc0[0];
+#pragma unroll
+        for (int tap = 0; tap < 9; tap++) {
+            const int dp = flipped ? 1 - tap / 3 : tap / 3 - 1, dq = flipped ? 1 - tap % 3 : tap % 3 - 1;
+#pragma unroll
+            for (int ks = 0; ks < 4; ks++) {
+                const uint32_t ao = ((1 + dp) * TC_IN_ROW + (1 + dq) * 16 + 2 * ks * TC_IN_LBO) >> 4;
+                const uint32_t bo = (tap * TC_W_TAP + 2 * ks * (TC_NOUT * 16)) >> 4;
+                umma_f16(d, a0 + ao, bdesc0 + bo, TC_IDESC, (tap | ks) != 0);
+            }
+        }
+        umma_commit(bar(b));
+    };
+
+    // tile 1's input (tile 0's was staged above)
+    if (my_tiles > 1) stage(blockIdx.x + gridDim.x, 1);
+    cp_async_commit();
+    bool ok = true;
+    for (int k = 0; k < my_tiles && ok; k++) {
+        const int b = k & 1;
+        if (tid == 0) {
+            // 36 MMAs of tile k into accumulator b
+            tc_fence_after();
+            if (flip) issue(b, true);
+            else issue(b, false);
+        }
+        // tile k-1's results while tile k's MMAs run (and tile k+1's input copy is under way)
+        if (k > 0 && !epilogue(k - 1)) ok = false;
+        // tile k+1's input has arrived (copied during tile k-1's epilogue,
+        // or before the loop for k = 0)
+        cp_async_wait0();
+        fence_async_smem();
+        tc_fence_before();
+        ok = __syncthreads_and(ok);
+    }
+    if (ok && my_tiles > 0) epilogue(my_tiles - 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
 // Persistent grid: two CTAs per SM (the weights of a 64 x 64 layer take
 // 81 KB of shared memory), at most one CTA per 256-pixel tile.
+// The tcgen05 kernel serves the 64 -> 64 layers unless HLBM_SUR_TC=0
+// (then the staged mma.sync kernel does).
+bool use_tc()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("HLBM_SUR_TC");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 template <int CIN, int NOUT>
 cudaError_t launch_conv_t(const ConvArgs &a, cudaStream_t st)
 {
@@ -578,6 +916,20 @@ cudaError_t launch_conv_t(const ConvArgs &a, cudaStream_t st)
             e = cudaFuncSetAttribute(conv_mma_kernel<CIN, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)G::smem_bytes);
         if (e != cudaSuccess) { sms = 0; return e; }
+    }
+    if (CIN == TC_CIN && NOUT == TC_NOUT && a.W % TC_TW == 0 && a.npix % (a.H * a.W) == 0 && use_tc()) {
+        static bool tc_ready = false;
+        if (!tc_ready) {
+            const cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)TC_SMEM);
+            if (e != cudaSuccess) return e;
+            tc_ready = true;
+        }
+        const int ntiles = a.npix / TC_TW;
+        const int blocks = ntiles < sms ? ntiles : sms;
+        conv_tc_kernel<<<blocks, TC_THREADS, TC_SMEM, st>>>(a.in, a.B, a.bias, a.nbias, a.out, a.z, a.zprev, a.H, a.W,
+                                                            ntiles, a.mode, a.flip);
+        return cudaGetLastError();
     }
     if (a.W % STG_TW == 0 && a.npix % (a.H * a.W) == 0) {
         using S = StagedConvGeom<CIN, NOUT>;
@@ -846,7 +1198,10 @@ int hlbm_sur_adam(hlbm_sur *s, float lr, float beta1, float beta2, float eps)
 int hlbm_sur_synchronize(hlbm_sur *s)
 {
     if (!s) return HLBM_ERR_ARG;
-    return cudaStreamSynchronize(s->stream) == cudaSuccess ? HLBM_OK : HLBM_ERR_CUDA;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
+    int timeout = 0;
+    if (cudaMemcpyFromSymbol(&timeout, g_tc_timeout, sizeof(int)) != cudaSuccess) return HLBM_ERR_CUDA;
+    return timeout ? HLBM_ERR_TIMEOUT : HLBM_OK;
 }
 
 
