@@ -82,6 +82,86 @@ __device__ __forceinline__ float gelu_grad_f(float x)
     return (x >= 0.0f ? 1.0f - r : r) + x * 0.3989422804014327f * e;
 }
 
+// Two FP32 values in one 64-bit register pair, for the packed .f32x2
+// instructions (one instruction, two independent IEEE operations).
+struct fp2 {
+    float x, y;
+};
+__device__ __forceinline__ unsigned long long fp2_bits(fp2 a)
+{
+    unsigned long long u;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(a.x), "f"(a.y));
+    return u;
+}
+__device__ __forceinline__ fp2 fp2_of(unsigned long long u)
+{
+    fp2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(u));
+    return r;
+}
+__device__ __forceinline__ fp2 bc2(float a) { return fp2{a, a}; }
+__device__ __forceinline__ fp2 add2(fp2 a, fp2 b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(fp2_bits(a)), "l"(fp2_bits(b)));
+    return fp2_of(d);
+}
+__device__ __forceinline__ fp2 sub2(fp2 a, fp2 b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(fp2_bits(a)), "l"(fp2_bits(b)));
+    return fp2_of(d);
+}
+__device__ __forceinline__ fp2 mul2(fp2 a, fp2 b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(fp2_bits(a)), "l"(fp2_bits(b)));
+    return fp2_of(d);
+}
+__device__ __forceinline__ fp2 fma2(fp2 a, fp2 b, fp2 c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(fp2_bits(a)), "l"(fp2_bits(b)), "l"(fp2_bits(c)));
+    return fp2_of(d);
+}
+
+// normal_tail on two values: the same formula, with the factor 1/2 folded
+// into the coefficients (exact: a power of two)
+__device__ __forceinline__ void normal_tail2(fp2 x, fp2 &r, fp2 &e)
+{
+    const fp2 den = fma2(fp2{fabsf(x.x), fabsf(x.y)}, bc2(0.3275911f * 0.70710678118654752f), bc2(1.0f));
+    const fp2 t{rcp_fast(den.x), rcp_fast(den.y)};
+    fp2 q = fma2(t, bc2(0.5f * 1.061405429f), bc2(0.5f * -1.453152027f));
+    q = fma2(t, q, bc2(0.5f * 1.421413741f));
+    q = fma2(t, q, bc2(0.5f * -0.284496736f));
+    q = fma2(t, q, bc2(0.5f * 0.254829592f));
+    q = mul2(t, q);
+    const fp2 g = mul2(mul2(x, x), bc2(-0.72134752044448170f));
+    e = fp2{ex2_fast(g.x), ex2_fast(g.y)};
+    r = mul2(q, e);
+}
+
+// Phi(x) for two values, from r = Phi(-|x|)
+__device__ __forceinline__ fp2 cdf2(fp2 x, fp2 r)
+{
+    const fp2 c = sub2(bc2(1.0f), r);
+    return fp2{x.x >= 0.0f ? c.x : r.x, x.y >= 0.0f ? c.y : r.y};
+}
+
+__device__ __forceinline__ fp2 gelu2(fp2 x)
+{
+    fp2 r, e;
+    normal_tail2(x, r, e);
+    return mul2(x, cdf2(x, r));
+}
+
+__device__ __forceinline__ fp2 gelu_grad2(fp2 x)
+{
+    fp2 r, e;
+    normal_tail2(x, r, e);
+    return fma2(mul2(x, bc2(0.3989422804014327f)), e, cdf2(x, r));
+}
+
 // Two floats rounded to BF16, low half first.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -608,13 +688,15 @@ conv_staged_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__
                 const size_t idx = p * NOUT + col;
                 if (mode == 2 && zprev) {
                     const float2 zp = *reinterpret_cast<const float2 *>(zprev + idx);
-                    z0 *= gelu_grad_f(zp.x);
-                    z1 *= gelu_grad_f(zp.y);
+                    const fp2 d = mul2(fp2{z0, z1}, gelu_grad2(fp2{zp.x, zp.y}));
+                    z0 = d.x;
+                    z1 = d.y;
                 }
                 if (z_f32) *reinterpret_cast<float2 *>(z_f32 + idx) = make_float2(z0, z1);
                 if (mode == 1) {
-                    z0 = gelu_f(z0);
-                    z1 = gelu_f(z1);
+                    const fp2 gv = gelu2(fp2{z0, z1});
+                    z0 = gv.x;
+                    z1 = gv.y;
                 }
                 *reinterpret_cast<uint32_t *>(out_bf + idx) = pack_bf16(z0, z1);
             }
@@ -623,35 +705,67 @@ conv_staged_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__
 }
 
 // ---- 5th-generation tensor cores (tcgen05, TMEM accumulators) ---------------------
-// The 64 -> 64 convolution on images whose width is a multiple of 128, as a
-// persistent kernel with one CTA of 16 warps per SM:
+// The convolutions with CIN, NOUT in {16, 64} (padded channels) on images
+// whose width is a multiple of 128, as a persistent kernel with one CTA of
+// 17 warps per SM:
 //   - the nine taps' weights stay in shared memory for the whole launch;
-//   - each 128-pixel row segment is one M = 128 tile: the three input rows it
-//     reaches are copied into one of two shared-memory buffers, and one
-//     thread issues its 36 MMAs (9 taps x 4 K-slices of 16 channels,
-//     M = 128, N = 64, K = 16, BF16 operands) into one of two TMEM
-//     accumulators of 64 FP32 columns, with tcgen05.commit signalling an
-//     mbarrier when they are done;
-//   - while the MMAs of tile i run, all warps read tile i-1's accumulator
-//     (tcgen05.ld), apply bias / GELU and store, then copy tile i+1's input.
-// Operands use the canonical K-major layout without swizzle: 8-row x 16-byte
-// core matrices, rows 16 bytes apart, 8-row groups SBO = 128 bytes apart
-// (so consecutive pixels are consecutive 16-byte rows and a tap's pixel
-// shift is a plain 16-byte offset of the descriptor's start address), the
-// two 8-channel halves of a K-slice LBO bytes apart.
-constexpr int TC_THREADS = 512, TC_TW = 128, TC_CIN = 64, TC_NOUT = 64, TC_RW = TC_TW + 2;
-constexpr uint32_t TC_W_TAP = 8 * TC_NOUT * 16;          // one tap's weights: 8 channel chunks x 64 rows x 16 B
-constexpr uint32_t TC_W_BYTES = 9 * TC_W_TAP;            // 73728
-constexpr uint32_t TC_IN_LBO = TC_RW * 16;               // 2080: channel chunk stride of a staged row
-constexpr uint32_t TC_IN_ROW = 8 * TC_IN_LBO;            // 16640: one staged input row
-constexpr uint32_t TC_IN_BYTES = 3 * TC_IN_ROW;          // 49920
-constexpr uint32_t TC_BAR_OFF = TC_W_BYTES + 2 * TC_IN_BYTES;   // 173568: two mbarriers, then the TMEM address
-constexpr uint32_t TC_BIAS_OFF = TC_BAR_OFF + 32;                 // 64 FP32 bias values
-// Dynamic shared memory requested: the operands need 173.6 KB; the rest is
-// slack so that every address a descriptor can form stays inside the block.
+//   - each 128-pixel row segment is one M = 128 tile; a CTA walks down a
+//     contiguous run of tiles of one column segment, so consecutive tiles
+//     share two of their three input rows.  The rows live in a ring of five
+//     shared-memory slots: the current tile's three, the next tile's new
+//     row, and the row after it, copied two tiles ahead (a run that crosses
+//     an image refills the ring);
+//   - one thread issues a tile's 9 CIN / 16 MMAs (M = 128, N = NOUT, K = 16,
+//     BF16 operands) into one of two TMEM accumulators of NOUT FP32 columns,
+//     with tcgen05.commit signalling an mbarrier when they are done;
+//   - while the MMAs of tile k run, all warps read tile k-1's accumulator
+//     (tcgen05.ld), apply bias / GELU and store.
+//   - warps 0-15 copy rows and run the epilogue; warp 16 only issues MMAs.
+// Operands are K-major.  With 64 channels a pixel (or a weight row) is one
+// 128-byte row of the 128-byte swizzle layout, so a tap's pixel shift moves
+// the operand by whole aligned rows.  With 16 channels they use the layout
+// without swizzle: 8-row x 16-byte core matrices, rows 16 bytes apart,
+// 8-row groups SBO = 128 bytes apart (consecutive pixels are consecutive
+// 16-byte rows and a pixel shift is a 16-byte offset of the start
+// address), the two 8-channel halves of a K-slice LBO bytes apart.
+constexpr int TC_THREADS = 544, TC_TW = 128, TC_RW = TC_TW + 2;
+constexpr int TC_EPI = 512;        // warps 0-15: copies and epilogue; warp 16 issues the MMAs
+constexpr int TC_MMA_TID = 512;
+constexpr uint32_t TC_IN_LBO = TC_RW * 16;               // 2080: channel-chunk stride of a staged row
+// Dynamic shared memory requested: the operands need at most 173.6 KB (64 ->
+// 64); the rest is slack so that every address a descriptor can form stays
+// inside the block.
 constexpr uint32_t TC_SMEM = 220 * 1024;
-constexpr uint32_t TC_TMEM_COLS = 2 * TC_NOUT;           // two accumulators
 constexpr long long TC_WAIT_CYCLES = 2000000000ll;       // about 1 s at 2 GHz
+
+template <int CIN, int NOUT>
+struct TcGeom {
+    static constexpr int CH = CIN / 8;                         // 16-byte channel chunks per pixel
+    // 64 channels: one pixel (or weight row) is one 128-byte row of the
+    // 128-byte swizzle layout (16-byte chunk c of row r stored at chunk
+    // c ^ (r % 8), rows 128 bytes apart, 8-row groups 1024 bytes apart), so a
+    // tap's pixel shift moves the operand by whole rows.  16 channels: the
+    // layout without swizzle.
+    static constexpr bool SW = CIN == 64;
+    static constexpr uint32_t W_LBO = NOUT * 16;               // chunk stride of one tap's weights (no swizzle)
+    static constexpr uint32_t W_TAP = CH * W_LBO;              // one tap: [n][128 B] or [k / 8][n][8]
+    static constexpr uint32_t W_BYTES = 9 * W_TAP;
+    static constexpr uint32_t IN_ROW = SW ? (TC_RW * 128 + 1023) / 1024 * 1024  // [column][128 B]
+                                          : CH * TC_IN_LBO;                       // [k / 8][column][8]
+    static constexpr int SLOTS = 5;                              // row ring
+    static constexpr uint32_t BAR_OFF = W_BYTES + SLOTS * IN_ROW;  // two mbarriers, then the TMEM address
+    static constexpr uint32_t BIAS_OFF = BAR_OFF + 32;           // NOUT FP32 bias values
+    static constexpr uint32_t TMEM_COLS = 2 * NOUT < 32 ? 32 : 2 * NOUT;  // two accumulators (allocation >= 32)
+    static constexpr int COLS = NOUT / 4;                        // accumulator columns per warp in the epilogue
+    // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1),
+    // BF16 A and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17,
+    // M >> 4 at bit 24.
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NOUT >> 3) << 17) |
+                                      ((uint32_t)(TC_TW >> 4) << 24);
+    static_assert(BIAS_OFF + 4 * NOUT <= TC_SMEM, "shared memory");
+    static_assert(!SW || (W_TAP % 1024 == 0 && W_BYTES % 1024 == 0 && IN_ROW % 1024 == 0), "swizzle atoms");
+    static_assert(NOUT % 16 == 0 && CIN % 16 == 0, "shapes");
+};
 
 // Set when an mbarrier wait of the tcgen05 kernel gave up (read by
 // hlbm_sur_synchronize).
@@ -667,11 +781,16 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
-// A and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at
-// bit 24.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_NOUT >> 3) << 17) |
-                              ((uint32_t)(TC_TW >> 4) << 24);
+// The same with the 128-byte swizzle (layout type 2): SBO = 1024 bytes
+// between 8-row groups, LBO unused (16), base offset 0.  The swizzle phase
+// follows the absolute shared-memory address (chunk bits 4-6 XOR row bits
+// 7-9), so an operand may start at any 128-byte row of a 1024-byte aligned
+// buffer, and 32-byte steps of the start address select the K-slice.
+__device__ __forceinline__ uint64_t umma_desc_sw(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
 
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
@@ -708,8 +827,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return true;
 }
 
-// 16 TMEM columns of this warp's 32 lanes (one FP32 value per column).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+// COLS TMEM columns of this warp's 32 lanes (one FP32 value per column).
+template <int COLS>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float *v);
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float *v)
 {
     uint32_t r[16];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -722,32 +844,65 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
 #pragma unroll
     for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
 }
+template <>
+__device__ __forceinline__ void tmem_ld<4>(uint32_t taddr, float *v)
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = __uint_as_float(r[k]);
+}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// 16 bytes: COLS / ... BF16 values of out (COLS = 4: 8 bytes)
+template <int COLS>
+__device__ __forceinline__ void store_bf16(__nv_bfloat16 *dst, const float *v)
+{
+    if constexpr (COLS == 4) {
+        *reinterpret_cast<uint2 *>(dst) = make_uint2(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]));
+    } else {
+        uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+        for (int c = 0; c < COLS / 8; c++)
+            d[c] = make_uint4(pack_bf16(v[8 * c], v[8 * c + 1]), pack_bf16(v[8 * c + 2], v[8 * c + 3]),
+                              pack_bf16(v[8 * c + 4], v[8 * c + 5]), pack_bf16(v[8 * c + 6], v[8 * c + 7]));
+    }
+}
+
+template <int CIN, int NOUT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 conv_tc_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ B,
                const float *__restrict__ bias, int nbias, __nv_bfloat16 *__restrict__ out_bf,
                float *__restrict__ z_f32, const float *__restrict__ zprev, int H, int W, int ntiles, int mode,
                int flip)
 {
+    using G = TcGeom<CIN, NOUT>;
+    constexpr int CH = G::CH, COLS = G::COLS;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     const uint32_t sbase = smem_addr(tc_smem);
-    const uint32_t w_s = sbase;
-    auto in_s = [&](int b) { return sbase + TC_W_BYTES + b * TC_IN_BYTES; };
-    auto bar = [&](int b) { return sbase + TC_BAR_OFF + 8 * b; };
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + TC_BAR_OFF + 16);
-    float *bias_s = reinterpret_cast<float *>(tc_smem + TC_BIAS_OFF);
+    const uint32_t w_s = sbase, ring_s = sbase + G::W_BYTES;
+    auto bar = [&](int b) { return sbase + G::BAR_OFF + 8 * b; };
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + G::BAR_OFF + 16);
+    float *bias_s = reinterpret_cast<float *>(tc_smem + G::BIAS_OFF);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nseg = W / TC_TW;
-    if (tid < TC_NOUT) bias_s[tid] = (bias && tid < nbias) ? bias[tid] : 0.0f;
+    const int R = ntiles / nseg;  // image rows of the batch, B H
+    // the swizzled layouts assume 1024-byte aligned shared memory
+    if (G::SW && (sbase & 1023u) != 0) {
+        if (tid == 0) atomicExch(&g_tc_timeout, 2);
+        return;
+    }
+    if (tid < NOUT) bias_s[tid] = (bias && tid < nbias) ? bias[tid] : 0.0f;
 
     // TMEM for the two accumulators (one warp allocates), the mbarriers
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                     "r"(TC_TMEM_COLS) : "memory");
+                     "r"(G::TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
@@ -756,32 +911,36 @@ conv_tc_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__rest
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // weights of all taps: B[tap][n][k] -> [tap][k / 8][n][8]
-    for (int e = tid; e < 9 * TC_NOUT * 8; e += TC_THREADS) {
-        const int tap = e >> 9, rem = e & 511, nrow = rem >> 3, kc = rem & 7;
-        cp_async16(tc_smem + tap * TC_W_TAP + kc * (TC_NOUT * 16) + nrow * 16,
-                   B + ((size_t)tap * TC_NOUT + nrow) * TC_CIN + kc * 8);
+    for (int e = tid; e < 9 * NOUT * CH; e += TC_THREADS) {
+        const int tap = e / (NOUT * CH), rem = e - tap * (NOUT * CH), nrow = rem / CH, kc = rem - nrow * CH;
+        const uint32_t off = G::SW ? nrow * 128 + ((kc ^ (nrow & 7)) << 4) : kc * G::W_LBO + nrow * 16;
+        cp_async16(tc_smem + tap * G::W_TAP + off, B + ((size_t)tap * NOUT + nrow) * CIN + kc * 8);
     }
-    // input rows i-1 .. i+1, columns j0-1 .. j0+128 of a tile -> [row][k / 8][column][8]:
-    // thread t copies channel chunk t % 8 of columns t / 8 + 64 m (m = 0, 1, 2)
-    const int s_kc = tid & 7, s_px = tid >> 3;
-    auto stage = [&](int tile, int buf) {
-        const int seg = tile % nseg, row = tile / nseg;
-        const int n = row / H, i = row - n * H, j0 = seg * TC_TW;
-        unsigned char *dst = tc_smem + TC_W_BYTES + buf * TC_IN_BYTES + s_kc * TC_IN_LBO;
+    // Tiles are numbered column segment first: T = seg R + r, r = n H + i;
+    // this CTA takes T in [t0, t0 + my_tiles).  Tile T + 1 shares two input
+    // rows with T unless T is an image's last row (or the segment's).
+    const int t0 = (int)(((long long)blockIdx.x * ntiles) / gridDim.x);
+    const int my_tiles = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x) - t0;
+    auto successor = [&](int T) { return (T % H) != H - 1; };
+    // input row i - 1 + d (wrapped in the image) of tile T, columns j0-1 ..
+    // j0+128 -> ring slot [k / 8][column][8]: thread t copies channel chunk
+    // t % CH of columns t / CH + (512 / CH) m
+    const int s_kc = tid % CH, s_px = tid / CH;
+    auto load_row = [&](int T, int d, int slot) {
+        if (tid >= TC_EPI) return;
+        const int seg = T / R, r = T - seg * R;
+        const int n = r / H, i = r - n * H, j0 = seg * TC_TW;
+        const __nv_bfloat16 *src = in + ((size_t)n * H + wrap(i - 1 + d, H)) * W * CIN + s_kc * 8;
+        unsigned char *dst = tc_smem + G::W_BYTES + slot * G::IN_ROW;
 #pragma unroll
-        for (int rr = 0; rr < 3; rr++) {
-            const __nv_bfloat16 *src = in + ((size_t)n * H + wrap(i + rr - 1, H)) * W * TC_CIN + s_kc * 8;
-#pragma unroll
-            for (int m = 0; m < 3; m++) {
-                const int px = s_px + 64 * m;
-                if (px < TC_RW) cp_async16(dst + rr * TC_IN_ROW + px * 16, src + (size_t)wrap(j0 + px - 1, W) * TC_CIN);
-            }
+        for (int m = 0; m < (TC_RW * CH + TC_EPI - 1) / TC_EPI; m++) {
+            const int px = s_px + (TC_EPI / CH) * m;
+            const uint32_t off = G::SW ? px * 128 + ((s_kc ^ (px & 7)) << 4) : s_kc * TC_IN_LBO + px * 16;
+            if (px < TC_RW) cp_async16(dst + off, src + (size_t)wrap(j0 + px - 1, W) * CIN);
         }
     };
-    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    if (my_tiles > 0) stage(blockIdx.x, 0);
     cp_async_commit();
-    cp_async_wait0();
+    cp_async_wait0();  // the weights
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -789,110 +948,147 @@ conv_tc_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__rest
     const uint32_t tmem = *tmem_slot;
 
     // epilogue of local tile k (accumulator k & 1): warp w reads TMEM lanes
-    // 32 (w % 4) .. +31 (pixels) and columns 16 (w / 4) .. +15 (outputs)
-    // Once tile k's MMAs are complete, its input buffer is free: tile k + 2's
-    // input is copied into it right away, overlapping the epilogue math.
-    auto epilogue = [&](int k) -> bool {
-        const int tile = blockIdx.x + k * gridDim.x;
+    // 32 (w % 4) .. +31 (pixels) and columns COLS (w / 4) .. +COLS-1 (outputs).
+    // Once tile k's MMAs are complete, the ring slot of its first input row
+    // is free: then() copies a later tile's row into it right away, so that
+    // the copy overlaps the epilogue math.
+    auto epilogue = [&](int k, auto then) -> bool {
+        const int T = t0 + k;
         // the warp-wide TMEM load below needs the whole warp: agree on the outcome
         if (!__all_sync(0xffffffffu, mbar_wait(bar(k & 1), (k >> 1) & 1))) return false;
-        if (k + 2 < my_tiles) stage(blockIdx.x + (k + 2) * gridDim.x, k & 1);
-        cp_async_commit();
+        then();
         tc_fence_after();
         const int q = warp & 3, h = warp >> 2;
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (k & 1) * TC_NOUT + 16 * h, v);
-        const size_t p = (size_t)tile * TC_TW + 32 * q + lane;  // tile = row * nseg + seg
-        const size_t o = p * TC_NOUT + 16 * h;                      // this thread's 16 outputs
+        float v[COLS];
+        tmem_ld<COLS>(tmem + ((uint32_t)(32 * q) << 16) + (k & 1) * NOUT + COLS * h, v);
+        const int seg = T / R, r = T - seg * R;
+        const size_t p = (size_t)r * W + seg * TC_TW + 32 * q + lane;
+        const size_t o = p * NOUT + COLS * h;  // this thread's COLS outputs
+        // pairs of adjacent outputs in packed FP32
+        const float2 *bs = reinterpret_cast<const float2 *>(bias_s + COLS * h);
 #pragma unroll
-        for (int c = 0; c < 16; c++) v[c] += bias_s[16 * h + c];
+        for (int c = 0; c < COLS / 2; c++) {
+            const float2 b2 = bs[c];
+            const fp2 z = add2(fp2{v[2 * c], v[2 * c + 1]}, fp2{b2.x, b2.y});
+            v[2 * c] = z.x;
+            v[2 * c + 1] = z.y;
+        }
         if (mode == 2 && zprev) {
             const float4 *zp = reinterpret_cast<const float4 *>(zprev + o);
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
+            for (int c = 0; c < COLS / 4; c++) {
                 const float4 g = zp[c];
-                v[4 * c + 0] *= gelu_grad_f(g.x);
-                v[4 * c + 1] *= gelu_grad_f(g.y);
-                v[4 * c + 2] *= gelu_grad_f(g.z);
-                v[4 * c + 3] *= gelu_grad_f(g.w);
+                const fp2 d0 = mul2(fp2{v[4 * c], v[4 * c + 1]}, gelu_grad2(fp2{g.x, g.y}));
+                const fp2 d1 = mul2(fp2{v[4 * c + 2], v[4 * c + 3]}, gelu_grad2(fp2{g.z, g.w}));
+                v[4 * c] = d0.x; v[4 * c + 1] = d0.y; v[4 * c + 2] = d1.x; v[4 * c + 3] = d1.y;
             }
         }
         if (z_f32) {
             float4 *zd = reinterpret_cast<float4 *>(z_f32 + o);
 #pragma unroll
-            for (int c = 0; c < 4; c++) zd[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+            for (int c = 0; c < COLS / 4; c++) zd[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
         }
         if (mode == 1) {
 #pragma unroll
-            for (int c = 0; c < 16; c++) v[c] = gelu_f(v[c]);
+            for (int c = 0; c < COLS / 2; c++) {
+                const fp2 gv = gelu2(fp2{v[2 * c], v[2 * c + 1]});
+                v[2 * c] = gv.x;
+                v[2 * c + 1] = gv.y;
+            }
         }
-        uint4 *dst = reinterpret_cast<uint4 *>(out_bf + o);
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-            uint4 u;
-            u.x = pack_bf16(v[8 * c + 0], v[8 * c + 1]);
-            u.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
-            u.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
-            u.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
-            dst[c] = u;
-        }
+        store_bf16<COLS>(out_bf + o, v);
         return true;
     };
 
-    // descriptors of tap 0, K-slice 0; the others differ only in the start
-    // address field (low 14 bits, in 16-byte units), by compile-time offsets
-    const uint64_t adesc0[2] = {umma_desc(in_s(0), TC_IN_LBO, 128), umma_desc(in_s(1), TC_IN_LBO, 128)};
-    const uint64_t bdesc0 = umma_desc(w_s, TC_NOUT * 16, 128);
-    auto issue = [&](int b, bool flipped) {
-        const uint32_t d = tmem + b * TC_NOUT;
-        const uint64_t a0 = b ? adesc0[1] : adesc0[0];
+    // The MMAs of a tile whose input rows i-1, i, i+1 sit in ring slots
+    // (base + 0, 1, 2) % 5: a K-slice of tap (dp, dq) starts at row slot
+    // (base + 1 + dp), column 1 + dq; descriptors differ from the slot's
+    // only in the start-address field (16-byte units).
+    const uint64_t bdesc0 = G::SW ? umma_desc_sw(w_s) : umma_desc(w_s, G::W_LBO, 128);
+    auto issue = [&](int b, int base, bool flipped) {
+        const uint32_t d = tmem + b * NOUT;
+        uint64_t rowdesc[3];
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+            const uint32_t a = ring_s + ((base + e) % G::SLOTS) * G::IN_ROW;
+            rowdesc[e] = G::SW ? umma_desc_sw(a) : umma_desc(a, TC_IN_LBO, 128);
+        }
 #pragma unroll
         for (int tap = 0; tap < 9; tap++) {
             const int dp = flipped ? 1 - tap / 3 : tap / 3 - 1, dq = flipped ? 1 - tap % 3 : tap % 3 - 1;
 #pragma unroll
-            for (int ks = 0; ks < 4; ks++) {
-                const uint32_t ao = ((1 + dp) * TC_IN_ROW + (1 + dq) * 16 + 2 * ks * TC_IN_LBO) >> 4;
-                const uint32_t bo = (tap * TC_W_TAP + 2 * ks * (TC_NOUT * 16)) >> 4;
-                umma_f16(d, a0 + ao, bdesc0 + bo, TC_IDESC, (tap | ks) != 0);
+            for (int ks = 0; ks < CIN / 16; ks++) {
+                // start-address offsets: the pixel shift (whole 128-byte rows
+                // when swizzled) and the K-slice (32 bytes within the row)
+                const uint32_t ao = G::SW ? ((1 + dq) * 128 + 32 * ks) >> 4 : ((1 + dq) * 16 + 2 * ks * TC_IN_LBO) >> 4;
+                const uint32_t bo = G::SW ? (tap * G::W_TAP + 32 * ks) >> 4 : (tap * G::W_TAP + 2 * ks * G::W_LBO) >> 4;
+                umma_f16(d, rowdesc[1 + dp] + ao, bdesc0 + bo, G::IDESC, (tap | ks) != 0);
             }
         }
         umma_commit(bar(b));
     };
 
-    // tile 1's input (tile 0's was staged above)
-    if (my_tiles > 1) stage(blockIdx.x + gridDim.x, 1);
-    cp_async_commit();
     bool ok = true;
+    int j0 = 0;  // local index of the tile that started the current run
     for (int k = 0; k < my_tiles && ok; k++) {
-        const int b = k & 1;
-        if (tid == 0) {
-            // 36 MMAs of tile k into accumulator b
-            tc_fence_after();
-            if (flip) issue(b, true);
-            else issue(b, false);
+        const int T = t0 + k;
+        if (k == 0 || !successor(T - 1)) {
+            // a new run: wait until the ring is free (the previous tile's
+            // MMAs are done), then copy this tile's three rows and the next
+            // tile's new row
+            if (k > 0) ok = __all_sync(0xffffffffu, mbar_wait(bar((k - 1) & 1), ((k - 1) >> 1) & 1));
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+            j0 = k;
+            for (int d = 0; d < 3; d++) load_row(T, d, d);
+            if (k + 1 < my_tiles && successor(T)) load_row(T + 1, 2, 3);
+            cp_async_commit();
+            cp_async_wait0();
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
         }
-        // tile k-1's results while tile k's MMAs run (and tile k+1's input copy is under way)
-        if (k > 0 && !epilogue(k - 1)) ok = false;
-        // tile k+1's input has arrived (copied during tile k-1's epilogue,
-        // or before the loop for k = 0)
-        cp_async_wait0();
+        const int base = k - j0;
+        if (tid == TC_MMA_TID) {
+            // the MMAs of tile k into accumulator k & 1
+            tc_fence_after();
+            if (flip) issue(k & 1, base, true);
+            else issue(k & 1, base, false);
+        }
+        // tile k+2's new row, into the slot tile k-1's MMAs release
+        auto prefetch = [&]() {
+            if (k + 2 < my_tiles && successor(T) && successor(T + 1)) load_row(T + 2, 2, (base + 4) % G::SLOTS);
+        };
+        // tile k-1's results while tile k's MMAs run (warps 0-15)
+        if (tid < TC_EPI) {
+            if (k > 0) {
+                if (!epilogue(k - 1, prefetch)) ok = false;
+            } else {
+                prefetch();
+            }
+        }
+        cp_async_commit();
+        // tile k+1's new row (copied one iteration earlier) has arrived; the
+        // row of tile k+2 may still be in flight
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
         fence_async_smem();
         tc_fence_before();
         ok = __syncthreads_and(ok);
     }
-    if (ok && my_tiles > 0) epilogue(my_tiles - 1);
+    if (ok && my_tiles > 0 && tid < TC_EPI) epilogue(my_tiles - 1, [] {});
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS) : "memory");
     }
 }
 
 // Persistent grid: two CTAs per SM (the weights of a 64 x 64 layer take
 // 81 KB of shared memory), at most one CTA per 256-pixel tile.
-// The tcgen05 kernel serves the 64 -> 64 layers unless HLBM_SUR_TC=0
-// (then the staged mma.sync kernel does).
+// The tcgen05 kernel serves the layers with 16 or 64 padded input and
+// output channels unless HLBM_SUR_TC=0 (then the staged mma.sync kernel
+// does).
 bool use_tc()
 {
     static int v = -1;
@@ -917,19 +1113,21 @@ cudaError_t launch_conv_t(const ConvArgs &a, cudaStream_t st)
                                      (int)G::smem_bytes);
         if (e != cudaSuccess) { sms = 0; return e; }
     }
-    if (CIN == TC_CIN && NOUT == TC_NOUT && a.W % TC_TW == 0 && a.npix % (a.H * a.W) == 0 && use_tc()) {
-        static bool tc_ready = false;
-        if (!tc_ready) {
-            const cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)TC_SMEM);
-            if (e != cudaSuccess) return e;
-            tc_ready = true;
+    if constexpr ((CIN == 16 || CIN == 64) && (NOUT == 16 || NOUT == 64)) {
+        if (a.W % TC_TW == 0 && a.npix % (a.H * a.W) == 0 && use_tc()) {
+            static bool tc_ready = false;
+            if (!tc_ready) {
+                const cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<CIN, NOUT>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+                if (e != cudaSuccess) return e;
+                tc_ready = true;
+            }
+            const int ntiles = a.npix / TC_TW;
+            const int blocks = ntiles < sms ? ntiles : sms;
+            conv_tc_kernel<CIN, NOUT><<<blocks, TC_THREADS, TC_SMEM, st>>>(a.in, a.B, a.bias, a.nbias, a.out, a.z,
+                                                                          a.zprev, a.H, a.W, ntiles, a.mode, a.flip);
+            return cudaGetLastError();
         }
-        const int ntiles = a.npix / TC_TW;
-        const int blocks = ntiles < sms ? ntiles : sms;
-        conv_tc_kernel<<<blocks, TC_THREADS, TC_SMEM, st>>>(a.in, a.B, a.bias, a.nbias, a.out, a.z, a.zprev, a.H, a.W,
-                                                            ntiles, a.mode, a.flip);
-        return cudaGetLastError();
     }
     if (a.W % STG_TW == 0 && a.npix % (a.H * a.W) == 0) {
         using S = StagedConvGeom<CIN, NOUT>;

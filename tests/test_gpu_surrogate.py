@@ -144,3 +144,45 @@ def test_predict_equals_forward_and_blocks_backward(env, shape):
         hlbm.hlbm_sur_backward(sur.s, x)
     assert e.value.code == hlbm.HLBM_ERR_ARG
     sur.close()
+
+
+_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2002_03644_gb300 import hlbm, surrogate
+B, H, W = (int(v) for v in sys.argv[2:5])
+widths = (4, 64, 64, 4)
+torch.cuda.set_device(0)
+sur = surrogate.Surrogate(widths, H, W, batch_max=B, seed=11)
+rng = np.random.default_rng(12)
+x = torch.from_numpy(rng.normal(size=(B, H, W, 4)).astype(np.float32)).cuda()
+t = torch.from_numpy(rng.normal(size=(B, H, W, 4)).astype(np.float32)).cuda()
+y = sur.forward(x).cpu().numpy()
+hlbm.hlbm_sur_backward(sur.s, t)
+np.savez(sys.argv[5], y=y, g=sur.grads())
+hlbm.hlbm_sur_synchronize(sur.s)
+sur.close()
+"""
+
+
+@pytest.mark.parametrize("shape", [(4, 48, 256), (160, 2, 128)], ids=["4x48x256", "160x2x128"])
+def test_tensor_core_kernel_matches_mma_sync_kernel(env, shape, tmp_path):
+    """The tcgen05 convolutions (16 -> 64, 64 -> 64, 64 -> 16 and the
+    transposed ones of the backward pass) against the mma.sync kernels on
+    batches large enough that each CTA walks several tiles, with runs that
+    cross image boundaries (images of 48 and of 2 rows): outputs and
+    gradients.  Both accumulate the same BF16 products in FP32."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for tc in ("1", "0"):
+        out = str(tmp_path / f"tc{tc}.npz")
+        envv = dict(os.environ, HLBM_SUR_TC=tc)
+        subprocess.run([sys.executable, "-c", _CHILD, root, *map(str, shape), out], check=True, env=envv,
+                       timeout=600)
+        res[tc] = np.load(out)
+    assert np.isfinite(res["1"]["y"]).all()
+    assert rel(res["1"]["y"], res["0"]["y"]) < 1e-3
+    assert rel(res["1"]["g"], res["0"]["g"]) < 1e-3
