@@ -218,9 +218,9 @@ int hlbm_batch_step(hlbm_batch *b, int64_t n);
 /* Time every compiled work shape on the current states (restored afterwards)
  * and keep the fastest; *tile receives its index (may be NULL).  The choice
  * holds until the next call.  Indices 0-4 are tiles of the tiled kernel
- * (32x16, 64x16, 32x8, 64x32, 32x32); 5 and 6 are the row-marching kernel
- * (strips of 120 columns, row segments of 16 and 32), tried only when all
- * cases share one sigma > 0 / sigma = 0 and one phi_mode. */
+ * (32x16, 64x16, 32x8, 64x32, 32x32); 5 to 10 are the row-marching kernel
+ * (strips of 120 columns, row segments of 16, 32, 48, 64, 96 and 128), tried
+ * only when all cases share one sigma > 0 / sigma = 0 and one phi_mode. */
 int hlbm_batch_autotune(hlbm_batch *b, int *tile);
 
 /* Work shape index in use and its dimensions: tile width and height and

@@ -916,11 +916,13 @@ struct TileShape {
 };
 constexpr TileShape kBatchTiles[] = {{32, 16, 256}, {64, 16, 256}, {32, 8, 128}, {64, 32, 512}, {32, 32, 512}};
 constexpr int kNumBatchTiles = 5;
-// Kinds 5 and 6: the row-marching kernel (64 threads, strips of 120
-// columns) with segments of 16 and 32 rows.  They need one sigma > 0 / Phi
-// choice for all cases (the kernel is specialised on both).
-constexpr int kBatchMarchRows[] = {16, 32};
-constexpr int kNumBatchKinds = kNumBatchTiles + 2;
+// Kinds 5 to 10: the row-marching kernel (64 threads, strips of 120
+// columns) with segments of 16, 32, 48, 64, 96 and 128 rows (longer
+// segments repeat the four-row ring refill less often, shorter ones balance
+// the persistent grid better).  They need one sigma > 0 / Phi choice for all
+// cases (the kernel is specialised on both).
+constexpr int kBatchMarchRows[] = {16, 32, 48, 64, 96, 128};
+constexpr int kNumBatchKinds = kNumBatchTiles + (int)(sizeof(kBatchMarchRows) / sizeof(kBatchMarchRows[0]));
 constexpr int kBatchMarchNT = 64, kBatchMarchMinB = 8;
 constexpr int kGraphSteps = 16;  // steps per captured graph (even: parity returns)
 
