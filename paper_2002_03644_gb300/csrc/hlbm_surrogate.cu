@@ -479,14 +479,19 @@ __global__ void residual_loss_kernel(const float *__restrict__ xin, const float 
 {
     double local = 0.0;
     const long long n = (long long)npix * c_real;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int p = (int)(e / c_real), c = (int)(e - (long long)p * c_real);
-        const float yy = xin[e] + zlast[(size_t)p * cpad_last + c];
-        y[e] = yy;
-        if (target) {
-            const float d = yy - target[e];
-            local += (double)d * d;
-            dz_last[(size_t)p * cpad_last + c] = 2.0f * d / (float)n;
+    const float inv_n2 = 2.0f / (float)n;
+    // one pixel per thread: its c_real outputs
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        const size_t e0 = (size_t)p * c_real;
+        const float *zp = zlast + (size_t)p * cpad_last;
+        for (int c = 0; c < c_real; c++) {
+            const float yy = xin[e0 + c] + zp[c];
+            y[e0 + c] = yy;
+            if (target) {
+                const float d = yy - target[e0 + c];
+                local += (double)d * d;
+                dz_last[(size_t)p * cpad_last + c] = d * inv_n2;
+            }
         }
     }
     if (target) {
