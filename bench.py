@@ -560,6 +560,7 @@ def run_surrogate(args):
         sur.predict(x, y)
     e1.record(stream)
     torch.cuda.synchronize()
+    sur.synchronize()  # raises if a tensor-core kernel reported a timeout
     t_sur = e0.elapsed_time(e1) / 1e3 / (reps * batch)
     case = inputs.random_fourier(n=n, seed=1)
     s = hlbm.Solver(n, n, stream=sh, precision=hlbm.HLBM_FP32, **case.params())

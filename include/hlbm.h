@@ -253,6 +253,10 @@ int hlbm_sur_predict(hlbm_sur *s, const float *x, float *y, int B);
 /* after hlbm_sur_forward: gradients of mean((y - target)^2); *loss if non-NULL */
 int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss);
 int hlbm_sur_adam(hlbm_sur *s, float lr, float beta1, float beta2, float eps);
+/* Wait for the surrogate's stream.  HLBM_ERR_TIMEOUT if a wait of a
+ * tensor-core kernel on its own MMAs gave up (after about a second; the
+ * kernel then returns and its results are invalid), HLBM_ERR_CUDA on a CUDA
+ * error. */
 int hlbm_sur_synchronize(hlbm_sur *s);
 void hlbm_sur_destroy(hlbm_sur *s);
 

@@ -772,9 +772,9 @@ struct TcGeom {
     static_assert(NOUT % 16 == 0 && CIN % 16 == 0, "shapes");
 };
 
-// Set when an mbarrier wait of the tcgen05 kernel gave up (read by
-// hlbm_sur_synchronize).
-__device__ int g_tc_timeout = 0;
+// Status of the tcgen05 kernel, read by hlbm_sur_synchronize: 1 when an
+// mbarrier wait gave up, 2 when the shared memory was not 1024-byte aligned.
+__device__ int g_tc_status = 0;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -825,7 +825,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > TC_WAIT_CYCLES) {
-            atomicExch(&g_tc_timeout, 1);
+            atomicExch(&g_tc_status, 1);
             return false;
         }
     }
@@ -899,7 +899,7 @@ conv_tc_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__rest
     const int R = ntiles / nseg;  // image rows of the batch, B H
     // the swizzled layouts assume 1024-byte aligned shared memory
     if (G::SW && (sbase & 1023u) != 0) {
-        if (tid == 0) atomicExch(&g_tc_timeout, 2);
+        if (tid == 0) atomicExch(&g_tc_status, 2);
         return;
     }
     if (tid < NOUT) bias_s[tid] = (bias && tid < nbias) ? bias[tid] : 0.0f;
@@ -1402,9 +1402,9 @@ int hlbm_sur_synchronize(hlbm_sur *s)
 {
     if (!s) return HLBM_ERR_ARG;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
-    int timeout = 0;
-    if (cudaMemcpyFromSymbol(&timeout, g_tc_timeout, sizeof(int)) != cudaSuccess) return HLBM_ERR_CUDA;
-    return timeout ? HLBM_ERR_TIMEOUT : HLBM_OK;
+    int st = 0;
+    if (cudaMemcpyFromSymbol(&st, g_tc_status, sizeof(int)) != cudaSuccess) return HLBM_ERR_CUDA;
+    return st == 0 ? HLBM_OK : (st == 1 ? HLBM_ERR_TIMEOUT : HLBM_ERR_CUDA);
 }
 
 

@@ -186,6 +186,11 @@ class Surrogate:
         hlbm.hlbm_sur_predict(self.s, x, y, x.shape[0])
         return y
 
+    def synchronize(self):
+        """Wait for the surrogate's work; raises HlbmError if a tensor-core
+        kernel reported a timeout."""
+        hlbm.hlbm_sur_synchronize(self.s)
+
     def train_step(self, x, target, lr):
         hlbm.hlbm_sur_forward(self.s, x, None, x.shape[0])
         loss = hlbm.hlbm_sur_backward(self.s, target)
@@ -206,6 +211,7 @@ class Surrogate:
                 idx = torch.as_tensor(order[b0:b0 + batch], device=X.device)
                 tot += self.train_step(X[idx].contiguous(), Y[idx].contiguous(), lr)
                 cnt += 1
+            self.synchronize()
             hist.append(tot / max(cnt, 1))
             if log:
                 log(ep, hist[-1])
