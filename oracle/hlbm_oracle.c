@@ -28,10 +28,11 @@
  *    sides copy the nearest interior value, Dirichlet sides hold a fixed state
  *    (rho, u, theta) with a1 = 0 and populations at equilibrium.  Ghosts of a
  *    level are refilled from the interior of the same level.  At corners a
- *    Dirichlet y side wins, then a Dirichlet x side, else both axes are mapped.
- *    Wall sides (y sides only) are no-slip, fixed-temperature walls half-way
- *    between the first ghost row and the first interior row: ghost row g
- *    mirrors interior row g - 1 with rho equal, u reflected about the wall
+ *    Dirichlet or wall y side wins, then a Dirichlet or wall x side, else both
+ *    axes are mapped.
+ *    Wall sides are no-slip, fixed-temperature walls half-way between the
+ *    first ghost layer and the first interior layer: ghost layer g mirrors
+ *    interior layer g - 1 with the pressure kept, u reflected about the wall
  *    velocity (u_g = 2 u_w - u) and theta about the wall temperature
  *    (theta_g = 2 theta_w - theta), s from that rho and theta, and ghost
  *    populations rebuilt by the regularised formula of the collision from
@@ -287,10 +288,12 @@ static inline int IX(const hlbmo *o, int x, int y) { return (y + G) * o->px + (x
 
 static int wrap(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
 
-/* Refill the ghost frame of one array: x sides over interior rows first,
- * then y sides over the full padded width (so a Dirichlet y side wins at a
- * corner).  dv holds the Dirichlet value per side. */
-static void fill_ghosts(const hlbmo *o, double *a, const double dv[4])
+/* The ghost frame of one array is refilled in two passes: the x sides over
+ * the interior rows, then the y sides over the full padded width, so that a
+ * y side wins at a corner.  dv holds the Dirichlet value per side; wall
+ * sides are skipped here and filled between and after the passes (see
+ * fill_level, fill_a1_ghosts and collide). */
+static void fill_x(const hlbmo *o, double *a, const double dv[4])
 {
     for (int y = 0; y < o->ny; y++)
         for (int g = 1; g <= G; g++) {
@@ -298,21 +301,27 @@ static void fill_ghosts(const hlbmo *o, double *a, const double dv[4])
             switch (o->bc[0]) {
             case BC_PERIODIC: a[IX(o, xl, y)] = a[IX(o, wrap(xl, o->nx), y)]; break;
             case BC_ZEROGRAD: a[IX(o, xl, y)] = a[IX(o, 0, y)]; break;
+            case BC_WALL: break;
             default: a[IX(o, xl, y)] = dv[0];
             }
             switch (o->bc[1]) {
             case BC_PERIODIC: a[IX(o, xr, y)] = a[IX(o, wrap(xr, o->nx), y)]; break;
             case BC_ZEROGRAD: a[IX(o, xr, y)] = a[IX(o, o->nx - 1, y)]; break;
+            case BC_WALL: break;
             default: a[IX(o, xr, y)] = dv[1];
             }
         }
+}
+
+static void fill_y(const hlbmo *o, double *a, const double dv[4])
+{
     for (int x = -G; x < o->nx + G; x++)
         for (int g = 1; g <= G; g++) {
             const int yl = -g, yr = o->ny - 1 + g;
             switch (o->bc[2]) {
             case BC_PERIODIC: a[IX(o, x, yl)] = a[IX(o, x, wrap(yl, o->ny))]; break;
             case BC_ZEROGRAD: a[IX(o, x, yl)] = a[IX(o, x, 0)]; break;
-            case BC_WALL: break;  /* fill_wall_macros / wall_populations */
+            case BC_WALL: break;
             default: a[IX(o, x, yl)] = dv[2];
             }
             switch (o->bc[3]) {
@@ -329,35 +338,39 @@ static void side_values(const hlbmo *o, int q, double dv[4])
     for (int k = 0; k < 4; k++) dv[k] = o->bcs[k][q];
 }
 
-static void fill_macros(hlbmo *o, double *rho, double *ux, double *uy, double *th)
+/* Wall side k (0: x-, 1: x+, 2: y-, 3: y+), ghost layer g (1 or 2) and
+ * position t along the wall (a row for an x side, over the interior rows; a
+ * column for a y side, over the full padded width): the ghost cell and the
+ * interior cell it mirrors about the wall, which lies half-way between the
+ * first ghost layer and the first interior layer. */
+static int wall_span(const hlbmo *o, int k, int *t0) { *t0 = k < 2 ? 0 : -G; return k < 2 ? o->ny : o->nx + 2 * G; }
+static void wall_cells(const hlbmo *o, int k, int g, int t, int *kg, int *km)
 {
-    double dv[4];
-    side_values(o, 0, dv); fill_ghosts(o, rho, dv);
-    side_values(o, 1, dv); fill_ghosts(o, ux, dv);
-    side_values(o, 2, dv); fill_ghosts(o, uy, dv);
-    side_values(o, 3, dv); fill_ghosts(o, th, dv);
+    if (k < 2) {
+        *kg = IX(o, k == 0 ? -g : o->nx - 1 + g, t);
+        *km = IX(o, k == 0 ? g - 1 : o->nx - g, t);
+    } else {
+        *kg = IX(o, t, k == 2 ? -g : o->ny - 1 + g);
+        *km = IX(o, t, k == 2 ? g - 1 : o->ny - g);
+    }
 }
-
-/* Wall side k (2: y-, 3: y+): ghost row g (1 or 2) and the interior row it
- * mirrors about the wall, which lies half-way between row -1 and row 0 (or
- * between rows ny - 1 and ny). */
-static int wall_ghost_row(const hlbmo *o, int k, int g) { return k == 2 ? -g : o->ny - 1 + g; }
-static int wall_mirror_row(const hlbmo *o, int k, int g) { return k == 2 ? g - 1 : o->ny - g; }
 
 static double entropy_of(const hlbmo *o, double rho, double th);
 
-/* Ghost macros of the wall sides over the full padded width (the x ghosts
- * of the mirrored rows are filled first, so a wall wins at a corner): rho
- * mirrored, u reflected about the wall velocity, theta about the wall
- * temperature, s of the ghost rho and theta. */
-static void fill_wall_macros(hlbmo *o, double *rho, double *ux, double *uy, double *th, double *s)
+/* Ghost macros of the wall sides k0, k0 + 1: u reflected about the wall
+ * velocity, theta about the wall temperature, the mirrored cell's pressure
+ * (rho_g theta_g = rho theta), s of the ghost rho and theta. */
+static void wall_macros(hlbmo *o, int k0, double *rho, double *ux, double *uy, double *th, double *s)
 {
-    for (int k = 2; k < 4; k++) {
+    for (int k = k0; k < k0 + 2; k++) {
         if (o->bc[k] != BC_WALL) continue;
         const double uw = o->bcs[k][1], vw = o->bcs[k][2], tw = o->bcs[k][3];
+        int t0;
+        const int n = wall_span(o, k, &t0);
         for (int g = 1; g <= G; g++)
-            for (int x = -G; x < o->nx + G; x++) {
-                const int kg = IX(o, x, wall_ghost_row(o, k, g)), km = IX(o, x, wall_mirror_row(o, k, g));
+            for (int t = t0; t < t0 + n; t++) {
+                int kg, km;
+                wall_cells(o, k, g, t, &kg, &km);
                 ux[kg] = 2.0 * uw - ux[km];
                 uy[kg] = 2.0 * vw - uy[km];
                 th[kg] = 2.0 * tw - th[km];
@@ -365,6 +378,21 @@ static void fill_wall_macros(hlbmo *o, double *rho, double *ux, double *uy, doub
                 s[kg] = entropy_of(o, rho[kg], th[kg]);
             }
     }
+}
+
+/* The ghost frame of a level's rho, u, theta and s: x sides (x walls
+ * mirror the interior columns), then y sides over the full width (y walls
+ * mirror rows whose x ghosts are already filled). */
+static void fill_level(hlbmo *o, double *rho, double *ux, double *uy, double *th, double *s)
+{
+    double *f[4] = {rho, ux, uy, th};
+    double dv[4];
+    for (int q = 0; q < 4; q++) { side_values(o, q, dv); fill_x(o, f[q], dv); }
+    fill_x(o, s, o->b_s);
+    wall_macros(o, 0, rho, ux, uy, th, s);
+    for (int q = 0; q < 4; q++) { side_values(o, q, dv); fill_y(o, f[q], dv); }
+    fill_y(o, s, o->b_s);
+    wall_macros(o, 2, rho, ux, uy, th, s);
 }
 
 static double *alloc_field(const hlbmo *o)
@@ -400,9 +428,8 @@ hlbmo *hlbmo_create(int nx, int ny, double gamma, double Pr, double mu, double s
         o->bc[k] = bc[k];
         for (int q = 0; q < 4; q++) o->bcs[k][q] = bc_state ? bc_state[4 * k + q] : 0.0;
         if (bc[k] < BC_PERIODIC || bc[k] > BC_WALL) { free(o); return NULL; }
-        /* walls on the y sides only, with a positive temperature and two
-         * interior rows to mirror */
-        if (bc[k] == BC_WALL && (k < 2 || ny < 2 || !(o->bcs[k][3] > 0.0))) { free(o); return NULL; }
+        /* walls need a positive temperature and two interior layers to mirror */
+        if (bc[k] == BC_WALL && ((k < 2 ? nx : ny) < 2 || !(o->bcs[k][3] > 0.0))) { free(o); return NULL; }
     }
     /* c_v = c_s^2/(gamma-1), c_p = gamma c_s^2/(gamma-1) (Sec. 2.4).
      * Heat conductivity lambda = mu c_p / Pr, the definition of the Prandtl
@@ -524,9 +551,7 @@ int hlbmo_init(hlbmo *o, const double *rho0, const double *ux0, const double *uy
             o->rho[k] = rho0[c]; o->ux[k] = ux0[c]; o->uy[k] = uy0[c]; o->th[k] = th0[c];
             o->s[k] = entropy_of(o, rho0[c], th0[c]);
         }
-    fill_macros(o, o->rho, o->ux, o->uy, o->th);
-    fill_ghosts(o, o->s, o->b_s);
-    fill_wall_macros(o, o->rho, o->ux, o->uy, o->th, o->s);
+    fill_level(o, o->rho, o->ux, o->uy, o->th, o->s);
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             const int c = y * o->nx + x, k = IX(o, x, y);
@@ -550,28 +575,57 @@ int hlbmo_init(hlbmo *o, const double *rho0, const double *ux0, const double *uy
     return 0;
 }
 
-/* Post-collision populations of the wall ghost rows: the regularised
- * formula of eq streamalgo from the ghost macros of level n and the a1 of
- * the mirrored cell (a Dirichlet x ghost has a1 = 0), without psi. */
-static void wall_populations(hlbmo *o)
+/* a1 on the ghost frame, for the wall populations: copies on periodic and
+ * zero-gradient sides, 0 on Dirichlet sides, the mirrored cell's a1 on wall
+ * sides (x sides first, then y sides over the full width). */
+static void fill_a1_ghosts(hlbmo *o)
 {
     const double zero[4] = {0.0, 0.0, 0.0, 0.0};
-    fill_ghosts(o, o->axx, zero);
-    fill_ghosts(o, o->axy, zero);
-    fill_ghosts(o, o->ayy, zero);
-    for (int k = 2; k < 4; k++) {
+    double *a[3] = {o->axx, o->axy, o->ayy};
+    for (int pass = 0; pass < 2; pass++) {
+        for (int q = 0; q < 3; q++) (pass == 0 ? fill_x : fill_y)(o, a[q], zero);
+        for (int k = 2 * pass; k < 2 * pass + 2; k++) {
+            if (o->bc[k] != BC_WALL) continue;
+            int t0;
+            const int n = wall_span(o, k, &t0);
+            for (int g = 1; g <= G; g++)
+                for (int t = t0; t < t0 + n; t++) {
+                    int kg, km;
+                    wall_cells(o, k, g, t, &kg, &km);
+                    for (int q = 0; q < 3; q++) a[q][kg] = a[q][km];
+                }
+        }
+    }
+}
+
+/* Post-collision populations of the wall ghost layers of sides k0, k0 + 1:
+ * the regularised formula of eq streamalgo from the ghost macros of level n
+ * and the mirrored cell's a1, without psi. */
+static void wall_populations(hlbmo *o, int k0)
+{
+    for (int k = k0; k < k0 + 2; k++) {
         if (o->bc[k] != BC_WALL) continue;
+        int t0;
+        const int n = wall_span(o, k, &t0);
         for (int g = 1; g <= G; g++)
-            for (int x = -G; x < o->nx + G; x++) {
-                const int kg = IX(o, x, wall_ghost_row(o, k, g)), km = IX(o, x, wall_mirror_row(o, k, g));
+            for (int t = t0; t < t0 + n; t++) {
+                int kg, km;
+                wall_cells(o, k, g, t, &kg, &km);
                 const double p = o->rho[kg] * CS2 * o->th[kg];
                 const double taub = o->mu / p + 0.5;
                 double feq[Q], f1[Q];
                 hlbmo_feq_cell(o->rho[kg], o->ux[kg], o->uy[kg], o->th[kg], feq);
-                hlbmo_f1_cell(o->axx[km], o->axy[km], o->ayy[km], o->ux[kg], o->uy[kg], o->th[kg], f1);
+                hlbmo_f1_cell(o->axx[kg], o->axy[kg], o->ayy[kg], o->ux[kg], o->uy[kg], o->th[kg], f1);
                 for (int i = 0; i < Q; i++) o->F[i][kg] = feq[i] + (1.0 - 1.0 / taub) * f1[i];
             }
     }
+}
+
+static int has_wall(const hlbmo *o)
+{
+    for (int k = 0; k < 4; k++)
+        if (o->bc[k] == BC_WALL) return 1;
+    return 0;
 }
 
 /* Algorithm 1, step 5 for every interior cell: F_i = f^eq_i + (1 - 1/tau_bar)
@@ -588,12 +642,16 @@ static void collide(hlbmo *o)
             for (int i = 0; i < Q; i++)
                 o->F[i][k] = o->feq[i][k] + (1.0 - 1.0 / taub) * f1[i] + 0.5 * o->psi[i][k];
         }
-    for (int i = 0; i < Q; i++) {
-        double dv[4];
-        for (int s = 0; s < 4; s++) dv[s] = o->b_feq[s][i];
-        fill_ghosts(o, o->F[i], dv);
+    const int walls = has_wall(o);
+    if (walls) fill_a1_ghosts(o);
+    for (int pass = 0; pass < 2; pass++) {
+        for (int i = 0; i < Q; i++) {
+            double dv[4];
+            for (int s = 0; s < 4; s++) dv[s] = o->b_feq[s][i];
+            (pass == 0 ? fill_x : fill_y)(o, o->F[i], dv);
+        }
+        if (walls) wall_populations(o, 2 * pass);
     }
-    if (o->bc[2] == BC_WALL || o->bc[3] == BC_WALL) wall_populations(o);
 }
 
 /* Entropy right-hand side of eq (sequaalgo) at level n (Algorithm 1, step 7):
@@ -676,9 +734,7 @@ int hlbmo_step(hlbmo *o, long nsteps)
                 const int k = IX(o, x, y);
                 o->th1[k] = theta_of(o, o->rho1[k], o->s1[k]);
             }
-        fill_macros(o, o->rho1, o->ux1, o->uy1, o->th1);
-        fill_ghosts(o, o->s1, o->b_s);
-        fill_wall_macros(o, o->rho1, o->ux1, o->uy1, o->th1, o->s1);
+        fill_level(o, o->rho1, o->ux1, o->uy1, o->th1, o->s1);
         /* step 9: psi at n+1 */
         compute_psi(o, o->rho1, o->ux1, o->uy1, o->th1, o->psi1);
         /* step 10: f^eq at n+1 */
