@@ -57,18 +57,20 @@ enum { HLBM_FP64 = 0, HLBM_FP32 = 1, HLBM_FP32_F16POP = 2, HLBM_FP32_BF16POP = 3
 /* boundary kind per side (Sec. 4-5 use periodic, zero-gradient and imposed
  * states and walls; the paper refers their exact form to an earlier work)
  *
- * HLBM_BC_WALL (y sides only; HLBM_ERR_UNSUPPORTED on an x side, with
- * HLBM_FP32_MOMENTS and in batches; HLBM_ERR_ARG if ny < 2 or the wall
- * temperature is not positive): a no-slip wall moving at (u_w, v_w) =
- * (bc_state[side][1], bc_state[side][2]) at temperature theta_w =
- * bc_state[side][3] (bc_state[side][0] is ignored), placed half-way between
- * the last interior row and the first ghost row, so two walls are ny apart.  Ghost row g mirrors interior row g - 1: u_g = 2 u_w -
- * u, theta_g = 2 theta_w - theta, rho_g = rho theta / theta_g (the interior
- * pressure, so no mass crosses the wall to first order), s from rho_g and
- * theta_g, and populations f^eq + (1 - 1/tau_bar) f1 built from those macros
- * and the mirrored cell's a1 (no psi).  A case with a wall runs the tiled
- * kernel, plus one thin ghost-row kernel per step.  Mass is conserved only
- * to the wall's first-order flux balance (Couette: 3e-4 over 1e5 steps). */
+ * HLBM_BC_WALL (any side; HLBM_ERR_UNSUPPORTED with HLBM_FP32_MOMENTS and
+ * in batches; HLBM_ERR_ARG if the grid has fewer than 2 cells across the
+ * wall or the wall temperature is not positive): a no-slip wall moving at
+ * (u_w, v_w) = (bc_state[side][1], bc_state[side][2]) at temperature
+ * theta_w = bc_state[side][3] (bc_state[side][0] is ignored), placed
+ * half-way between the last interior layer and the first ghost layer, so
+ * two walls are ny (or nx) apart.  Ghost layer g mirrors interior layer
+ * g - 1: u_g = 2 u_w - u, theta_g = 2 theta_w - theta, rho_g = rho theta /
+ * theta_g (the interior pressure, so no mass crosses the wall to first
+ * order), s from rho_g and theta_g, and populations f^eq + (1 - 1/tau_bar)
+ * f1 built from those macros and the mirrored cell's a1 (no psi).  A case
+ * with a wall runs the tiled kernel, plus one thin ghost-layer kernel per
+ * step.  Mass is conserved only to the wall's first-order flux balance
+ * (Couette: 3e-4 over 1e5 steps). */
 enum {
     HLBM_BC_PERIODIC = 0,  /* wrap to the opposite side */
     HLBM_BC_ZEROGRAD = 1,  /* every quantity copies the nearest interior cell */
@@ -95,7 +97,7 @@ enum {
 /* Side order of bc[] and bc_state[]: x-, x+, y-, y+.  bc_state[k] holds the
  * imposed (rho, ux, uy, theta) of a Dirichlet side k, or (unused, u_w, v_w,
  * theta_w) of a wall side k.  At a corner cell a Dirichlet or wall y side
- * takes precedence, then a Dirichlet x side. */
+ * takes precedence, then a Dirichlet or wall x side. */
 typedef struct {
     int32_t nx, ny;        /* interior cells, >= 1 each */
     int32_t precision;     /* HLBM_FP64, HLBM_FP32, HLBM_FP32_F16POP, HLBM_FP32_BF16POP or HLBM_FP32_MOMENTS */

@@ -5,6 +5,7 @@
 // hlbm_step only launches kernels on the handle's stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -403,7 +404,7 @@ static cudaError_t launch_wall_ghosts(hlbm_handle *h)
     return with_types(h, [&](auto ty) {
         using T = typename decltype(ty)::t;
         using S = typename decltype(ty)::s;
-        dim3 grid((h->kp.wall_p + 127) / 128, 4);
+        dim3 grid((std::max(h->kp.wall_p, h->kp.wall_q) + 127) / 128, 8);
         wall_ghost_kernel<T, S><<<grid, 128, 0, h->stream>>>(pop_planes<T, S>(h, h->cur), aux_planes<T, S>(h, h->cur),
                                                              h->kp);
         return cudaGetLastError();
@@ -485,9 +486,8 @@ static int validate(const hlbm_params *p)
         if (p->bc[k] == HLBM_BC_DIRICHLET && (!(p->bc_state[k][0] > 0.0) || !(p->bc_state[k][3] > 0.0)))
             return HLBM_ERR_ARG;
         if (p->bc[k] == HLBM_BC_WALL) {
-            // y sides only, two interior rows to mirror, a positive temperature
-            if (k < 2) return HLBM_ERR_UNSUPPORTED;
-            if (p->ny < 2 || !(p->bc_state[k][3] > 0.0)) return HLBM_ERR_ARG;
+            // two interior layers to mirror, a positive temperature
+            if ((k < 2 ? p->nx : p->ny) < 2 || !(p->bc_state[k][3] > 0.0)) return HLBM_ERR_ARG;
             if (!std::isfinite(p->bc_state[k][1]) || !std::isfinite(p->bc_state[k][2])) return HLBM_ERR_ARG;
             if (p->precision == HLBM_FP32_MOMENTS) return HLBM_ERR_UNSUPPORTED;
         }
@@ -632,11 +632,12 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         return HLBM_ERR_CUDA;
     }
     fill_kparams(h);
-    h->walls = params->bc[2] == HLBM_BC_WALL || params->bc[3] == HLBM_BC_WALL;
+    h->walls = false;
+    for (int k = 0; k < 4; k++) h->walls = h->walls || params->bc[k] == HLBM_BC_WALL;
     if (h->walls) {
-        // ghost rows for the tiled kernel; walls never take the marching or
-        // TMA kernels
-        const size_t wb = (size_t)kWallPlanes * 4 * (params->nx + 4) * h->asize;
+        // ghost layers for the tiled kernel; walls never take the marching
+        // or TMA kernels
+        const size_t wb = (size_t)kWallPlanes * 4 * ((params->nx + 4) + (params->ny + 4)) * h->asize;
         if (cudaMalloc(&h->wall_g, wb) != cudaSuccess) {
             cudaGetLastError();
             hlbm_destroy(h);
@@ -644,6 +645,7 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         }
         h->kp.wall_g = h->wall_g;
         h->kp.wall_p = params->nx + 4;
+        h->kp.wall_q = params->ny + 4;
         h->tile_variant = env_choice("HLBM_FP32_TILE", 4, 0, kNumFp32Tiles);
         *out = h;
         return HLBM_OK;
@@ -1147,7 +1149,8 @@ int hlbm_batch_create(const hlbm_params *params, int ncase, void *stream, hlbm_b
     *out = nullptr;
     for (int c = 0; c < ncase; c++) {
         if (params[c].precision != HLBM_FP32) return HLBM_ERR_UNSUPPORTED;
-        if (params[c].bc[2] == HLBM_BC_WALL || params[c].bc[3] == HLBM_BC_WALL) return HLBM_ERR_UNSUPPORTED;
+        for (int k = 0; k < 4; k++)
+            if (params[c].bc[k] == HLBM_BC_WALL) return HLBM_ERR_UNSUPPORTED;
     }
     hlbm_batch *b = new (std::nothrow) hlbm_batch();
     if (!b) return HLBM_ERR_NOMEM;

@@ -41,15 +41,17 @@
 // the domain is the value at the mapped cell; for clamped sides it is copied
 // from the tile's own edge after phase 2.  A Dirichlet y side wins at a
 // corner, then a Dirichlet x side.
-// Wall sides (y only, tiled kernel): a no-slip, fixed-temperature wall
-// half-way between the first ghost row and the first interior row.  Ghost
-// row g mirrors interior row g - 1: u reflected about the wall velocity,
-// theta about the wall temperature, the pressure of the mirrored cell
-// (rho_g theta_g = rho theta), s of that rho and theta, and post-collision
+// Wall sides (tiled kernel): a no-slip, fixed-temperature wall half-way
+// between the first ghost layer and the first interior layer.  Ghost layer g
+// mirrors interior layer g - 1: u reflected about the wall velocity, theta
+// about the wall temperature, the pressure of the mirrored cell (rho_g
+// theta_g = rho theta), s of that rho and theta, and post-collision
 // populations rebuilt from them and the mirrored cell's a1 by the collision
-// formula without psi.  wall_ghost_kernel writes the level-n ghost rows to a
-// small buffer before each step; the level-(n+1) ghosts are mirrored inside
-// the tile after phase 2.
+// formula without psi.  A wall or Dirichlet y side wins at a corner; the
+// x ghosts of a wall row's mirrored row are taken first (an x wall's ghost
+// is mirrored once more).  wall_ghost_kernel writes the level-n ghost layers
+// to a small buffer before each step; the level-(n+1) ghosts are mirrored
+// inside the tile after phase 2.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -83,11 +85,12 @@ struct KParams {
     // reference populations subtracted before 16-bit storage (precision
     // forms HLBM_FP32_F16POP / HLBM_FP32_BF16POP; unused otherwise)
     float f_ref[9];
-    // wall ghost rows of level n (arithmetic type): 10 planes (F_0..F_8, s)
-    // of 4 rows (y- depth 1, 2; y+ depth 1, 2) of wall_p = nx + 4 columns
-    // (x = -2 .. nx + 1); null without wall sides
+    // wall ghost layers of level n (arithmetic type): 10 planes (F_0..F_8,
+    // s), each of 4 rows (y- depth 1, 2; y+ depth 1, 2) of wall_p = nx + 4
+    // columns (x = -2 .. nx + 1), then 4 columns (x- depth 1, 2; x+ depth 1,
+    // 2) of wall_q = ny + 4 rows (y = -2 .. ny + 1); null without wall sides
     void *wall_g;
-    int wall_p;
+    int wall_p, wall_q;
 };
 
 // ---- population storage ----------------------------------------------------------
@@ -179,29 +182,43 @@ __device__ __forceinline__ int locate(int gx, int gy, const KParams &kp, int pit
 }
 
 // locate() with wall sides: a coordinate beyond a wall maps to the wall
-// ghost buffer, returned as -(kWallCode + index) with index = row * wall_p +
-// x + 2 (row = (side - 2) * 2 + depth - 1; the depth is clamped to 2 and x
-// to [-2, nx + 1], which covers every ghost value a tile reads).
+// ghost buffer, returned as -(kWallCode + index).  A y wall (checked first,
+// so that it wins at a corner) gives index = row * wall_p + x + 2 (row =
+// (side - 2) * 2 + depth - 1, x clamped to [-2, nx + 1]); otherwise y is
+// mapped and an x wall gives index = 4 wall_p + col * wall_q + y + 2 (col =
+// side * 2 + depth - 1).  Depths are clamped to 2, which covers every ghost
+// value a tile reads.
 constexpr int kWallCode = 8;
 constexpr int kWallPlanes = 10;
 __device__ __forceinline__ int locate_w(int gx, int gy, const KParams &kp, int pitch)
 {
     if (gy < 0 || gy >= kp.ny) {
         const int s = gy < 0 ? 2 : 3;
-        if (kp.bc[s] == BC_WALL) {
+        const int b = kp.bc[s];
+        if (b == BC_WALL) {
             const int d = min(gy < 0 ? -gy : gy - kp.ny + 1, 2);
             const int x = min(max(gx, -2), kp.nx + 1);
             return -(kWallCode + ((s - 2) * 2 + d - 1) * kp.wall_p + x + 2);
         }
+        if (b == BC_DIRICHLET) return -(s + 1);
+        gy = (b == BC_PERIODIC) ? wrapi(gy, kp.ny) : (gy < 0 ? 0 : kp.ny - 1);
+    }
+    if ((gx < 0 || gx >= kp.nx) && kp.bc[gx < 0 ? 0 : 1] == BC_WALL) {
+        const int s = gx < 0 ? 0 : 1;
+        const int d = min(gx < 0 ? -gx : gx - kp.nx + 1, 2);
+        return -(kWallCode + 4 * kp.wall_p + (s * 2 + d - 1) * kp.wall_q + gy + 2);
     }
     return locate(gx, gy, kp, pitch);
 }
+
+// Whether a wall code belongs to an x wall.
+__device__ __forceinline__ bool wall_is_x(int o, const KParams &kp) { return -o - kWallCode >= 4 * kp.wall_p; }
 
 // Plane q (0..8 populations, 9 entropy) of wall ghost index w.
 template <typename T>
 __device__ __forceinline__ T wall_val(const KParams &kp, int w, int q)
 {
-    return static_cast<const T *>(kp.wall_g)[(size_t)q * 4 * kp.wall_p + w];
+    return static_cast<const T *>(kp.wall_g)[(size_t)q * (4 * kp.wall_p + 4 * kp.wall_q) + w];
 }
 
 // ---- FP32 hardware approximations ------------------------------------------
@@ -323,13 +340,14 @@ struct TileGeom {
 
 // Classification of a tile + 1 cell for phase 2: 0 compute, 1 Dirichlet
 // constant (side in *side), 2 copy from the clamped cell, 3 mirror of the
-// interior cell across a wall.
+// first interior row across a y wall, 4 of the first interior column across
+// an x wall.
 __device__ __forceinline__ int classify_r1(int gx, int gy, const KParams &kp, int *side)
 {
     const bool outx = gx < 0 || gx >= kp.nx, outy = gy < 0 || gy >= kp.ny;
     if (!outx && !outy) return 0;
     const int o = locate_w(gx, gy, kp, kp.pitch);
-    if (o <= -kWallCode) return 3;
+    if (o <= -kWallCode) return wall_is_x(o, kp) ? 4 : 3;
     if (o < 0) { *side = -o - 1; return 1; }
     const bool cx = outx && kp.bc[gx < 0 ? 0 : 1] == BC_ZEROGRAD;
     const bool cy = outy && kp.bc[gy < 0 ? 2 : 3] == BC_ZEROGRAD;
@@ -540,23 +558,28 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
         }
         __syncthreads();
         if (kp.wall_g) {
-            // wall sides: mirror the first interior row (after the clamped
-            // copies, which the mirrored row may hold at a corner)
-            for (int c = threadIdx.x; c < N1; c += NT) {
-                const int ly = c / R1X, lx = c - ly * R1X;
-                const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-                int sd = 0;
-                if (classify_r1(gx, gy, kp, &sd) != 3) continue;
-                const int ws = gy < 0 ? 2 : 3;
-                const int src = c + (gy < 0 ? R1X : -R1X);  // rows 0 and ny - 1
-                const T th = T(2) * side.th(ws) - nTh[src];
-                nTh[c] = th;
-                nRho[c] = fdiv(nRho[src] * nTh[src], th);
-                nUx[c] = T(2) * side.ux(ws) - nUx[src];
-                nUy[c] = T(2) * side.uy(ws) - nUy[src];
-                nS[c] = T(0);  // not read: phase 3 uses the entropy of its own cell only
+            // wall sides: mirror the first interior column (x walls, after
+            // the clamped copies, which the mirrored column may hold at a
+            // corner), then the first interior row (y walls, whose mirrored
+            // row may hold x-wall ghosts)
+            for (int pass = 4; pass >= 3; pass--) {
+                for (int c = threadIdx.x; c < N1; c += NT) {
+                    const int ly = c / R1X, lx = c - ly * R1X;
+                    const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+                    int sd = 0;
+                    if (classify_r1(gx, gy, kp, &sd) != pass) continue;
+                    const int ws = pass == 4 ? (gx < 0 ? 0 : 1) : (gy < 0 ? 2 : 3);
+                    // columns 0 / nx - 1, rows 0 / ny - 1
+                    const int src = pass == 4 ? c + (gx < 0 ? 1 : -1) : c + (gy < 0 ? R1X : -R1X);
+                    const T th = T(2) * side.th(ws) - nTh[src];
+                    nTh[c] = th;
+                    nRho[c] = fdiv(nRho[src] * nTh[src], th);
+                    nUx[c] = T(2) * side.ux(ws) - nUx[src];
+                    nUy[c] = T(2) * side.uy(ws) - nUy[src];
+                    nS[c] = T(0);  // not read: phase 3 uses the entropy of its own cell only
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
 
@@ -672,55 +695,91 @@ batched_step_kernel(const BatchTables tab, const int parity)
     }
 }
 
-// ---- wall ghost rows of level n --------------------------------------------------
-// One thread per ghost cell: x = -2 .. nx + 1 (blockIdx.x, threadIdx.x) and
-// row = (side - 2) * 2 + depth - 1 (blockIdx.y).  The mirrored cell's rho and
-// u are the moments of its F(n), theta follows from its s(n); an x ghost of
-// the mirrored row takes the x side's map (a Dirichlet x side gives its
-// constants and a1 = 0).
+// ---- wall ghost layers of level n -----------------------------------------------
+// One thread per ghost cell (blockIdx.x, threadIdx.x along the wall;
+// blockIdx.y = layer): layers 0-3 are the y walls' rows (side 2 + layer / 2,
+// depth layer % 2 + 1) over x = -2 .. nx + 1, layers 4-7 the x walls'
+// columns (side (layer - 4) / 2, depth layer % 2 + 1) over y = -2 .. ny + 1.
+// The mirrored cell's rho and u are the moments of its F(n), theta follows
+// from its s(n), a1 is its own.  A cell beyond an x side takes the x side's
+// map: a Dirichlet x side gives its constants and a1 = 0, an x wall the
+// reflection of the cell it mirrors (so a y wall's corner ghost is mirrored
+// twice).
+template <typename T>
+struct WallCell {
+    T rho, ux, uy, th, axx, axy, ayy;
+};
+
+template <typename T>
+__device__ __forceinline__ void wall_reflect(const Side<T> &side, int ws, WallCell<T> &c)
+{
+    const T tg = T(2) * side.th(ws) - c.th;
+    c.rho = fdiv(c.rho * c.th, tg);
+    c.th = tg;
+    c.ux = T(2) * side.ux(ws) - c.ux;
+    c.uy = T(2) * side.uy(ws) - c.uy;
+}
+
 template <typename T, typename S>
 __global__ void wall_ghost_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
                                   const KParams kp)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int row = blockIdx.y;
-    const int ws = 2 + row / 2, depth = row % 2 + 1;
-    if (i >= kp.wall_p || kp.bc[ws] != BC_WALL) return;
+    const int layer = blockIdx.y;
+    const bool xw = layer >= 4;
+    const int ws = xw ? (layer - 4) / 2 : 2 + layer / 2, depth = layer % 2 + 1;
+    if (i >= (xw ? kp.wall_q : kp.wall_p) || kp.bc[ws] != BC_WALL) return;
     Consts<T> cs;
     cs.load(kp);
     const Side<T> side{kp};
     const long long P = kp.plane;
-    const int o = locate(i - 2, ws == 2 ? depth - 1 : kp.ny - depth, kp, kp.pitch);
-    T rho, ux, uy, th, axx = T(0), axy = T(0), ayy = T(0);
+    // the interior cell this ghost mirrors: (column, row)
+    int mx, my;
+    if (xw) {
+        mx = ws == 0 ? depth - 1 : kp.nx - depth;
+        my = i - 2;
+    } else {
+        mx = i - 2;
+        my = ws == 2 ? depth - 1 : kp.ny - depth;
+    }
+    // beyond an x wall (a y wall's corner): mirror across it first
+    int xwall = -1;
+    if (!xw && (mx < 0 || mx >= kp.nx) && kp.bc[mx < 0 ? 0 : 1] == BC_WALL) {
+        xwall = mx < 0 ? 0 : 1;
+        mx = mx < 0 ? -mx - 1 : 2 * kp.nx - 1 - mx;
+    }
+    const int o = locate(mx, my, kp, kp.pitch);
+    WallCell<T> c;
+    c.axx = c.axy = c.ayy = T(0);
     if (o >= 0) {
         T f[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) f[q] = S::get(inF[q * P + o], q, kp);
         T jx, jy;
-        moments(f, rho, jx, jy);
-        const T ir = fdiv(T(1), rho);
-        ux = jx * ir;
-        uy = jy * ir;
-        th = cs.theta(rho, inA[A_S * P + o]);
-        axx = inA[A_XX * P + o];
-        axy = inA[A_XY * P + o];
-        ayy = inA[A_YY * P + o];
+        moments(f, c.rho, jx, jy);
+        const T ir = fdiv(T(1), c.rho);
+        c.ux = jx * ir;
+        c.uy = jy * ir;
+        c.th = cs.theta(c.rho, inA[A_S * P + o]);
+        c.axx = inA[A_XX * P + o];
+        c.axy = inA[A_XY * P + o];
+        c.ayy = inA[A_YY * P + o];
     } else {
         const int sd = -o - 1;
-        rho = side.rho(sd); ux = side.ux(sd); uy = side.uy(sd); th = side.th(sd);
+        c.rho = side.rho(sd); c.ux = side.ux(sd); c.uy = side.uy(sd); c.th = side.th(sd);
     }
-    const T tg = T(2) * side.th(ws) - th;
-    const T rg = fdiv(rho * th, tg);
-    const T ug = T(2) * side.ux(ws) - ux, vg = T(2) * side.uy(ws) - uy;
-    const T p = rho * th * (T(1) / T(3));
+    if (xwall >= 0) wall_reflect(side, xwall, c);
+    const T p = c.rho * c.th * (T(1) / T(3));  // the pressure is kept by every reflection
+    wall_reflect(side, ws, c);
     const T omega = fdiv(cs.two_mu - p, cs.two_mu + p);
     T f[9];
-    build_populations(rg, ug, vg, tg, axx, axy, ayy, T(0), T(0), omega, f);
+    build_populations(c.rho, c.ux, c.uy, c.th, c.axx, c.axy, c.ayy, T(0), T(0), omega, f);
     T *wg = static_cast<T *>(kp.wall_g);
-    const size_t w = (size_t)row * kp.wall_p + i, stride = (size_t)4 * kp.wall_p;
+    const size_t w = xw ? (size_t)4 * kp.wall_p + (size_t)(layer - 4) * kp.wall_q + i : (size_t)layer * kp.wall_p + i;
+    const size_t stride = (size_t)4 * kp.wall_p + (size_t)4 * kp.wall_q;
 #pragma unroll
     for (int q = 0; q < 9; q++) wg[q * stride + w] = f[q];
-    wg[9 * stride + w] = (T)(kp.cv * (log((double)tg) - kp.gm1 * log((double)rg)));
+    wg[9 * stride + w] = (T)(kp.cv * (log((double)c.th) - kp.gm1 * log((double)c.rho)));
 }
 
 // ---- initialisation (Algorithm 1, steps 1-4) -----------------------------------
@@ -736,14 +795,20 @@ __global__ void init_kernel(const double *__restrict__ rho, const double *__rest
     if (gx >= kp.nx || gy >= kp.ny) return;
     const int n = kp.nx * kp.ny;
     auto at = [&](int dx, int dy, double &r, double &u, double &v, double &t) {
-        const int yy = gy + dy;
-        const bool wall = (yy < 0 || yy >= kp.ny) && kp.bc[yy < 0 ? 2 : 3] == BC_WALL;
+        int xx = gx + dx, yy = gy + dy;  // one of them at most is outside
+        int ws = -1;
         // beyond a wall: the mirrored interior cell, reflected (see wall_ghost_kernel)
-        const int o = locate(gx + dx, wall ? (yy < 0 ? -yy - 1 : 2 * kp.ny - 1 - yy) : yy, kp, kp.nx);
+        if ((yy < 0 || yy >= kp.ny) && kp.bc[yy < 0 ? 2 : 3] == BC_WALL) {
+            ws = yy < 0 ? 2 : 3;
+            yy = yy < 0 ? -yy - 1 : 2 * kp.ny - 1 - yy;
+        } else if ((xx < 0 || xx >= kp.nx) && kp.bc[xx < 0 ? 0 : 1] == BC_WALL) {
+            ws = xx < 0 ? 0 : 1;
+            xx = xx < 0 ? -xx - 1 : 2 * kp.nx - 1 - xx;
+        }
+        const int o = locate(xx, yy, kp, kp.nx);
         if (o >= 0) { r = rho[o]; u = ux[o]; v = uy[o]; t = th[o]; }
         else { const int s = -o - 1; r = kp.d_rho[s]; u = kp.d_ux[s]; v = kp.d_uy[s]; t = kp.d_th[s]; }
-        if (wall) {
-            const int ws = yy < 0 ? 2 : 3;
+        if (ws >= 0) {
             const double tg = 2.0 * kp.d_th[ws] - t;
             r = r * t / tg;
             t = tg;

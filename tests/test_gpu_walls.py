@@ -1,9 +1,9 @@
-"""Wall sides (no-slip, fixed temperature, y sides) on the GPU against the
-FP64 oracle, with the tolerances of the other parity tests (1e-10 FP64,
-1e-4 FP32): moving and resting walls at temperatures above and below the
-gas, periodic, zero-gradient and Dirichlet x sides (corners), sigma = 0 and
-> 0, both Phi forms, grids from two rows to several tiles with ragged
-tails.  Walls always take the tiled kernel, whatever the kernel-choice
+"""Wall sides (no-slip, fixed temperature) on the GPU against the FP64
+oracle, with the tolerances of the other parity tests (1e-10 FP64, 1e-4
+FP32): moving and resting walls at temperatures above and below the gas, on
+the y sides, the x sides and all four, with periodic, zero-gradient and
+Dirichlet partner sides (corners), sigma = 0 and > 0, both Phi forms, grids
+from two cells across to several tiles with ragged tails.  Walls always take the tiled kernel, whatever the kernel-choice
 variables say; the 16-bit storage forms stay within their error bounds;
 and the thermal Couette flow (Sec. 4.4) matches the analytic profile."""
 import numpy as np
@@ -45,6 +45,25 @@ def wall_case(nx, ny, xbc=(0, 0), sigma=0.5, seed=21, phi_mode=0):
 @pytest.mark.parametrize("xbc", [(0, 0), (1, 1), (2, 1)])
 def test_walls_against_oracle(hl, precision, nx, ny, xbc):
     case = wall_case(nx, ny, xbc, seed=100 + nx)
+    _, _, got, ref = run_pair(hl, case, precision, 15)
+    compare(got, ref, case.gamma, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("nx,ny", [(2, 1), (3, 5), (41, 37), (67, 101)])
+@pytest.mark.parametrize("bc", [(W, W, 0, 0), (W, W, 1, 1), (W, W, 2, 1), (W, W, W, W), (1, W, W, 1)],
+                         ids=["xwall-per", "xwall-zg", "xwall-dir", "all-walls", "mixed"])
+def test_x_walls_against_oracle(hl, precision, nx, ny, bc):
+    """Walls on the x sides (and on all four), every kind of partner side,
+    corners included."""
+    if (bc[2] == W or bc[3] == W) and ny < 2:
+        pytest.skip("a y wall needs two rows")
+    bs = BS[[2, 3, 0, 1]][:, [0, 2, 1, 3]].copy()  # x walls: wall velocity along y
+    bs[2:] = BS[2:]
+    if bc[2] == 2:
+        bs[2] = BS[0]
+    case = inputs.random_smooth(nx, ny, seed=300 + nx, amp=0.04, u0=(0.01, 0.06), theta0=0.2, mu=3e-3,
+                                sigma=0.5, bc=bc, bc_state=bs)
     _, _, got, ref = run_pair(hl, case, precision, 15)
     compare(got, ref, case.gamma, TOL[precision])
 

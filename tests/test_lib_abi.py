@@ -90,12 +90,12 @@ def test_invalid_params_rejected_without_touching_the_gpu(lib):
 
 
 def test_wall_sides_validated_without_touching_the_gpu(lib):
-    """Walls: y sides only, ny >= 2, a positive wall temperature, no moment
-    state and no batches; each is refused before any CUDA call."""
+    """Walls: two cells across the wall, a positive wall temperature, no
+    moment state and no batches; each is refused before any CUDA call."""
     from paper_2002_03644_gb300 import hlbm
     W, P = hlbm.HLBM_BC_WALL, hlbm.HLBM_BC_PERIODIC
     bs = [[1.0, 0.0, 0.0, 0.2]] * 4
-    cases = [(dict(bc=(W, W, P, P)), hlbm.HLBM_ERR_UNSUPPORTED),
+    cases = [(dict(bc=(W, W, P, P), nx=1), hlbm.HLBM_ERR_ARG),
              (dict(bc=(P, P, W, W), ny=1), hlbm.HLBM_ERR_ARG),
              (dict(bc=(P, P, W, W), bc_state=[[1.0, 0.0, 0.0, 0.2]] * 3 + [[1.0, 0.0, 0.0, 0.0]]), hlbm.HLBM_ERR_ARG),
              (dict(bc=(P, P, W, W), precision=hlbm.HLBM_FP32_MOMENTS), hlbm.HLBM_ERR_UNSUPPORTED)]
