@@ -181,7 +181,7 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_name(precision, cells, sigma=0.0, phi_mode=0):
+def kernel_name(precision, cells, sigma=0.0, phi_mode=0, periodic=False):
     """The fused-step kernel the library launches for this precision: the
     row-marching kernel for FP32 and the 16-bit forms on grids of more than
     768^2 cells unless HLBM_MARCH=-1 (then the tiled kernels, chosen by
@@ -194,8 +194,11 @@ def kernel_name(precision, cells, sigma=0.0, phi_mode=0):
         t = {"fp64": "double,FullStore<double>", "fp16pop": "float,HalfStore", "bf16pop": "float,BF16Store"}
         f64 = precision == "fp64"
         nt, minb = [(64, 8), (96, 5), (128, 4), (64, 1)][march]
-        return "march_pair_kernel<%s,%d,%d,%s,%s>" % (t.get(precision, "float,FullStore<float>"), nt, 1 if f64 else minb,
-                                                      str(sigma > 0).lower(), str(phi_mode == 0).lower())
+        # the default FP32 kernel has an instantiation for all-periodic grids
+        per = ",true" if (march == 0 and precision == "fp32" and periodic) else ""
+        return "march_pair_kernel<%s,%d,%d,%s,%s%s>" % (t.get(precision, "float,FullStore<float>"), nt,
+                                                        1 if f64 else minb, str(sigma > 0).lower(),
+                                                        str(phi_mode == 0).lower(), per)
     if precision == "fp64":
         return "fused_step_kernel<double,FullStore<double>,32,8,256>"
     if precision in ("fp16pop", "bf16pop"):
@@ -397,7 +400,8 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(args.precision, args.n),
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
-                "kernel": kernel_name(args.precision, cells, case.sigma, case.phi_mode),
+                "kernel": kernel_name(args.precision, cells, case.sigma, case.phi_mode,
+                                      all(b == 0 for b in case.bc) and case.ny >= 4),
                 "algorithmic_bytes_per_launch": bpc * cells}
     else:
         # FP64 is bound by GB300's FP64 pipe: FP64 operations (add, mul, 2 per

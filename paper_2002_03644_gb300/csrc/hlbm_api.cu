@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -68,6 +69,7 @@ struct hlbm_handle {
     int march_variant = -1;     // row-marching kernel variant, -1: tiled / TMA kernels
     bool moments = false;       // HLBM_FP32_MOMENTS: 7 FP32 planes, moment-state kernel
     bool walls = false;         // a wall side: tiled kernel plus wall_ghost_kernel each step
+    bool periodic = false;      // all four sides periodic and ny >= 4 (specialised marching kernels)
     void *wall_g = nullptr;     // wall ghost rows (KParams::wall_g)
     int march_nseg = 1;         // row segments per strip
     int *d_err = nullptr;       // device-side timeout flag of the TMA kernel
@@ -273,21 +275,21 @@ static int march_segments(const hlbm_handle *h, long long strips, int per_sm, in
 // Paired-column marching kernel with NT threads (strips of 2 (NT - 4)
 // columns), register budget set by MINB resident CTAs per SM; the
 // instantiation matches the handle's sigma > 0 and Phi choice.
-template <typename T, typename S, int NT, int MINB>
+template <typename T, typename S, int NT, int MINB, bool PER = false>
 static void *pair_kernel_ptr(const hlbm_handle *h)
 {
     const bool sig = h->kp.sigma_nonzero != 0, phi0 = h->kp.phi_mode == 0;
-    if (sig) return phi0 ? (void *)march_pair_kernel<T, S, NT, MINB, true, true>
-                         : (void *)march_pair_kernel<T, S, NT, MINB, true, false>;
-    return phi0 ? (void *)march_pair_kernel<T, S, NT, MINB, false, true>
-                : (void *)march_pair_kernel<T, S, NT, MINB, false, false>;
+    if (sig) return phi0 ? (void *)march_pair_kernel<T, S, NT, MINB, true, true, PER>
+                         : (void *)march_pair_kernel<T, S, NT, MINB, true, false, PER>;
+    return phi0 ? (void *)march_pair_kernel<T, S, NT, MINB, false, true, PER>
+                : (void *)march_pair_kernel<T, S, NT, MINB, false, false, PER>;
 }
 
-template <typename T, typename S, int NT, int MINB>
+template <typename T, typename S, int NT, int MINB, bool PER = false>
 static cudaError_t pair_setup(hlbm_handle *h)
 {
     using G = PairGeom<T, NT>;
-    const void *fn = pair_kernel_ptr<T, S, NT, MINB>(h);
+    const void *fn = pair_kernel_ptr<T, S, NT, MINB, PER>(h);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
@@ -299,7 +301,7 @@ static cudaError_t pair_setup(hlbm_handle *h)
     return cudaSuccess;
 }
 
-template <typename T, typename S, int NT, int MINB>
+template <typename T, typename S, int NT, int MINB, bool PER = false>
 static cudaError_t launch_pair(hlbm_handle *h)
 {
     using G = PairGeom<T, NT>;
@@ -311,13 +313,13 @@ static cudaError_t launch_pair(hlbm_handle *h)
     T *outA = aux_planes<T, S>(h, b);
     const bool sig = h->kp.sigma_nonzero != 0, phi0 = h->kp.phi_mode == 0;
     if (sig && phi0)
-        march_pair_kernel<T, S, NT, MINB, true, true><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
+        march_pair_kernel<T, S, NT, MINB, true, true, PER><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
     else if (sig)
-        march_pair_kernel<T, S, NT, MINB, true, false><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
+        march_pair_kernel<T, S, NT, MINB, true, false, PER><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
     else if (phi0)
-        march_pair_kernel<T, S, NT, MINB, false, true><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
+        march_pair_kernel<T, S, NT, MINB, false, true, PER><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
     else
-        march_pair_kernel<T, S, NT, MINB, false, false><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
+        march_pair_kernel<T, S, NT, MINB, false, false, PER><<<grid, NT, G::smem_bytes, h->stream>>>(inF, inA, outF, outA, h->kp, h->march_nseg);
     return cudaGetLastError();
 }
 
@@ -333,7 +335,12 @@ static cudaError_t march_dispatch(hlbm_handle *h)
     case 1: return Launch ? launch_pair<T, S, 96, f64 ? 1 : 5>(h) : pair_setup<T, S, 96, f64 ? 1 : 5>(h);
     case 2: return Launch ? launch_pair<T, S, 128, f64 ? 1 : 4>(h) : pair_setup<T, S, 128, f64 ? 1 : 4>(h);
     case 3: return Launch ? launch_pair<T, S, 64, 1>(h) : pair_setup<T, S, 64, 1>(h);
-    default: return Launch ? launch_pair<T, S, 64, f64 ? 1 : 8>(h) : pair_setup<T, S, 64, f64 ? 1 : 8>(h);
+    default:
+        // the default FP32 kernel has an all-periodic instantiation
+        if constexpr (std::is_same<S, FullStore<float>>::value) {
+            if (h->periodic) return Launch ? launch_pair<T, S, 64, 8, true>(h) : pair_setup<T, S, 64, 8, true>(h);
+        }
+        return Launch ? launch_pair<T, S, 64, f64 ? 1 : 8>(h) : pair_setup<T, S, 64, f64 ? 1 : 8>(h);
     }
 }
 
@@ -633,7 +640,12 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
     }
     fill_kparams(h);
     h->walls = false;
-    for (int k = 0; k < 4; k++) h->walls = h->walls || params->bc[k] == HLBM_BC_WALL;
+    h->periodic = true;
+    for (int k = 0; k < 4; k++) {
+        h->walls = h->walls || params->bc[k] == HLBM_BC_WALL;
+        h->periodic = h->periodic && params->bc[k] == HLBM_BC_PERIODIC;
+    }
+    h->periodic = h->periodic && params->ny >= 4;
     if (h->walls) {
         // ghost layers for the tiled kernel; walls never take the marching
         // or TMA kernels
@@ -944,6 +956,7 @@ struct hlbm_batch {
     MarchItem *d_items = nullptr;  // marching kinds: (case, strip, segment) list
     int nitems = 0;
     bool march_ok = false, sig = false, phi0 = true;
+    bool periodic = false;  // every case periodic on all sides
     int grid = 0;
     size_t smem = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // starting parity 0 / 1
@@ -959,29 +972,42 @@ static cudaError_t batch_launch(hlbm_batch *b, int parity)
     return cudaGetLastError();
 }
 
-template <bool SIG, bool PHI0>
+template <bool SIG, bool PHI0, bool PER>
 static cudaError_t batch_march_launch(hlbm_batch *b, int parity)
 {
     MarchTables tab;
     tab.kps = b->d_kps; tab.planes = b->d_planes; tab.items = b->d_items; tab.nitems = b->nitems;
-    batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, SIG, PHI0><<<b->grid, kBatchMarchNT, b->smem, b->stream>>>(tab, parity);
+    batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, SIG, PHI0, PER><<<b->grid, kBatchMarchNT, b->smem, b->stream>>>(
+        tab, parity);
     return cudaGetLastError();
 }
 
+template <bool PER>
+static const void *batch_march_fn_t(const hlbm_batch *b)
+{
+    if (b->sig) return b->phi0 ? (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, true, true, PER>
+                               : (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, true, false, PER>;
+    return b->phi0 ? (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, false, true, PER>
+                   : (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, false, false, PER>;
+}
+
+// all cases periodic: the specialised kernel
 static const void *batch_march_fn(const hlbm_batch *b)
 {
-    if (b->sig) return b->phi0 ? (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, true, true>
-                               : (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, true, false>;
-    return b->phi0 ? (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, false, true>
-                   : (const void *)batched_march_kernel<kBatchMarchNT, kBatchMarchMinB, false, false>;
+    return b->periodic ? batch_march_fn_t<true>(b) : batch_march_fn_t<false>(b);
+}
+
+template <bool PER>
+static cudaError_t batch_march_launch_any(hlbm_batch *b, int parity)
+{
+    if (b->sig) return b->phi0 ? batch_march_launch<true, true, PER>(b, parity) : batch_march_launch<true, false, PER>(b, parity);
+    return b->phi0 ? batch_march_launch<false, true, PER>(b, parity) : batch_march_launch<false, false, PER>(b, parity);
 }
 
 static cudaError_t batch_launch_any(hlbm_batch *b, int parity)
 {
-    if (b->tile >= kNumBatchTiles) {
-        if (b->sig) return b->phi0 ? batch_march_launch<true, true>(b, parity) : batch_march_launch<true, false>(b, parity);
-        return b->phi0 ? batch_march_launch<false, true>(b, parity) : batch_march_launch<false, false>(b, parity);
-    }
+    if (b->tile >= kNumBatchTiles)
+        return b->periodic ? batch_march_launch_any<true>(b, parity) : batch_march_launch_any<false>(b, parity);
     switch (b->tile) {
     case 1: return batch_launch<64, 16, 256>(b, parity);
     case 2: return batch_launch<32, 8, 128>(b, parity);
@@ -1170,8 +1196,11 @@ int hlbm_batch_create(const hlbm_params *params, int ncase, void *stream, hlbm_b
     b->sig = b->cases[0]->kp.sigma_nonzero != 0;
     b->phi0 = b->cases[0]->kp.phi_mode == 0;
     b->march_ok = true;
-    for (hlbm_handle *h : b->cases)
+    b->periodic = true;
+    for (hlbm_handle *h : b->cases) {
         if ((h->kp.sigma_nonzero != 0) != b->sig || (h->kp.phi_mode == 0) != b->phi0) b->march_ok = false;
+        b->periodic = b->periodic && h->periodic;
+    }
     // starting shape (HLBM_BATCH_TILE=<k> for tests and sweeps; autotune may change it)
     b->tile = env_choice("HLBM_BATCH_TILE", 0, 0, kNumBatchKinds);
     if (b->tile >= kNumBatchTiles && !b->march_ok) b->tile = 0;

@@ -57,6 +57,9 @@ __device__ __forceinline__ int join_map(int mr, int mc, int pitch)
     return mr < 0 ? mr : (mc < 0 ? mc : mr * pitch + mc);
 }
 
+// The periodic image of i in [0, n) (a division only for i outside).
+__device__ __forceinline__ int wrap_per(int i, int n) { return (unsigned)i < (unsigned)n ? i : wrapi(i, n); }
+
 // Row segment k of nseg: rows [k ny / nseg, (k + 1) ny / nseg).
 __device__ __forceinline__ int seg_start(int k, int nseg, int ny)
 {
@@ -182,7 +185,7 @@ struct PairGeom {
 // One strip (columns x0 .. x0+W-1) and one row segment [ys, ye) of one
 // case; all NT threads of the CTA take part (the caller separates
 // consecutive segments with a barrier).
-template <typename T, typename S, int NT, bool SIG, bool PHI0>
+template <typename T, typename S, int NT, bool SIG, bool PHI0, bool PER>
 __device__ __forceinline__ void march_pair_segment(const typename S::raw *__restrict__ inF,
                                                    const T *__restrict__ inA, typename S::raw *__restrict__ outF,
                                                    T *__restrict__ outA, const KParams &kp, const int x0,
@@ -208,15 +211,21 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
     const int pitch = kp.pitch;
     const int t = threadIdx.x;
     const int base = ys - 4;
+    // PER (all four sides periodic, ny >= 4): every index map is a wrap, and
+    // the boundary selections below are compiled out; the rows a segment
+    // reads lie within [-3, ny + 3), one period from the domain at most
+    auto mrow = [&](int gy) {
+        return PER ? (gy < 0 ? gy + kp.ny : (gy >= kp.ny ? gy - kp.ny : gy)) : map_row(gy, kp);
+    };
 
     // load-phase pair t: columns gxL, gxL + 1
     const int gxL = x0 - 4 + 2 * t;
-    const int mcLa = map_col(gxL, kp), mcLb = map_col(gxL + 1, kp);
+    const int mcLa = PER ? wrap_per(gxL, kp.nx) : map_col(gxL, kp), mcLb = PER ? wrap_per(gxL + 1, kp.nx) : map_col(gxL + 1, kp);
     const bool vecL = gxL >= 0 && gxL + 1 < kp.nx;
     // phase-2 / phase-3 pair q = t + 1: columns gx2, gx2 + 1
     const int gx2 = gxL + 2;
     const bool do2 = t < NT - 2;
-    const int mc2a = map_col(gx2, kp), mc2b = map_col(gx2 + 1, kp);
+    const int mc2a = PER ? wrap_per(gx2, kp.nx) : map_col(gx2, kp), mc2b = PER ? wrap_per(gx2 + 1, kp.nx) : map_col(gx2 + 1, kp);
     const bool vec2 = gx2 >= 0 && gx2 + 1 < kp.nx;
     // Dirichlet x sides: level n+1 beyond them is the side's state
     bool dir2[2];
@@ -225,14 +234,14 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
     for (int c = 0; c < 2; c++) {
         const int gx = gx2 + c;
         side2[c] = gx < 0 ? 0 : 1;
-        dir2[c] = (gx < 0 || gx >= kp.nx) && kp.bc[side2[c]] == BC_DIRICHLET;
+        dir2[c] = !PER && (gx < 0 || gx >= kp.nx) && kp.bc[side2[c]] == BC_DIRICHLET;
     }
     const bool do3 = t >= 1 && t <= G::NP;
     const bool v3a = do3 && gx2 < kp.nx, v3b = do3 && gx2 + 1 < kp.nx;
     // zero-gradient x sides: the neighbour beyond the edge is the edge cell itself
-    const bool zgW = gx2 == 0 && kp.bc[0] == BC_ZEROGRAD;             // west of cell a
-    const bool zgEa = gx2 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD;    // east of cell a
-    const bool zgEb = gx2 + 1 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD; // east of cell b
+    const bool zgW = !PER && gx2 == 0 && kp.bc[0] == BC_ZEROGRAD;             // west of cell a
+    const bool zgEa = !PER && gx2 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD;    // east of cell a
+    const bool zgEb = !PER && gx2 + 1 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD; // east of cell b
 
     // prefetch registers: F(n) of row r+2, s(n) of row r+3 (load pair),
     // a1(n) of row r+1 (phase-2 pair)
@@ -272,10 +281,10 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
         }
     };
     auto fetch = [&](int r) {
-        load_F(map_row(r + 2, kp), pFa, pFb);
-        load_s(map_row(r + 3, kp), pSa, pSb);
+        load_F(mrow(r + 2), pFa, pFb);
+        load_s(mrow(r + 3), pSa, pSb);
         if (PHI0 && do2) {
-            const int mr = map_row(r + 1, kp);
+            const int mr = mrow(r + 1);
             if (mr >= 0 && vec2) {
                 const T *src = inA + ((long long)mr * pitch + gx2);
 #pragma unroll
@@ -300,7 +309,7 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         const int gy = ys - 3 + k;
-        load_s(map_row(gy, kp), sPa, sPb);
+        load_s(mrow(gy), sPa, sPb);
         rS[((gy - base) % 5) * NT + t] = Vec2<T>::make(sPa, sPb);
     }
     fetch(base);
@@ -337,7 +346,7 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
             gC[(fs2 * 3 + 0) * NT + t] = Vec2<T>::make(fa[2], fb[2]);
             gC[(fs2 * 3 + 1) * NT + t] = Vec2<T>::make(fa[5], fb[5]);
             gC[(fs2 * 3 + 2) * NT + t] = Vec2<T>::make(fa[6], fb[6]);
-            const int mr = map_row(r + 2, kp);
+            const int mr = mrow(r + 2);
             T m[2][4];
             auto macros = [&](const T *f, T sv, int o, T *mm) {
                 if (o >= 0) {
@@ -364,8 +373,8 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
                 m[0][0] = rho.x; m[0][1] = ux.x; m[0][2] = uy.x; m[0][3] = th.x;
                 m[1][0] = rho.y; m[1][1] = ux.y; m[1][2] = uy.y; m[1][3] = th.y;
                 const int oa = join_map(mr, mcLa, pitch), ob = join_map(mr, mcLb, pitch);
-                if (oa < 0) { const int sd = -oa - 1; m[0][0] = side.rho(sd); m[0][1] = side.ux(sd); m[0][2] = side.uy(sd); m[0][3] = side.th(sd); }
-                if (ob < 0) { const int sd = -ob - 1; m[1][0] = side.rho(sd); m[1][1] = side.ux(sd); m[1][2] = side.uy(sd); m[1][3] = side.th(sd); }
+                if (!PER && oa < 0) { const int sd = -oa - 1; m[0][0] = side.rho(sd); m[0][1] = side.ux(sd); m[0][2] = side.uy(sd); m[0][3] = side.th(sd); }
+                if (!PER && ob < 0) { const int sd = -ob - 1; m[1][0] = side.rho(sd); m[1][1] = side.ux(sd); m[1][2] = side.uy(sd); m[1][3] = side.th(sd); }
             } else {
                 macros(fa, sPa, join_map(mr, mcLa, pitch), m[0]);
                 macros(fb, sPb, join_map(mr, mcLb, pitch), m[1]);
@@ -456,7 +465,7 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
                 // Dirichlet cells hold the side's constants
                 const bool out2y = y2 < 0 || y2 >= kp.ny;
                 const int side2y = y2 < 0 ? 2 : 3;
-                const bool dir2y = out2y && kp.bc[side2y] == BC_DIRICHLET;
+                const bool dir2y = !PER && out2y && kp.bc[side2y] == BC_DIRICHLET;
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
                     if (dir2y || dir2[c]) {
@@ -476,8 +485,8 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
         // ---- phase 3: row r on pair q = t + 1 (own values from the previous iteration)
         if (r >= ys && do3) {
             const int q = t + 1;
-            const bool zS = r == 0 && kp.bc[2] == BC_ZEROGRAD;
-            const bool zN = r == kp.ny - 1 && kp.bc[3] == BC_ZEROGRAD;
+            const bool zS = !PER && r == 0 && kp.bc[2] == BC_ZEROGRAD;
+            const bool zN = !PER && r == kp.ny - 1 && kp.bc[3] == BC_ZEROGRAD;
             V nW[4], nE[4], nS[4], nN[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -566,16 +575,18 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
     }
 }
 
-// One case: blockIdx.x picks the strip, blockIdx.y the row segment.
-template <typename T, typename S, int NT, int MINB, bool SIG, bool PHI0>
+// One case: blockIdx.x picks the strip, blockIdx.y the row segment.  PER:
+// all four sides periodic and ny >= 4 (the boundary selections compiled
+// out).
+template <typename T, typename S, int NT, int MINB, bool SIG, bool PHI0, bool PER = false>
 __global__ void __launch_bounds__(NT, MINB)
 march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
                   typename S::raw *__restrict__ outF, T *__restrict__ outA, const KParams kp, const int nseg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ys = seg_start(blockIdx.y, nseg, kp.ny), ye = seg_start(blockIdx.y + 1, nseg, kp.ny);
-    march_pair_segment<T, S, NT, SIG, PHI0>(inF, inA, outF, outA, kp, blockIdx.x * PairGeom<T, NT>::W, ys, ye,
-                                            smem_raw);
+    march_pair_segment<T, S, NT, SIG, PHI0, PER>(inF, inA, outF, outA, kp, blockIdx.x * PairGeom<T, NT>::W, ys, ye,
+                                                 smem_raw);
 }
 
 // ---- many cases in one persistent launch (FP32) ---------------------------------
@@ -593,7 +604,7 @@ struct MarchTables {
     int nitems;
 };
 
-template <int NT, int MINB, bool SIG, bool PHI0>
+template <int NT, int MINB, bool SIG, bool PHI0, bool PER = false>
 __global__ void __launch_bounds__(NT, MINB)
 batched_march_kernel(const MarchTables tab, const int parity)
 {
@@ -612,9 +623,9 @@ batched_march_kernel(const MarchTables tab, const int parity)
             __syncthreads();
         }
         const CasePlanes &pl = tab.planes[it.c];
-        march_pair_segment<float, FullStore<float>, NT, SIG, PHI0>(pl.inF[parity], pl.inA[parity], pl.outF[parity],
-                                                                  pl.outA[parity], skp, it.x0, it.ys, it.ye,
-                                                                  smem_raw);
+        march_pair_segment<float, FullStore<float>, NT, SIG, PHI0, PER>(pl.inF[parity], pl.inA[parity],
+                                                                       pl.outF[parity], pl.outA[parity], skp, it.x0,
+                                                                       it.ys, it.ye, smem_raw);
     }
 }
 
