@@ -645,7 +645,9 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         h->walls = h->walls || params->bc[k] == HLBM_BC_WALL;
         h->periodic = h->periodic && params->bc[k] == HLBM_BC_PERIODIC;
     }
-    h->periodic = h->periodic && params->ny >= 4;
+    // HLBM_MARCH_GENERAL=1 keeps the general marching kernels on periodic
+    // grids (tests compare the two)
+    h->periodic = h->periodic && params->ny >= 4 && env_choice("HLBM_MARCH_GENERAL", 0, 0, 2) == 0;
     if (h->walls) {
         // ghost layers for the tiled kernel; walls never take the marching
         // or TMA kernels
