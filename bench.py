@@ -188,7 +188,8 @@ def kernel_name(precision, cells, sigma=0.0, phi_mode=0, periodic=False):
     HLBM_FP32_TMA / HLBM_FP32_TILE), the tiled kernel for FP64 and small
     grids unless HLBM_MARCH selects a marching variant."""
     if precision == "moments":
-        return "march_moment_kernel<64,8,%s,%s>" % (str(sigma > 0).lower(), str(phi_mode == 0).lower())
+        return "march_moment_kernel<64,8,%s,%s%s>" % (str(sigma > 0).lower(), str(phi_mode == 0).lower(),
+                                                      ",true" if periodic else "")
     march = int(os.environ.get("HLBM_MARCH", "-1" if precision == "fp64" or cells <= 768 * 768 else "0"))
     if 0 <= march < 4:
         t = {"fp64": "double,FullStore<double>", "fp16pop": "float,HalfStore", "bf16pop": "float,BF16Store"}

@@ -366,13 +366,20 @@ static cudaError_t setup_march(hlbm_handle *h)
 // matches the handle's sigma > 0 and Phi choice.
 constexpr int kMomNT = 64, kMomMinB = 8;
 
-static const void *moment_kernel_ptr(const hlbm_handle *h)
+template <bool PER>
+static const void *moment_kernel_ptr_t(const hlbm_handle *h)
 {
     const bool sig = h->kp.sigma_nonzero != 0, phi0 = h->kp.phi_mode == 0;
-    if (sig) return phi0 ? (const void *)march_moment_kernel<kMomNT, kMomMinB, true, true>
-                         : (const void *)march_moment_kernel<kMomNT, kMomMinB, true, false>;
-    return phi0 ? (const void *)march_moment_kernel<kMomNT, kMomMinB, false, true>
-                : (const void *)march_moment_kernel<kMomNT, kMomMinB, false, false>;
+    if (sig) return phi0 ? (const void *)march_moment_kernel<kMomNT, kMomMinB, true, true, PER>
+                         : (const void *)march_moment_kernel<kMomNT, kMomMinB, true, false, PER>;
+    return phi0 ? (const void *)march_moment_kernel<kMomNT, kMomMinB, false, true, PER>
+                : (const void *)march_moment_kernel<kMomNT, kMomMinB, false, false, PER>;
+}
+
+// all-periodic grids take the instantiation without boundary selections
+static const void *moment_kernel_ptr(const hlbm_handle *h)
+{
+    return h->periodic ? moment_kernel_ptr_t<true>(h) : moment_kernel_ptr_t<false>(h);
 }
 
 static cudaError_t setup_moments(hlbm_handle *h)
@@ -396,13 +403,9 @@ static cudaError_t launch_moments(hlbm_handle *h)
     dim3 grid((h->p.nx + G::W - 1) / G::W, h->march_nseg);
     const float *in = static_cast<const float *>(h->state[h->cur]);
     float *out = static_cast<float *>(h->state[h->cur ^ 1]);
-    const bool sig = h->kp.sigma_nonzero != 0, phi0 = h->kp.phi_mode == 0;
-    const size_t sm = G::smem_bytes;
-    if (sig && phi0) march_moment_kernel<kMomNT, kMomMinB, true, true><<<grid, kMomNT, sm, h->stream>>>(in, out, h->kp, h->march_nseg);
-    else if (sig) march_moment_kernel<kMomNT, kMomMinB, true, false><<<grid, kMomNT, sm, h->stream>>>(in, out, h->kp, h->march_nseg);
-    else if (phi0) march_moment_kernel<kMomNT, kMomMinB, false, true><<<grid, kMomNT, sm, h->stream>>>(in, out, h->kp, h->march_nseg);
-    else march_moment_kernel<kMomNT, kMomMinB, false, false><<<grid, kMomNT, sm, h->stream>>>(in, out, h->kp, h->march_nseg);
-    return cudaGetLastError();
+    // one launch through the selected instantiation's pointer
+    void *args[] = {(void *)&in, (void *)&out, (void *)&h->kp, (void *)&h->march_nseg};
+    return cudaLaunchKernel(moment_kernel_ptr(h), grid, dim3(kMomNT), args, G::smem_bytes, h->stream);
 }
 
 // Level-n ghost rows of the wall sides, from the current state.

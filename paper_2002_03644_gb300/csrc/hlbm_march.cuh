@@ -667,7 +667,7 @@ struct MomGeom {
     static constexpr size_t smem_bytes = sizeof(float) * (size_t)N;
 };
 
-template <int NT, bool SIG, bool PHI0>
+template <int NT, bool SIG, bool PHI0, bool PER>
 __device__ __forceinline__ void moment_segment(const float *__restrict__ in, float *__restrict__ out,
                                                const KParams &kp, const int x0, const int ys, const int ye,
                                                unsigned char *smem_raw)
@@ -690,17 +690,20 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
     const int pitch = kp.pitch;
     const int t = threadIdx.x;
     const int base = ys - 6;
+    // PER (all four sides periodic): every index map is a wrap, and the
+    // boundary selections below are compiled out
+    auto mrow = [&](int gy) { return PER ? wrap_per(gy, kp.ny) : map_row(gy, kp); };
 
     // load / rebuild pair t: columns gxL, gxL + 1
     const int gxL = x0 - 6 + 2 * t;
-    const int mcLa = map_col(gxL, kp), mcLb = map_col(gxL + 1, kp);
+    const int mcLa = PER ? wrap_per(gxL, kp.nx) : map_col(gxL, kp), mcLb = PER ? wrap_per(gxL + 1, kp.nx) : map_col(gxL + 1, kp);
     const bool vecL = gxL >= 0 && gxL + 1 < kp.nx;
     const bool doR = t >= 1 && t <= NT - 2;
     // phase-2 / phase-3 pair q = t + 2: columns gx2, gx2 + 1
     const int q = t + 2;
     const int gx2 = gxL + 4;
     const bool do2 = t <= NT - 5;
-    const int mc2a = map_col(gx2, kp), mc2b = map_col(gx2 + 1, kp);
+    const int mc2a = PER ? wrap_per(gx2, kp.nx) : map_col(gx2, kp), mc2b = PER ? wrap_per(gx2 + 1, kp.nx) : map_col(gx2 + 1, kp);
     const bool vec2 = gx2 >= 0 && gx2 + 1 < kp.nx;
     bool dir2[2];
     int side2[2];
@@ -708,15 +711,15 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
     for (int c = 0; c < 2; c++) {
         const int gx = gx2 + c;
         side2[c] = gx < 0 ? 0 : 1;
-        dir2[c] = (gx < 0 || gx >= kp.nx) && kp.bc[side2[c]] == BC_DIRICHLET;
+        dir2[c] = !PER && (gx < 0 || gx >= kp.nx) && kp.bc[side2[c]] == BC_DIRICHLET;
     }
     const bool do3 = t >= 1 && t <= G::NP;
     const bool v3a = do3 && gx2 < kp.nx, v3b = do3 && gx2 + 1 < kp.nx;
     // zero-gradient x sides: a neighbour (phase 3) or a pull source (phase 2)
     // beyond the edge is the edge cell itself
-    const bool zgW = gx2 == 0 && kp.bc[0] == BC_ZEROGRAD;             // west of cell a
-    const bool zgEa = gx2 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD;    // east of cell a
-    const bool zgEb = gx2 + 1 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD; // east of cell b
+    const bool zgW = !PER && gx2 == 0 && kp.bc[0] == BC_ZEROGRAD;             // west of cell a
+    const bool zgEa = !PER && gx2 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD;    // east of cell a
+    const bool zgEb = !PER && gx2 + 1 == kp.nx - 1 && kp.bc[1] == BC_ZEROGRAD; // east of cell b
 
     // prefetch registers: moments of row r+4 (load pair), a1 of row r+2 (phase-2 pair)
     float pM[2][4], pA[2][3], pA2[2][3];
@@ -730,7 +733,7 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
     // moments of row y at the load pair; a Dirichlet position gives the side's
     // state with a1 = 0
     auto load_row = [&](int y) {
-        const int mr = map_row(y, kp);
+        const int mr = mrow(y);
         if (mr >= 0 && vecL) {
             const float *src = in + ((long long)mr * pitch + gxL);
 #pragma unroll
@@ -747,7 +750,7 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const int o = join_map(mr, c ? mcLb : mcLa, pitch);
-                if (o >= 0) {
+                if (PER || o >= 0) {
 #pragma unroll
                     for (int k = 0; k < 4; k++) pM[c][k] = in[k * P + o];
 #pragma unroll
@@ -763,7 +766,7 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
     // a1(n) of row y at the phase-2 pair (for Phi)
     auto load_a2 = [&](int y) {
         if (!PHI0 || !do2) return;
-        const int mr = map_row(y, kp);
+        const int mr = mrow(y);
         if (mr >= 0 && vec2) {
             const float *src = in + ((long long)mr * pitch + gx2);
 #pragma unroll
@@ -776,7 +779,7 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
             for (int c = 0; c < 2; c++) {
                 const int o = join_map(mr, c ? mc2b : mc2a, pitch);
 #pragma unroll
-                for (int k = 0; k < 3; k++) pA2[c][k] = o >= 0 ? in[(MS_AXX + k) * P + o] : 0.0f;
+                for (int k = 0; k < 3; k++) pA2[c][k] = (PER || o >= 0) ? in[(MS_AXX + k) * P + o] : 0.0f;
             }
         }
     };
@@ -804,12 +807,12 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
             load_a2(r + 2);
         }
         {
-            const int mr = map_row(r + 3, kp);
+            const int mr = mrow(r + 3);
             float th[2];
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const int o = join_map(mr, c ? mcLb : mcLa, pitch);
-                th[c] = o >= 0 ? cs.theta(mv[c][0], mv[c][3]) : side.th(-o - 1);
+                th[c] = (PER || o >= 0) ? cs.theta(mv[c][0], mv[c][3]) : side.th(-o - 1);
             }
             const int m3 = (rel + 3) & 3;
             rM[(m3 * 4 + 0) * NT + t] = V{mv[0][0], mv[1][0]};
@@ -833,7 +836,7 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
                 cS[k] = M1[k * NT + t];
                 cN[k] = M3[k * NT + t];
             }
-            const int mr = map_row(r + 2, kp);
+            const int mr = mrow(r + 2);
             float fa[9], fb[9];
             {
                 // both cells at once (packed FP32): west of a is pair t-1, east of b pair t+1
@@ -849,11 +852,11 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
                 for (int i = 0; i < 9; i++) { fa[i] = fo[i].x; fb[i] = fo[i].y; }
             }
             const int oa = join_map(mr, mcLa, pitch), ob = join_map(mr, mcLb, pitch);
-            if (oa < 0) {
+            if (!PER && oa < 0) {
 #pragma unroll
                 for (int i = 0; i < 9; i++) fa[i] = side.F(-oa - 1, i);
             }
-            if (ob < 0) {
+            if (!PER && ob < 0) {
 #pragma unroll
                 for (int i = 0; i < 9; i++) fb[i] = side.F(-ob - 1, i);
             }
@@ -889,8 +892,8 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
             const V sS2 = rS[s0 * NT + q], sS1 = rS[s1 * NT + q], sN1 = rS[s3 * NT + q], sN2 = rS[s4 * NT + q];
             // pull sources: F_0,1,3 of row y2, F_2,5,6 of row y2-1, F_4,7,8 of row y2+1;
             // beyond a zero-gradient side, the edge row / column itself
-            const bool zS = y2 == 0 && kp.bc[2] == BC_ZEROGRAD;
-            const bool zN = y2 == kp.ny - 1 && kp.bc[3] == BC_ZEROGRAD;
+            const bool zS = !PER && y2 == 0 && kp.bc[2] == BC_ZEROGRAD;
+            const bool zN = !PER && y2 == kp.ny - 1 && kp.bc[3] == BC_ZEROGRAD;
             const int bsl = (rel + 1) & 1;                               // row y2 in gB
             const int csl = zS ? (rel + 1) % 3 : rel % 3;                // row y2-1 (or y2) in gC
             const int asl = zN ? (rel + 1) & 1 : (rel + 2) & 1;          // row y2+1 (or y2) in gA
@@ -939,7 +942,7 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
             }
             const bool out2y = y2 < 0 || y2 >= kp.ny;
             const int side2y = y2 < 0 ? 2 : 3;
-            const bool dir2y = out2y && kp.bc[side2y] == BC_DIRICHLET;
+            const bool dir2y = !PER && out2y && kp.bc[side2y] == BC_DIRICHLET;
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 if (dir2y || dir2[c]) {
@@ -959,8 +962,8 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
         // ---- phase 3: a1(n+1) of row r; write the level-(n+1) moments
         if (r >= ys && do3) {
             const int ns0 = (rel + 2) % 3, ns1 = rel % 3, ns2 = (rel + 1) % 3;  // rows r-1, r, r+1
-            const bool zS = r == 0 && kp.bc[2] == BC_ZEROGRAD;
-            const bool zN = r == kp.ny - 1 && kp.bc[3] == BC_ZEROGRAD;
+            const bool zS = !PER && r == 0 && kp.bc[2] == BC_ZEROGRAD;
+            const bool zN = !PER && r == kp.ny - 1 && kp.bc[3] == BC_ZEROGRAD;
             V nW[4], nE[4], nS[4], nN[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -1024,13 +1027,13 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
     }
 }
 
-template <int NT, int MINB, bool SIG, bool PHI0>
+template <int NT, int MINB, bool SIG, bool PHI0, bool PER = false>
 __global__ void __launch_bounds__(NT, MINB)
 march_moment_kernel(const float *__restrict__ in, float *__restrict__ out, const KParams kp, const int nseg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ys = seg_start(blockIdx.y, nseg, kp.ny), ye = seg_start(blockIdx.y + 1, nseg, kp.ny);
-    moment_segment<NT, SIG, PHI0>(in, out, kp, blockIdx.x * MomGeom<NT>::W, ys, ye, smem_raw);
+    moment_segment<NT, SIG, PHI0, PER>(in, out, kp, blockIdx.x * MomGeom<NT>::W, ys, ye, smem_raw);
 }
 
 // Moment state from FP64 caller fields (Algorithm 1, steps 1-4): rho, u, s

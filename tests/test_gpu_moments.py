@@ -110,3 +110,21 @@ def test_moments_state_roundtrip_diagnostics_and_populations(hl):
     with pytest.raises(hl.HlbmError) as e:
         a.populations()
     assert e.value.code == hl.HLBM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("sigma", [0.0, 0.6])
+def test_moments_periodic_instantiation_equals_general_kernel(hl, sigma):
+    """All-periodic grids take the moment kernel with the boundary
+    selections compiled out; it must equal the general kernel bitwise."""
+    from test_gpu_parity import _env
+    case = inputs.random_smooth(130, 67, seed=9, amp=0.05, u0=(0.05, -0.02), theta0=0.2, mu=3e-3, sigma=sigma)
+    out = []
+    for general in ("0", "1"):
+        with _env(HLBM_MARCH_GENERAL=general):
+            s = hl.Solver(case.nx, case.ny, precision=MOM, **case.params())
+        s.init(*case.fields())
+        s.step(25)
+        out.append(s.macros())
+        s.close()
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
