@@ -195,8 +195,8 @@ def kernel_name(precision, cells, sigma=0.0, phi_mode=0, periodic=False):
         t = {"fp64": "double,FullStore<double>", "fp16pop": "float,HalfStore", "bf16pop": "float,BF16Store"}
         f64 = precision == "fp64"
         nt, minb = [(64, 8), (96, 5), (128, 4), (64, 1)][march]
-        # the default FP32 kernel has an instantiation for all-periodic grids
-        per = ",true" if (march == 0 and precision == "fp32" and periodic) else ""
+        # the default FP32-arithmetic kernel has an instantiation for all-periodic grids
+        per = ",true" if (march == 0 and not f64 and periodic) else ""
         return "march_pair_kernel<%s,%d,%d,%s,%s%s>" % (t.get(precision, "float,FullStore<float>"), nt,
                                                         1 if f64 else minb, str(sigma > 0).lower(),
                                                         str(phi_mode == 0).lower(), per)
@@ -402,7 +402,8 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": profiled_traffic(args.precision, args.n),
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                 "kernel": kernel_name(args.precision, cells, case.sigma, case.phi_mode,
-                                      all(b == 0 for b in case.bc) and case.ny >= 4),
+                                      all(b == 0 for b in case.bc) and case.ny >= 4
+                                      and os.environ.get("HLBM_MARCH_GENERAL", "0") != "1"),
                 "algorithmic_bytes_per_launch": bpc * cells}
     else:
         # FP64 is bound by GB300's FP64 pipe: FP64 operations (add, mul, 2 per

@@ -336,8 +336,9 @@ static cudaError_t march_dispatch(hlbm_handle *h)
     case 2: return Launch ? launch_pair<T, S, 128, f64 ? 1 : 4>(h) : pair_setup<T, S, 128, f64 ? 1 : 4>(h);
     case 3: return Launch ? launch_pair<T, S, 64, 1>(h) : pair_setup<T, S, 64, 1>(h);
     default:
-        // the default FP32 kernel has an all-periodic instantiation
-        if constexpr (std::is_same<S, FullStore<float>>::value) {
+        // the default FP32-arithmetic kernel (FP32 or 16-bit storage) has an
+        // all-periodic instantiation
+        if constexpr (!f64) {
             if (h->periodic) return Launch ? launch_pair<T, S, 64, 8, true>(h) : pair_setup<T, S, 64, 8, true>(h);
         }
         return Launch ? launch_pair<T, S, 64, f64 ? 1 : 8>(h) : pair_setup<T, S, 64, f64 ? 1 : 8>(h);

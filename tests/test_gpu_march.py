@@ -97,15 +97,17 @@ def test_march_16bit_forms_within_their_bounds(hl):
             assert e[k]["linf"] <= BOUND[prec], (prec, k, e[k])
 
 
+@pytest.mark.parametrize("precision", [1, 2, 3])
 @pytest.mark.parametrize("sigma", [0.0, 0.5])
-def test_periodic_instantiation_equals_general_kernel(hl, sigma):
-    """On an all-periodic grid the default FP32 kernel compiles the boundary
-    selections out; every value must equal the general kernel's bitwise."""
+def test_periodic_instantiation_equals_general_kernel(hl, sigma, precision):
+    """On an all-periodic grid the default FP32-arithmetic kernel (FP32 and
+    the 16-bit storage forms) compiles the boundary selections out; every
+    value must equal the general kernel's bitwise."""
     case = inputs.random_smooth(173, 141, seed=41, amp=0.05, u0=(0.06, -0.02), theta0=0.2, mu=3e-3, sigma=sigma)
     out = []
     for general in ("0", "1"):
         with _env(HLBM_MARCH=0, HLBM_MARCH_GENERAL=general):
-            s = hl.Solver(case.nx, case.ny, precision=1, **case.params())
+            s = hl.Solver(case.nx, case.ny, precision=precision, **case.params())
         s.init(*case.fields())
         s.step(25)
         out.append(s.macros())
