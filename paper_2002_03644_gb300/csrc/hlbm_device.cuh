@@ -783,7 +783,21 @@ __global__ void wall_ghost_kernel(const typename S::raw *__restrict__ inF, const
 }
 
 // ---- initialisation (Algorithm 1, steps 1-4) -----------------------------------
-// In FP64 from FP64 caller fields (row-major [ny][nx]); writes the state in T.
+// Entropy of an initial cell, s = c_v (ln theta - (gamma - 1) ln rho), in the
+// arithmetic type of the state.
+__device__ __forceinline__ double init_entropy(const KParams &kp, double rho, double th)
+{
+    return kp.cv * (log(th) - kp.gm1 * log(rho));
+}
+__device__ __forceinline__ float init_entropy(const KParams &kp, float rho, float th)
+{
+    return (float)kp.cv * (logf(th) - kp.f_gm1 * logf(rho));
+}
+
+// From FP64 caller fields (row-major [ny][nx]); writes the state in T.  The
+// arithmetic is in T as well: the FP32-arithmetic forms round the fields to
+// FP32 on load, as their step does with every level, and FP64 computes in
+// FP64 throughout.
 template <typename T, typename S>
 __global__ void init_kernel(const double *__restrict__ rho, const double *__restrict__ ux,
                             const double *__restrict__ uy, const double *__restrict__ th,
@@ -794,7 +808,7 @@ __global__ void init_kernel(const double *__restrict__ rho, const double *__rest
     const int gy = blockIdx.y * blockDim.y + threadIdx.y;
     if (gx >= kp.nx || gy >= kp.ny) return;
     const int n = kp.nx * kp.ny;
-    auto at = [&](int dx, int dy, double &r, double &u, double &v, double &t) {
+    auto at = [&](int dx, int dy, T &r, T &u, T &v, T &t) {
         int xx = gx + dx, yy = gy + dy;  // one of them at most is outside
         int ws = -1;
         // beyond a wall: the mirrored interior cell, reflected (see wall_ghost_kernel)
@@ -806,50 +820,51 @@ __global__ void init_kernel(const double *__restrict__ rho, const double *__rest
             xx = xx < 0 ? -xx - 1 : 2 * kp.nx - 1 - xx;
         }
         const int o = locate(xx, yy, kp, kp.nx);
-        if (o >= 0) { r = rho[o]; u = ux[o]; v = uy[o]; t = th[o]; }
-        else { const int s = -o - 1; r = kp.d_rho[s]; u = kp.d_ux[s]; v = kp.d_uy[s]; t = kp.d_th[s]; }
+        if (o >= 0) { r = (T)rho[o]; u = (T)ux[o]; v = (T)uy[o]; t = (T)th[o]; }
+        else { const int s = -o - 1; r = (T)kp.d_rho[s]; u = (T)kp.d_ux[s]; v = (T)kp.d_uy[s]; t = (T)kp.d_th[s]; }
         if (ws >= 0) {
-            const double tg = 2.0 * kp.d_th[ws] - t;
+            const T tg = T(2) * (T)kp.d_th[ws] - t;
             r = r * t / tg;
             t = tg;
-            u = 2.0 * kp.d_ux[ws] - u;
-            v = 2.0 * kp.d_uy[ws] - v;
+            u = T(2) * (T)kp.d_ux[ws] - u;
+            v = T(2) * (T)kp.d_uy[ws] - v;
         }
     };
-    double r0, u0, v0, t0, rxm, uxm, vxm, txm, rxp, uxp, vxp, txp, rym, uym, vym, tym, ryp, uyp, vyp, typ;
+    T r0, u0, v0, t0, rxm, uxm, vxm, txm, rxp, uxp, vxp, txp, rym, uym, vym, tym, ryp, uyp, vyp, typ;
     at(0, 0, r0, u0, v0, t0);
     at(-1, 0, rxm, uxm, vxm, txm); at(1, 0, rxp, uxp, vxp, txp);
     at(0, -1, rym, uym, vym, tym); at(0, 1, ryp, uyp, vyp, typ);
-    const double p = r0 * t0 / 3.0;
-    const double dxux = 0.5 * (uxp - uxm), dyux = 0.5 * (uyp - uym);
-    const double dxuy = 0.5 * (vxp - vxm), dyuy = 0.5 * (vyp - vym);
-    double axx, axy, ayy;
+    const T mu = (T)kp.mu;
+    const T p = r0 * t0 / T(3);
+    const T dxux = T(0.5) * (uxp - uxm), dyux = T(0.5) * (uyp - uym);
+    const T dxuy = T(0.5) * (vxp - vxm), dyuy = T(0.5) * (vyp - vym);
+    T axx, axy, ayy;
     const int c = gy * kp.nx + gx;
     if (a1) {
-        axx = a1[c]; axy = a1[n + c]; ayy = a1[2 * n + c];
+        axx = (T)a1[c]; axy = (T)a1[n + c]; ayy = (T)a1[2 * n + c];
     } else {
-        const double cfd = -(kp.mu + 0.5 * p);
+        const T cfd = -(mu + T(0.5) * p);
         axx = cfd * (dxux - dyuy); axy = cfd * (dyux + dxuy); ayy = -axx;
     }
-    auto gam = [](double r, double u, double t) { return r * u * (1.0 - t - u * u); };
-    const double gxc = gam(r0, u0, t0), gyc = gam(r0, v0, t0);
+    auto gam = [](T r, T u, T t) { return r * u * (T(1) - t - u * u); };
+    const T gxc = gam(r0, u0, t0), gyc = gam(r0, v0, t0);
     const bool cen = kp.e1_centred != 0;
-    const double e1xx = (u0 > 0.0 && !cen) ? gxc - gam(rxm, uxm, txm)
-                      : ((u0 < 0.0 && !cen) ? gam(rxp, uxp, txp) - gxc : 0.5 * (gam(rxp, uxp, txp) - gam(rxm, uxm, txm)));
-    const double e1yy = (v0 > 0.0 && !cen) ? gyc - gam(rym, vym, tym)
-                      : ((v0 < 0.0 && !cen) ? gam(ryp, vyp, typ) - gyc : 0.5 * (gam(ryp, vyp, typ) - gam(rym, vym, tym)));
-    const double e2 = p * kp.two_minus_gamma * (dxux + dyuy);
-    const double omega = (2.0 * kp.mu - p) / (2.0 * kp.mu + p);
-    double f[9];
-    build_populations<double>(r0, u0, v0, t0, axx, axy, ayy, e1xx + e2, e1yy + e2, omega, f);
+    const T e1xx = (u0 > T(0) && !cen) ? gxc - gam(rxm, uxm, txm)
+                 : ((u0 < T(0) && !cen) ? gam(rxp, uxp, txp) - gxc : T(0.5) * (gam(rxp, uxp, txp) - gam(rxm, uxm, txm)));
+    const T e1yy = (v0 > T(0) && !cen) ? gyc - gam(rym, vym, tym)
+                 : ((v0 < T(0) && !cen) ? gam(ryp, vyp, typ) - gyc : T(0.5) * (gam(ryp, vyp, typ) - gam(rym, vym, tym)));
+    const T e2 = p * (T)kp.two_minus_gamma * (dxux + dyuy);
+    const T omega = (T(2) * mu - p) / (T(2) * mu + p);
+    T f[9];
+    build_populations<T>(r0, u0, v0, t0, axx, axy, ayy, e1xx + e2, e1yy + e2, omega, f);
     const long long P = kp.plane;
     const int o = gy * kp.pitch + gx;
 #pragma unroll
-    for (int i = 0; i < 9; i++) outF[i * P + o] = S::put((T)f[i], i, kp);
-    outA[A_S * P + o] = (T)(kp.cv * (log(t0) - kp.gm1 * log(r0)));
-    outA[A_XX * P + o] = (T)axx;
-    outA[A_XY * P + o] = (T)axy;
-    outA[A_YY * P + o] = (T)ayy;
+    for (int i = 0; i < 9; i++) outF[i * P + o] = S::put(f[i], i, kp);
+    outA[A_S * P + o] = init_entropy(kp, r0, t0);
+    outA[A_XX * P + o] = axx;
+    outA[A_XY * P + o] = axy;
+    outA[A_YY * P + o] = ayy;
 }
 
 // ---- field extraction ----------------------------------------------------------

@@ -1037,7 +1037,8 @@ march_moment_kernel(const float *__restrict__ in, float *__restrict__ out, const
 }
 
 // Moment state from FP64 caller fields (Algorithm 1, steps 1-4): rho, u, s
-// and a1 (given, or a1^FD of the initial fields as in init_kernel).
+// and a1 (given, or a1^FD of the initial fields as in init_kernel), computed
+// in FP32 from the fields rounded to FP32, as init_kernel does for FP32.
 __global__ void init_moments_kernel(const double *__restrict__ rho, const double *__restrict__ ux,
                                     const double *__restrict__ uy, const double *__restrict__ th,
                                     const double *__restrict__ a1, float *__restrict__ out, const KParams kp)
@@ -1049,29 +1050,31 @@ __global__ void init_moments_kernel(const double *__restrict__ rho, const double
     const int c = gy * kp.nx + gx;
     const long long P = kp.plane;
     const int o = gy * kp.pitch + gx;
-    double axx, axy, ayy;
+    const float r0 = (float)rho[c], t0 = (float)th[c];
+    float axx, axy, ayy;
     if (a1) {
-        axx = a1[c]; axy = a1[n + c]; ayy = a1[2 * n + c];
+        axx = (float)a1[c]; axy = (float)a1[n + c]; ayy = (float)a1[2 * n + c];
     } else {
-        auto vel = [&](int dx, int dy, double &u, double &v) {
+        auto vel = [&](int dx, int dy, float &u, float &v) {
             const int q = locate(gx + dx, gy + dy, kp, kp.nx);
-            if (q >= 0) { u = ux[q]; v = uy[q]; } else { u = kp.d_ux[-q - 1]; v = kp.d_uy[-q - 1]; }
+            if (q >= 0) { u = (float)ux[q]; v = (float)uy[q]; }
+            else { u = (float)kp.d_ux[-q - 1]; v = (float)kp.d_uy[-q - 1]; }
         };
-        double uxm, vxm, uxp, vxp, uym, vym, uyp, vyp;
+        float uxm, vxm, uxp, vxp, uym, vym, uyp, vyp;
         vel(-1, 0, uxm, vxm); vel(1, 0, uxp, vxp); vel(0, -1, uym, vym); vel(0, 1, uyp, vyp);
-        const double p = rho[c] * th[c] / 3.0;
-        const double cfd = -(kp.mu + 0.5 * p);
-        axx = cfd * (0.5 * (uxp - uxm) - 0.5 * (vyp - vym));
-        axy = cfd * (0.5 * (uyp - uym) + 0.5 * (vxp - vxm));
+        const float p = r0 * t0 / 3.0f;
+        const float cfd = -((float)kp.mu + 0.5f * p);
+        axx = cfd * (0.5f * (uxp - uxm) - 0.5f * (vyp - vym));
+        axy = cfd * (0.5f * (uyp - uym) + 0.5f * (vxp - vxm));
         ayy = -axx;
     }
-    out[MS_RHO * P + o] = (float)rho[c];
+    out[MS_RHO * P + o] = r0;
     out[MS_UX * P + o] = (float)ux[c];
     out[MS_UY * P + o] = (float)uy[c];
-    out[MS_S * P + o] = (float)(kp.cv * (log(th[c]) - kp.gm1 * log(rho[c])));
-    out[MS_AXX * P + o] = (float)axx;
-    out[MS_AXY * P + o] = (float)axy;
-    out[MS_AYY * P + o] = (float)ayy;
+    out[MS_S * P + o] = init_entropy(kp, r0, t0);
+    out[MS_AXX * P + o] = axx;
+    out[MS_AXY * P + o] = axy;
+    out[MS_AYY * P + o] = ayy;
 }
 
 // Caller fields from the moment state (theta recomputed from rho and s).
