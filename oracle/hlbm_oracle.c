@@ -15,7 +15,7 @@
  * Units: lattice units, dx = dt = 1 (Sec. 2.1: variables made dimensionless
  * with T_r, rho_r, dx and dt = dx / C_0), so c_s^2 = 1/3 and D = 2.
  *
- * Readings of points the paper leaves open (each one is listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - mu is a constant per case and tau = mu / p per cell (mu = tau p, Sec. 2.4).
  *  - E1 is diagonal: E1_xx = d_x Gamma_x, E1_yy = d_y Gamma_y, E1_xy = 0, with
  *    Gamma_y built like Gamma_x; sgn(0) = 0 (Sec. 3.2).

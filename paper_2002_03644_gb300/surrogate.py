@@ -244,3 +244,25 @@ def hybrid_rollout(sur, norm, case, calls, K=16, judge_every=8, tol=None, stream
         else:
             state = y
     return state, log
+
+
+def _predict_workload(calls):
+    """A fixed inference workload for timing and profiling the convolution
+    kernels: the K = 16 network (4-64x5-4) with seeded random weights, one
+    predict call on a seeded normal 16 x 256 x 256 x 4 input three times for
+    warm-up, then `calls` more."""
+    import torch
+    torch.cuda.set_device(0)
+    sur = Surrogate((4, 64, 64, 64, 64, 64, 4), 256, 256, batch_max=16, seed=0)
+    x = torch.from_numpy(np.random.default_rng(1).normal(size=(16, 256, 256, 4)).astype(np.float32)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(3 + calls):
+        sur.predict(x, y)
+    sur.synchronize()
+    print("mean |y|", float(y.abs().mean()))
+    sur.close()
+
+
+if __name__ == "__main__":
+    import sys
+    _predict_workload(int(sys.argv[1]) if len(sys.argv) > 1 else 2)
