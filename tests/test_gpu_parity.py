@@ -145,6 +145,37 @@ def test_sod_shock_tube_fp64_first_150_steps(hl):
     compare(got, ref, case.gamma, TOL[0])
 
 
+@pytest.mark.parametrize("march", [-1, 0], ids=["tiled", "marching"])
+@pytest.mark.parametrize("n", [70, 131])
+def test_four_quadrant_riemann_fp64_within_the_schemes_own_sensitivity(hl, n, march):
+    """The four-quadrant Riemann problem: 2-D discontinuities meeting at a
+    junction, local Mach about 3, zero-gradient sides on all four edges.  It
+    runs on the tiled kernel and on the row-marching kernel's general
+    (non-periodic) form.  After one step every field is within the FP64
+    bound.  Within a few steps the upwind E1 of Sec. 3.2 switches on the
+    sign of velocities that are pure round-off at the junction, where one
+    side of each interface is at rest in one direction.  The oracle fed an
+    upper-right density larger by one part in 2^50 then drifts from itself
+    by about 2e-4 of the density scale after 25 steps (long before the
+    scheme leaves its range of stability).  After 25 steps the GPU must stay
+    within 10x that measured sensitivity."""
+    case = inputs.four_quadrant(n=n)
+    with _env(HLBM_MARCH=march):
+        _, _, got, ref = run_pair(hl, case, 0, 1)
+        compare(got, ref, case.gamma, TOL[0])
+        _, _, got, ref = run_pair(hl, case, 0, 25)
+    r2 = case.rho.copy()
+    r2[n // 2:, n // 2:] *= 1.0 + 2.0 ** -50  # keeps the quadrant's state uniform
+    o2 = Oracle(case.nx, case.ny, **case.params())
+    o2.init(r2, case.ux, case.uy, case.theta)
+    o2.step(25)
+    ref2 = o2.macros()
+    for k in ("rho", "ux", "uy", "theta", "s"):
+        own = np.abs(ref2[k] - ref[k]).max()
+        assert own > 0.0, k  # the sensitivity is there to be measured
+        assert np.abs(got[k] - ref[k]).max() <= 10.0 * own, (k, own)
+
+
 def test_sod_shock_tube_fp64_full_run_within_the_schemes_own_sensitivity(hl):
     """Over the full 310 steps the upwind E1 of Sec. 3.2 switches on the sign
     of velocities that are pure round-off ahead of the shock, so two correct
