@@ -43,6 +43,19 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* The rows of a per-cell pass are independent: each cell writes its own
+ * entries and reads only arrays that the pass does not write.  So they may
+ * be split over threads (OpenMP, when the library is built with it) without
+ * changing any result; one thread (the default) runs them in order. */
+#ifdef _OPENMP
+#define ROWS_PARALLEL _Pragma("omp parallel for schedule(static) if(o->threads > 1) num_threads(o->threads)")
+#else
+#define ROWS_PARALLEL
+#endif
 
 #define Q 9
 #define G 2                      /* ghost width: MUSCL needs s at i +- 2 */
@@ -282,6 +295,7 @@ typedef struct {
     double *feq1[Q], *psi1[Q];
     double *gx, *gy;          /* Gamma_x, Gamma_y of the level being differentiated */
     long step;
+    int threads;              /* threads for the per-cell passes (1: in order) */
 } hlbmo;
 
 static inline int IX(const hlbmo *o, int x, int y) { return (y + G) * o->px + (x + G); }
@@ -421,6 +435,7 @@ hlbmo *hlbmo_create(int nx, int ny, double gamma, double Pr, double mu, double s
     hlbmo *o = (hlbmo *)calloc(1, sizeof(hlbmo));
     if (!o) return NULL;
     make_tables();
+    o->threads = 1;
     o->nx = nx; o->ny = ny; o->px = nx + 2 * G; o->py = ny + 2 * G;
     o->gamma = gamma; o->Pr = Pr; o->mu = mu; o->sigma = sigma; o->phi_mode = phi_mode;
     o->ablation = ablation;
@@ -501,12 +516,14 @@ static double sgn(double v) { return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0); }
 static void compute_psi(hlbmo *o, const double *rho, const double *ux, const double *uy,
                         const double *th, double *psi[Q])
 {
+    ROWS_PARALLEL
     for (int y = -G; y < o->ny + G; y++)
         for (int x = -G; x < o->nx + G; x++) {
             const int k = IX(o, x, y);
             o->gx[k] = hlbmo_gamma_closure(rho[k], ux[k], th[k]);
             o->gy[k] = hlbmo_gamma_closure(rho[k], uy[k], th[k]);
         }
+    ROWS_PARALLEL
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             const int k = IX(o, x, y);
@@ -632,6 +649,7 @@ static int has_wall(const hlbmo *o)
  * f1_i + psi_i / 2 (eq streamalgo), the post-collision populations of level n. */
 static void collide(hlbmo *o)
 {
+    ROWS_PARALLEL
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             const int k = IX(o, x, y);
@@ -705,12 +723,14 @@ int hlbmo_step(hlbmo *o, long nsteps)
         /* step 5: collide with [f^eq, a1, psi]^(n) ... */
         collide(o);
         /* ... and stream: fbar_i(x) = F_i(x - c_i) */
+        ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
                 const int k = IX(o, x, y);
                 for (int i = 0; i < Q; i++) o->fb[i][k] = o->F[i][IX(o, x - CX[i], y - CY[i])];
             }
         /* step 6: rho, u at n+1, eqs (rhoalgo), (ualgo) */
+        ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
                 const int k = IX(o, x, y);
@@ -723,12 +743,14 @@ int hlbmo_step(hlbmo *o, long nsteps)
                 o->rho1[k] = r; o->ux1[k] = mx / r; o->uy1[k] = my / r;
             }
         /* step 7: s at n+1 from level-n rho, u, theta, a1 (explicit Euler, dt = 1) */
+        ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
                 const int k = IX(o, x, y);
                 o->s1[k] = o->s[k] + entropy_rhs(o, x, y);
             }
         /* step 8: theta at n+1 */
+        ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
                 const int k = IX(o, x, y);
@@ -738,6 +760,7 @@ int hlbmo_step(hlbmo *o, long nsteps)
         /* step 9: psi at n+1 */
         compute_psi(o, o->rho1, o->ux1, o->uy1, o->th1, o->psi1);
         /* step 10: f^eq at n+1 */
+        ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
                 const int k = IX(o, x, y);
@@ -746,6 +769,7 @@ int hlbmo_step(hlbmo *o, long nsteps)
                 for (int i = 0; i < Q; i++) o->feq1[i][k] = out[i];
             }
         /* step 11: a1 at n+1 = sigma a1^PR + (1 - sigma) a1^FD, eq (a1sigalgo) */
+        ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
                 const int k = IX(o, x, y);
@@ -810,3 +834,17 @@ void hlbmo_get_post_collision(hlbmo *o, double *out9)
 }
 
 long hlbmo_step_count(const hlbmo *o) { return o->step; }
+
+/* Threads for the per-cell passes of hlbmo_step (results do not depend on
+ * it); without OpenMP every pass runs on the calling thread. */
+void hlbmo_set_threads(hlbmo *o, int n) { o->threads = n > 1 ? n : 1; }
+
+/* Processors OpenMP can use, or 1 when the library is built without it. */
+int hlbmo_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_num_procs();
+#else
+    return 1;
+#endif
+}

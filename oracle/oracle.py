@@ -37,7 +37,10 @@ def build_oracle(force: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
            "-fno-fast-math", "-o", tmp, SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP only splits the rows of per-cell passes over threads (results
+    # are the same); without it the library runs every pass on one thread.
+    if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], stderr=subprocess.DEVNULL).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
 
@@ -64,6 +67,8 @@ def _load():
         lib.hlbmo_entropy_rhs.argtypes = [ctypes.c_void_p, _PD]
         lib.hlbmo_step_count.restype = ctypes.c_long
         lib.hlbmo_step_count.argtypes = [ctypes.c_void_p]
+        lib.hlbmo_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.hlbmo_max_threads.restype = ctypes.c_int
         lib.hlbmo_feq_cell.argtypes = [_D, _D, _D, _D, _PD]
         lib.hlbmo_f1_cell.argtypes = [_D, _D, _D, _D, _D, _D, _PD]
         lib.hlbmo_a1_high.argtypes = [_D, _D, _D, _D, _D, _D, _PD]
@@ -178,6 +183,11 @@ class Oracle:
     def step_count(self):
         return self.lib.hlbmo_step_count(self._h)
 
+    def set_threads(self, n):
+        """Split the rows of each per-cell pass over n threads (the results
+        do not change); 1, the default, runs them in order."""
+        self.lib.hlbmo_set_threads(self._h, int(n))
+
     def macros(self):
         """dict of rho, ux, uy, theta, s (each [ny, nx]) and a1 ([3, ny, nx])."""
         n, shp = self.n, (self.ny, self.nx)
@@ -208,3 +218,8 @@ class Oracle:
         out = np.zeros(self.n)
         self.lib.hlbmo_entropy_rhs(self._h, _ptr(out))
         return out.reshape(self.ny, self.nx)
+
+
+def max_threads():
+    """Processors the oracle can split its rows over (1 without OpenMP)."""
+    return _load().hlbmo_max_threads()

@@ -220,3 +220,23 @@ def test_cfl_relation_matches_printed_value(golden_dir):
     cfl = (Ma + 1.0) * c_inf
     assert abs(cfl - cfl_p) < tol
     assert abs(c_inf - math.sqrt(gamma * CS2 * T / Tr)) < 1e-15
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 3, 3), (2, 1, 1, 2)])
+def test_threaded_rows_change_no_result(bc):
+    """Splitting the rows of the per-cell passes over threads leaves every
+    value bitwise equal to the single-thread run."""
+    from oracle.oracle import max_threads
+    bs = np.array([[1.02, 0.08, 0.01, 0.21], [0.98, 0.05, -0.02, 0.19],
+                   [1.0, 0.03, 0.0, 0.19], [1.0, -0.05, 0.0, 0.215]])
+    case = inputs.random_smooth(37, 29, seed=8, amp=0.04, u0=(0.05, 0.01), theta0=0.2, mu=3e-3,
+                                sigma=0.5, bc=bc, bc_state=bs)
+    out = []
+    for threads in (1, max(2, min(4, max_threads()))):
+        o = Oracle(case.nx, case.ny, **case.params())
+        o.set_threads(threads)
+        o.init(*case.fields())
+        o.step(6)
+        out.append(o.macros())
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
