@@ -183,14 +183,14 @@ def kernel_source_hash():
 
 def kernel_name(precision, cells, sigma=0.0, phi_mode=0, periodic=False):
     """The fused-step kernel the library launches for this precision: the
-    row-marching kernel for FP32 and the 16-bit forms on grids of more than
-    768^2 cells unless HLBM_MARCH=-1 (then the tiled kernels, chosen by
-    HLBM_FP32_TMA / HLBM_FP32_TILE), the tiled kernel for FP64 and small
-    grids unless HLBM_MARCH selects a marching variant."""
+    row-marching kernel on grids of more than 768^2 cells unless
+    HLBM_MARCH=-1 (then the tiled kernels, chosen for FP32 by HLBM_FP32_TMA /
+    HLBM_FP32_TILE), the tiled kernel on small grids unless HLBM_MARCH
+    selects a marching variant."""
     if precision == "moments":
         return "march_moment_kernel<64,8,%s,%s%s>" % (str(sigma > 0).lower(), str(phi_mode == 0).lower(),
                                                       ",true" if periodic else "")
-    march = int(os.environ.get("HLBM_MARCH", "-1" if precision == "fp64" or cells <= 768 * 768 else "0"))
+    march = int(os.environ.get("HLBM_MARCH", "-1" if cells <= 768 * 768 else "0"))
     if 0 <= march < 4:
         t = {"fp64": "double,FullStore<double>", "fp16pop": "float,HalfStore", "bf16pop": "float,BF16Store"}
         f64 = precision == "fp64"
@@ -413,7 +413,7 @@ def run_ours(args):
     else:
         # FP64 is bound by GB300's FP64 pipe: FP64 operations (add, mul, 2 per
         # fma) executed per cell-update, counted by ncu, against the nominal
-        # FP64 rate (no measured FP64 peak exists for this machine)
+        # FP64 rate (no measured FP64 peak is available)
         fpc = profiled_fp64_flops(args.n)
         tf = None if fpc is None else fpc * cells / mean_launch_s / 1e12
         roof = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
@@ -421,7 +421,7 @@ def run_ours(args):
                 "traffic": profiled_traffic(args.precision, args.n),
                 "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s; no measured FP64 peak)",
                 "fp64_flops_per_cell": fpc, "hbm_gbs_achieved": achieved,
-                "kernel": "fused_step_kernel<double,FullStore<double>,32,8,256>",
+                "kernel": kernel_name(args.precision, cells, case.sigma, case.phi_mode),
                 "algorithmic_bytes_per_launch": bpc * cells}
 
     cpu = None

@@ -347,13 +347,14 @@ static cudaError_t march_dispatch(hlbm_handle *h)
 
 static cudaError_t setup_march(hlbm_handle *h)
 {
-    // FP32 and the 16-bit storage forms march by default on grids of more
-    // than kMarchMinCells cells (below that a grid has too few strips and
-    // segments to fill the GPU, and the tiled kernel is faster); FP64 uses
-    // the tiled kernel.  HLBM_MARCH=<k> picks a variant, -1 the tiled / TMA
-    // kernels.
+    // Every precision marches by default on grids of more than
+    // kMarchMinCells cells (below that a grid has too few strips and
+    // segments to fill the GPU, and the tiled kernel is faster).  In FP64 the
+    // marching kernel is 2-8 % faster at 1024^2-2048^2: it recomputes less
+    // halo on the FP64 pipe.  HLBM_MARCH=<k> picks a variant, -1 the tiled /
+    // TMA kernels.
     const bool big = (long long)h->p.nx * h->p.ny > kMarchMinCells;
-    h->march_variant = env_choice("HLBM_MARCH", (h->p.precision != HLBM_FP64 && big) ? 0 : -1, -1, kNumMarch);
+    h->march_variant = env_choice("HLBM_MARCH", big ? 0 : -1, -1, kNumMarch);
     if (h->march_variant < 0) return cudaSuccess;
     return with_types(h, [&](auto ty) {
         using T = typename decltype(ty)::t;

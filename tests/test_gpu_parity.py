@@ -210,6 +210,14 @@ def test_vortex_1024_fp32_bench_configuration(hl):
     compare(got, ref, case.gamma, TOL[1])
 
 
+def test_vortex_1024_fp64_default_kernel(hl):
+    """The same workload in FP64 on the kernel FP64 takes at this size (the
+    row-marching kernel), all cells within the FP64 bound."""
+    case = inputs.vortex(n=1024)
+    _, _, got, ref = run_pair(hl, case, 0, 2)
+    compare(got, ref, case.gamma, TOL[0])
+
+
 def test_vortex_fp64_long_run(hl):
     case = inputs.vortex(n=96, R=6.0)
     _, _, got, ref = run_pair(hl, case, 0, 250)
