@@ -137,8 +137,10 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out);
 /* Algorithm 1, input and initialisation (steps 1-4): from [rho, u, theta]^(0)
  * build s = c_v ln(theta / rho^(gamma-1)), a1^(0) (= a1^FD of eq. a1FD when
  * a1 is NULL, else the given three planes), psi^(0) and the post-collision
- * populations of level 0.  Resets the step counter.  rho, ux, uy, theta are
- * required; a1 may be NULL.  Synchronises before returning. */
+ * populations of level 0.  The fields are converted to the state's
+ * arithmetic type first (FP64 for HLBM_FP64, FP32 for every other form) and
+ * the initialisation is computed in it.  Resets the step counter.  rho, ux,
+ * uy, theta are required; a1 may be NULL.  Synchronises before returning. */
 int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const double *uy,
                      const double *theta, const double *a1, int mem_kind);
 
