@@ -113,6 +113,36 @@ def test_precision_forms_four_quadrant_within_the_problems_own_sensitivity(hl):
             f.write(json.dumps({"case": "quadrant96", "steps": steps, "errors": report}) + "\n")
 
 
+def test_four_quadrant_full_size_first_step(hl):
+    """The four-quadrant Riemann problem at its full 4096^2 size (zero-gradient
+    sides: the marching kernel's general form), one step, every cell: FP32
+    within 1e-4 and the 16-bit storage forms within their bounds, in
+    L-infinity.  After one step no velocity is yet round-off at the junction
+    (the oracle moved by 2^-50 stays within 1e-15 of itself), so the
+    pointwise bounds hold on this discontinuous data."""
+    from oracle.oracle import max_threads
+    case = inputs.four_quadrant(n=4096)
+    ora = Oracle(case.nx, case.ny, **case.params())
+    ora.set_threads(max_threads())
+    ora.init(*case.fields())
+    ora.step(1)
+    ref = ora.macros()
+    del ora
+    report = {}
+    for prec, name in ((1, "fp32"), (2, "fp16pop"), (3, "bf16pop")):
+        s = hl.Solver(case.nx, case.ny, precision=prec, **case.params())
+        s.init(*case.fields())
+        s.step(1)
+        got = s.macros()
+        s.close()
+        e = errors(got, ref, case.gamma)
+        report[name] = {k: e[k]["linf"] for k in FIELDS}
+        for k in ("rho", "ux", "uy", "theta", "s"):
+            assert np.isfinite(got[k]).all()
+            assert e[k]["linf"] <= BOUND[prec], (name, k, e[k])
+    print("\nfour-quadrant 4096^2, one step, L-infinity: " + json.dumps(report))
+
+
 @pytest.mark.parametrize("prec", [2, 3])
 def test_16bit_checkpoint_keeps_the_reference(hl, prec):
     case = inputs.vortex(n=96, R=6.0)
