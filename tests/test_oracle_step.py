@@ -191,6 +191,30 @@ def test_entropy_advection_exact_for_linear_entropy(u):
     assert np.allclose(rhs[:, 2:nx - 2], -u * k, rtol=1e-9, atol=1e-16)
 
 
+@pytest.mark.parametrize("cx,cy", [(0.0, 0.0), (3e-5, 0.0), (1e-5, -2e-5)])
+def test_entropy_conduction_term_of_a_quadratic_temperature(cx, cy):
+    """Gas at rest (no advection; no heating, since grad u = 0 and a1 = 0):
+    the entropy right-hand side of step 7 is the conduction term
+    lambda lap(theta) / (rho theta) alone.  The 5-point Laplacian of a
+    quadratic theta is exactly 2 (cx + cy), so a linear theta gives zero and
+    a quadratic one lambda 2 (cx + cy) / (rho theta) at every interior cell,
+    with lambda = mu c_p / Pr (the definition of the Prandtl number) and
+    c_p = gamma c_s^2 / (gamma - 1) (Sec. 2.4)."""
+    nx, ny = 20, 18
+    gamma, Pr, mu = 1.4, 0.71, 2e-3
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    theta = 0.2 + 1e-3 * X - 2e-3 * Y + cx * (X - 9.5) ** 2 + cy * (Y - 8.5) ** 2
+    rho = 1.0 + 0.01 * np.sin(0.3 * X + 0.2 * Y)
+    o = Oracle(nx, ny, gamma=gamma, Pr=Pr, mu=mu, sigma=0.0, bc=(BC_ZEROGRAD,) * 4)
+    zero = np.zeros((ny, nx))
+    o.init(rho, zero, zero, theta, a1=np.zeros((3, ny, nx)))
+    rhs = o.entropy_rhs()
+    lam = mu * (gamma * CS2 / (gamma - 1.0)) / Pr
+    want = lam * 2.0 * (cx + cy) / (rho * theta)
+    inner = (slice(2, ny - 2), slice(2, nx - 2))
+    assert np.allclose(rhs[inner], want[inner], rtol=1e-9, atol=1e-17)
+
+
 def test_phi_forms_agree_when_sigma_is_zero():
     """With sigma = 0, a1 = a1^FD at every level, so the regularised heating
     -(tau/tau_bar) a1 : grad u equals the finite-difference form
