@@ -215,6 +215,31 @@ def test_entropy_conduction_term_of_a_quadratic_temperature(cx, cy):
     assert np.allclose(rhs[inner], want[inner], rtol=1e-9, atol=1e-17)
 
 
+@pytest.mark.parametrize("phi_mode", [0, 1])
+@pytest.mark.parametrize("k", [2e-3, -5e-3])
+def test_viscous_heating_of_a_plane_shear(phi_mode, k):
+    """Plane shear u_x = k y with uniform theta and entropy (so there is no
+    conduction, and the advection -u . grad s vanishes): the entropy
+    right-hand side is the viscous heating Phi / (rho theta).  The centred
+    gradient of a linear field is exact.  For the finite-difference form
+    (phi_mode 1), mu (grad u + grad u^T - div u I) : grad u gives mu k^2.
+    For the regularised form (phi_mode 0), -(tau / tau_bar) a1 : grad u
+    gives the same with a1 = a1^FD = -tau_bar p (grad u + grad u^T - div u
+    I) at level 0 and mu = tau p (Sec. 2.4, 3.4).  So RHS = mu k^2 / (rho
+    theta) at every interior cell."""
+    nx, ny = 12, 16
+    gamma, mu, th0 = 1.4, 3e-3, 0.2
+    Y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    ux = k * (Y - 7.5)
+    rho = np.full((ny, nx), 1.05)  # with theta uniform, s is uniform too
+    o = Oracle(nx, ny, gamma=gamma, mu=mu, sigma=0.0, phi_mode=phi_mode,
+               bc=(BC_PERIODIC, BC_PERIODIC, BC_ZEROGRAD, BC_ZEROGRAD))
+    o.init(rho, ux, np.zeros((ny, nx)), np.full((ny, nx), th0))
+    rhs = o.entropy_rhs()
+    want = mu * k * k / (1.05 * th0)
+    assert np.allclose(rhs[2:ny - 2], want, rtol=1e-9, atol=0.0)
+
+
 def test_phi_forms_agree_when_sigma_is_zero():
     """With sigma = 0, a1 = a1^FD at every level, so the regularised heating
     -(tau/tau_bar) a1 : grad u equals the finite-difference form
