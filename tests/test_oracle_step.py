@@ -240,6 +240,40 @@ def test_viscous_heating_of_a_plane_shear(phi_mode, k):
     assert np.allclose(rhs[2:ny - 2], want, rtol=1e-9, atol=0.0)
 
 
+@pytest.mark.parametrize("gamma", [1.4, 1.67, 1.1])
+def test_correction_force_of_a_linear_expansion(gamma):
+    """u_x = k (x - x0), u_y = 0, rho and theta uniform, at level 0.  The
+    second Hermite moments of psi give E back (eq. Psialgo): sum_i H_xx,i
+    psi_i = E1_xx + E2 and sum_i H_yy,i psi_i = E1_yy + E2.  Here E1_yy = 0
+    (Gamma_y = 0).  E1_xx is the difference of Gamma_x = rho u_x (1 - theta
+    - u_x^2) taken upwind of the cell's u_x (backward where u_x > 0, forward
+    where u_x < 0, centred where u_x = 0; Sec. 3.2).  E2 = p ((D + 2) / D -
+    gamma) div u = p (2 - gamma) k in 2-D (eq. E2 corr term), exact for a
+    linear field."""
+    nx, ny, k, x0, th0, r0 = 15, 4, 4e-3, 7.0, 0.25, 1.1
+    x = np.arange(nx, dtype=float)
+    ux1 = k * (x - x0)
+    o = Oracle(nx, ny, gamma=gamma, mu=1e-3, sigma=0.0,
+               bc=(BC_ZEROGRAD, BC_ZEROGRAD, BC_PERIODIC, BC_PERIODIC))
+    o.init(np.full((ny, nx), r0), np.tile(ux1, (ny, 1)), np.zeros((ny, nx)), np.full((ny, nx), th0))
+    psi = o.psi()
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=float)
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=float)
+    exx = np.tensordot(cx * cx - CS2, psi, axes=1)
+    eyy = np.tensordot(cy * cy - CS2, psi, axes=1)
+    gam = r0 * ux1 * (1.0 - th0 - ux1 ** 2)
+    e2 = r0 * th0 * CS2 * (2.0 - gamma) * k
+    for i in range(1, nx - 1):
+        if ux1[i] > 0:
+            e1 = gam[i] - gam[i - 1]
+        elif ux1[i] < 0:
+            e1 = gam[i + 1] - gam[i]
+        else:
+            e1 = 0.5 * (gam[i + 1] - gam[i - 1])
+        assert np.allclose(exx[:, i], e1 + e2, rtol=1e-10, atol=1e-18), i
+        assert np.allclose(eyy[:, i], e2, rtol=1e-10, atol=1e-18), i
+
+
 def test_phi_forms_agree_when_sigma_is_zero():
     """With sigma = 0, a1 = a1^FD at every level, so the regularised heating
     -(tau/tau_bar) a1 : grad u equals the finite-difference form
