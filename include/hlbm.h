@@ -295,6 +295,21 @@ void hlbm_sur_destroy(hlbm_sur *s);
 int hlbm_diagnostics_noalloc(const void *state, int precision, int nx, int ny, int pitch, double gamma,
                              double out[8], void *stream);
 
+/* ---- self-test of the bounded device-side wait ------------------------------
+ * Failure detection without a device fault (the library's own behaviour, not
+ * a method of the paper).  The TMA and tensor-core kernels wait on mbarriers
+ * with a budget of SM clock cycles and report a wait that runs out as
+ * HLBM_ERR_TIMEOUT.  This call runs that wait on its own.  One device thread
+ * arms an mbarrier for one arrival.  It makes that arrival itself when
+ * `arrive` is non-zero and never otherwise, then polls for at most
+ * budget_cycles (1 .. 2^31, about 1 s at the GB300 clock).  Returns
+ * HLBM_ERR_TIMEOUT when the wait ran out, HLBM_OK when the phase completed,
+ * and HLBM_ERR_ARG for a budget outside the range.  It returns HLBM_ERR_CUDA
+ * on a CUDA error.  Work is enqueued on `stream` (a cudaStream_t, NULL for
+ * the legacy default stream), and the call waits for it.  No handle is
+ * involved, and the device stays usable whatever the outcome. */
+int hlbm_selftest_wait(void *stream, long long budget_cycles, int arrive);
+
 #ifdef __cplusplus
 }
 #endif

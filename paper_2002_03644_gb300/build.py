@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libhlbm.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("hlbm_api.cu", "hlbm_noalloc.cu", "hlbm_surrogate.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("hlbm_api.cu", "hlbm_noalloc.cu", "hlbm_surrogate.cu", "hlbm_selftest.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
 

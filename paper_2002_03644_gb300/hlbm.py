@@ -29,7 +29,7 @@ ENTRY_POINTS = (
     "hlbm_create", "hlbm_init_fields", "hlbm_step", "hlbm_get_macros", "hlbm_get_populations",
     "hlbm_diagnostics", "hlbm_state_bytes", "hlbm_get_state", "hlbm_set_state", "hlbm_step_count",
     "hlbm_synchronize", "hlbm_destroy", "hlbm_strerror", "hlbm_last_error", "hlbm_abi_version",
-    "hlbm_diagnostics_noalloc",
+    "hlbm_diagnostics_noalloc", "hlbm_selftest_wait",
     "hlbm_batch_create", "hlbm_batch_case", "hlbm_batch_step", "hlbm_batch_autotune", "hlbm_batch_tile",
     "hlbm_batch_destroy",
     "hlbm_sur_create", "hlbm_sur_param_count", "hlbm_sur_set_params", "hlbm_sur_get_params", "hlbm_sur_forward",
@@ -159,6 +159,8 @@ def _lib():
         lib.hlbm_diagnostics_noalloc.restype = ctypes.c_int
         lib.hlbm_diagnostics_noalloc.argtypes = [_PD, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_double, _PD, _P]
+        lib.hlbm_selftest_wait.restype = ctypes.c_int
+        lib.hlbm_selftest_wait.argtypes = [_P, ctypes.c_longlong, ctypes.c_int]
         _libh = lib
         return lib
 
@@ -309,6 +311,15 @@ def hlbm_diagnostics_noalloc(state_ptr, precision, nx, ny, pitch, gamma, stream=
                               f"{HLBM_NOALLOC_MAX_CELLS} cells")
     _check(code)
     return out
+
+
+def hlbm_selftest_wait(budget_cycles, arrive, stream=None):
+    """Run the library's bounded device-side wait on its own: an mbarrier
+    armed for one arrival, which the device thread makes (arrive=True) or
+    never makes, polled for at most budget_cycles SM clock cycles.  Returns
+    the status code (HLBM_ERR_TIMEOUT when the wait ran out, HLBM_OK when it
+    completed) instead of raising."""
+    return _lib().hlbm_selftest_wait(stream or None, int(budget_cycles), 1 if arrive else 0)
 
 
 def hlbm_batch_create(params_list, stream=None):

@@ -134,3 +134,11 @@ def test_stream_handles_passed_through():
 
     assert hlbm.torch_stream_handle(7) == 7
     assert hlbm.torch_stream_handle(FakeStream()) == 0x5eed
+
+
+def test_selftest_wait_budget_checked_without_touching_the_gpu(lib):
+    """A wait budget outside 1 .. 2^31 cycles is refused before any CUDA
+    call."""
+    from paper_2002_03644_gb300 import hlbm
+    for budget in (0, -5, (1 << 31) + 1):
+        assert hlbm.hlbm_selftest_wait(budget, False) == hlbm.HLBM_ERR_ARG
