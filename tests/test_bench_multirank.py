@@ -51,3 +51,25 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.job_throughput(10.0, 2.0, 1) == 5.0
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under torchrun with N > 1 the reference arm (the oracle on the host)
+    runs and prints on rank 0 alone; the other ranks exit 0 without work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    base = dict(os.environ, WORLD_SIZE="2", MASTER_ADDR="127.0.0.1", MASTER_PORT=str(_free_port()))
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "1",
+           "--n", "256"]
+    r1 = subprocess.run(cmd, cwd=root, env=dict(base, RANK="1", LOCAL_RANK="1"), capture_output=True, text=True,
+                        timeout=300)
+    assert r1.returncode == 0 and r1.stdout.strip() == ""
+    r0 = subprocess.run(cmd, cwd=root, env=dict(base, RANK="0", LOCAL_RANK="0"), capture_output=True, text=True,
+                        timeout=300)
+    assert r0.returncode == 0
+    line = json.loads(r0.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
