@@ -102,3 +102,25 @@ def test_batch_sweep_draws():
         assert c.gamma in (1.4, 1.3, 1.67)
         cfl = (c.meta["Ma"] + 1.0) * np.sqrt(c.gamma * c.meta["theta_inf"] * CS2)
         assert cfl == pytest.approx(0.7, rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_surrogate_fields_hold_the_lowest_modes_around_a_mean_flow(seed):
+    """Surrogate training fields: only the 8 lowest Fourier modes per axis
+    on rho, u and theta, around a mean flow whose Mach number is drawn in
+    [0.3, 1.2]."""
+    n = 64
+    c = inputs.random_fourier(n=n, seed=seed)
+    theta0 = 300.0 / 1478.75
+    c0 = np.sqrt(1.4 * theta0 * CS2)
+    mx, my = c.ux.mean(), c.uy.mean()
+    ma = np.hypot(mx, my) / c0
+    assert 0.3 <= ma <= 1.2 and ma == pytest.approx(c.meta["Ma"], rel=1e-12)
+    k = np.fft.fftfreq(n) * n
+    KY, KX = np.meshgrid(k, k, indexing="ij")
+    outside = (np.abs(KX) >= 8) | (np.abs(KY) >= 8)
+    for f in (c.rho - 1.0, c.ux - mx, c.uy - my, c.theta / theta0 - 1.0):
+        F = np.abs(np.fft.fft2(f))
+        assert F.max() > 0.0
+        assert F[outside].max() < 1e-10 * F.max()
+        assert F[0, 0] < 1e-10 * F.max()  # no mean in the perturbation
