@@ -134,7 +134,7 @@ typedef struct hlbm_handle hlbm_handle;
  * a1_xx, a1_xy, a1_yy) and FP64 staging buffers.  *out is NULL on failure. */
 int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out);
 
-/* Algorithm 1, input and initialisation (steps 1-4): from [rho, u, theta]^(0)
+/* Input and initialisation (Sec. 3.5): from [rho, u, theta]^(0)
  * build s = c_v ln(theta / rho^(gamma-1)), a1^(0) (= a1^FD of eq. a1FD when
  * a1 is NULL, else the given three planes), psi^(0) and the post-collision
  * populations of level 0.  The fields are converted to the state's
@@ -144,7 +144,10 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out);
 int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const double *uy,
                      const double *theta, const double *a1, int mem_kind);
 
-/* Algorithm 1, steps 5-11, n times (n >= 0). */
+/* n time steps (n >= 0) of Algorithm 1: collision and streaming (eq streamalgo),
+ * moments (eqs rhoalgo, ualgo), entropy update (eq sequaalgo), temperature
+ * (eq Entropie expression), psi (eq Psialgo), f^eq (eq Equilibrium) and a1
+ * (eq a1sigalgo). */
 int hlbm_step(hlbm_handle *h, int64_t n);
 
 /* Fields of the current level: rho, ux, uy, theta, s (one plane each) and a1
@@ -269,28 +272,39 @@ void hlbm_sur_destroy(hlbm_sur *s);
 
 /* The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory -- code that must live inside a device
- * memory budget it does not own, or that runs while another component is
- * building a CUDA graph -- and still need the checks of hlbm_diagnostics.
+ * memory budget it does not own (a host framework that hands out buffers
+ * but forbids new allocations), or embedded code that may not grow the
+ * device footprint after start-up -- and still need the checks of
+ * hlbm_diagnostics.
  *
  * Same results, in the same order, as hlbm_diagnostics, for a state that
  * the caller holds: `state` points to device memory with 13 planes of
  * [ny][pitch] elements (FP64 or FP32 per `precision`: 9 post-collision
  * populations, s, a1_xx, a1_xy, a1_yy), the layout hlbm_get_state copies
  * after its header.  gamma is the heat capacity ratio of the case.  out is
- * a host array of 8 doubles; the call waits for `stream` (a cudaStream_t,
- * NULL for the legacy default stream) before returning.
+ * a host array of 8 doubles.
+ *
+ * `stream` must be an explicit cudaStream_t, best one created with
+ * cudaStreamNonBlocking, that is not being captured: the call enqueues its
+ * kernels and a copy to `out` on it and waits for the stream before
+ * returning.  NULL (the legacy default stream) and a capturing stream are
+ * refused with HLBM_ERR_ARG, so that the call never joins, or breaks,
+ * a capture.
  *
  * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
  * is one file-scope device array of (1024 * 8 + 8) doubles (65.6 KB), which
  * every GPU that loads the library holds until the process exits.  Grids
  * above HLBM_NOALLOC_MAX_CELLS cells are rejected with HLBM_ERR_ARG, as are
- * nx, ny < 1, pitch < nx, gamma <= 1 and NULL pointers.
+ * nx, ny < 1, pitch < nx, gamma <= 1, precisions other than HLBM_FP64 and
+ * HLBM_FP32, and NULL pointers.
  *
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
- * All calls share the one array and each overwrites what it reads, so
- * results never depend on earlier calls; calls that overlap on the GPU
- * (other streams or threads) race on it and must be serialised by the
+ * Every call looks up the array's device address on the current device (a
+ * lookup, not an allocation), so a cudaDeviceReset in between does no harm.
+ * The first call on a device, and the first after a reset, loads the
+ * library's module on it; make that call before any stream capture in the
+ * process begins.  All calls share the one array and each overwrites what it
+ * reads, so results never depend on earlier calls; calls that overlap on the
+ * GPU (other streams or threads) race on it and must be serialised by the
  * caller. */
 int hlbm_diagnostics_noalloc(const void *state, int precision, int nx, int ny, int pitch, double gamma,
                              double out[8], void *stream);

@@ -2,23 +2,26 @@
 //
 // Some callers cannot call cudaMalloc: code that runs inside another
 // runtime's memory budget (a host framework that hands out device buffers
-// but forbids new allocations), code running while a CUDA graph is being
-// built by someone else, or embedded callers that must not grow the device
-// footprint after start-up.  hlbm_diagnostics_noalloc serves them: it runs
-// the same FP64 reduction as hlbm_diagnostics, but its block partials live in
-// a file-scope device array of fixed size instead of handle-owned memory.
+// but forbids new allocations), or embedded callers that must not grow the
+// device footprint after start-up.  hlbm_diagnostics_noalloc serves them: it
+// runs the same FP64 reduction as hlbm_diagnostics, but its block partials
+// live in a file-scope device array of fixed size instead of handle-owned
+// memory.
 //
 // The array is a static __device__ symbol.  Host code must not pass its name
 // to a kernel (on the host the name is only a stand-in, not a device
-// address); the first call on each device looks up the real address with
-// cudaGetSymbolAddress while that device is current and caches it.
+// address): every call looks up the real address with cudaGetSymbolAddress
+// while the caller's device is current.  The lookup allocates nothing, and
+// looking it up each time keeps the address right after a cudaDeviceReset
+// (which unloads the module and places the array anew).  The first call on
+// a device (and the first after a reset) loads the module: the array and all
+// three kernels of this file.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "hlbm.h"
 
@@ -35,15 +38,11 @@ namespace {
 constexpr int NA_CHUNK = 16384;     // cells per block
 constexpr int NA_MAX_BLOCKS = 1024; // partial slots in the static array
 static_assert((long long)NA_CHUNK * NA_MAX_BLOCKS == HLBM_NOALLOC_MAX_CELLS, "capacity");
-constexpr int NA_MAX_DEVICES = 64;
 
 // [NA_MAX_BLOCKS][DIAG_NV] block partials followed by DIAG_NV results:
 // (1024 * 8 + 8) doubles = 65.6 KB, held by every device that loads the
 // library until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[NA_MAX_BLOCKS * DIAG_NV + DIAG_NV];
-
-std::mutex g_setup_mutex;
-double *g_scratch_addr[NA_MAX_DEVICES] = {nullptr};
 
 // Same reduction as diag_partial_kernel, but block b covers the fixed chunk
 // [b * NA_CHUNK, (b + 1) * NA_CHUNK) so that the number of partials is
@@ -94,18 +93,20 @@ diag_partial_chunk_kernel(const T *__restrict__ in, double *__restrict__ partial
     if (threadIdx.x < DIAG_NV) partial[blockIdx.x * DIAG_NV + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// Device address of the static array on the current device (looked up once
-// per device).
-cudaError_t scratch_address(int dev, double **out)
+// Device address of the static array on the current device, looked up on
+// every call.  The kernels are touched as well (cudaFuncGetAttributes), so
+// that the first call loads everything a later call of either precision
+// launches; neither step allocates device memory.
+cudaError_t scratch_address(double **out)
 {
-    std::lock_guard<std::mutex> lk(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, diag_partial_chunk_kernel<double>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, diag_partial_chunk_kernel<float>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, diag_final_kernel)) != cudaSuccess) return e;
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 
@@ -118,10 +119,17 @@ extern "C" int hlbm_diagnostics_noalloc(const void *state, int precision, int nx
     if ((long long)nx * ny > HLBM_NOALLOC_MAX_CELLS) return HLBM_ERR_ARG;  // beyond the static scratch
     if (precision != HLBM_FP64 && precision != HLBM_FP32) return HLBM_ERR_ARG;
     if (!(gamma > 1.0) || !state) return HLBM_ERR_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return HLBM_ERR_CUDA;
+    // the legacy default stream synchronises with every blocking stream, and
+    // work enqueued on it while another stream captures in global mode breaks
+    // that capture: only an explicit stream is taken, and not one that is
+    // being captured (the call ends with a synchronisation)
+    if (!stream) return HLBM_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return HLBM_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return HLBM_ERR_ARG;
     double *scratch = nullptr;
-    if (scratch_address(dev, &scratch) != cudaSuccess) return HLBM_ERR_CUDA;
+    if (scratch_address(&scratch) != cudaSuccess) return HLBM_ERR_CUDA;
     double *partial = scratch;
     double *result = scratch + NA_MAX_BLOCKS * DIAG_NV;
 
@@ -138,7 +146,6 @@ extern "C" int hlbm_diagnostics_noalloc(const void *state, int precision, int nx
 
     const long long ncell = (long long)nx * ny;
     const int nblocks = (int)((ncell + NA_CHUNK - 1) / NA_CHUNK);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // every call overwrites the nblocks partials and the result it reads, so
     // nothing has to start at zero
     if (precision == HLBM_FP64)

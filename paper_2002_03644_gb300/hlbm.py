@@ -301,8 +301,10 @@ def hlbm_destroy(h):
 def hlbm_diagnostics_noalloc(state_ptr, precision, nx, ny, pitch, gamma, stream=None):
     """Diagnostics of a caller-held device state without any allocation by
     the library (for callers that may not allocate device memory).
-    state_ptr: device address of 13 planes [ny][pitch].  Grids above
-    HLBM_NOALLOC_MAX_CELLS cells are refused."""
+    state_ptr: device address of 13 planes [ny][pitch].  stream: an explicit
+    cudaStream_t (int) that is not being captured; None (the legacy default
+    stream) and a capturing stream are refused, as are grids above
+    HLBM_NOALLOC_MAX_CELLS cells."""
     out = np.zeros(8)
     code = _lib().hlbm_diagnostics_noalloc(state_ptr, int(precision), int(nx), int(ny), int(pitch),
                                            float(gamma), out.ctypes.data, stream or None)
