@@ -4,9 +4,15 @@
  * A plain, slow, FP64 CPU restatement of the improved compressible hybrid
  * lattice Boltzmann method (HLBM) of Renard, Feng, Boussuge and Sagaut,
  * "Improved compressible Hybrid Lattice Boltzmann Method on standard lattice
- * for subsonic and supersonic flows" (arXiv 2002.03644).  It follows
- * Algorithm 1 ("HLBM", Sec. 3.5) step by step, with one full array per
- * intermediate quantity and straightforward loops over cells.
+ * for subsonic and supersonic flows" (arXiv 2002.03644).  It is organised by
+ * the equations it evaluates: the regularised collision and pull-streaming
+ * of the D2Q9 populations (eq streamalgo, Sec. 3.3), their moments (eqs
+ * rhoalgo, ualgo), the finite-volume entropy update (eq sequaalgo, Sec. 3.4)
+ * and temperature recovery (eq Entropie expression, Sec. 2.4), the closure
+ * correction psi (eq Psialgo, Sec. 3.2), the equilibrium (eq Equilibrium,
+ * Sec. 2.3) and the off-equilibrium moment a1 (eqs a1sigalgo, a1FD,
+ * Sec. 3.3).  One full array holds every intermediate quantity, and each is
+ * computed by a straightforward loop over cells.
  *
  * Only tests/, __graft_entry__.smoke() and the CPU-baseline leg of bench.py
  * may load this library.  The CUDA library shares no code, header, table or
@@ -22,7 +28,7 @@
  *  - The MUSCL / Van Albada advection of s is written in non-conservative
  *    form u . grad s with cell-velocity upwinding (Sec. 3.4; see muscl_term).
  *  - Every quantity in the entropy right-hand side is taken at level n
- *    (Algorithm 1, step 7); lambda = mu c_p / Pr is constant (the printed
+ *    (the entropy equation is explicit in time); lambda = mu c_p / Pr is constant (the printed
  *    mu / (c_p Pr) contradicts the paper's own decay and Couette formulas).
  *  - Boundaries: a ghost frame of width 2.  Periodic sides wrap, zero-gradient
  *    sides copy the nearest interior value, Dirichlet sides hold a fixed state
@@ -508,7 +514,7 @@ static void velocity_gradient(const hlbmo *o, const double *ux, const double *uy
 /* sgn with sgn(0) = 0 */
 static double sgn(double v) { return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0); }
 
-/* Correction force psi of one level (Algorithm 1, steps 4 and 9): Gamma from
+/* Correction force psi of one level (eq Psialgo, Sec. 3.2): Gamma from
  * the ghost-filled macros, E1 by the upwind difference of Sec. 3.2, E2 by
  * centred differences (eq E2 corr term), psi by eq (Psialgo).  The ablation
  * bits restore parts of the original model the paper improves on: bit 1
@@ -561,7 +567,7 @@ int hlbmo_init(hlbmo *o, const double *rho0, const double *ux0, const double *uy
                const double *a1opt)
 {
     const int n = o->nx * o->ny;
-    /* Algorithm 1, step 1: input [rho, u, theta]^(0) */
+    /* the input state [rho, u, theta]^(0) and s from eq (Entropie expression) */
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             const int c = y * o->nx + x, k = IX(o, x, y);
@@ -573,10 +579,10 @@ int hlbmo_init(hlbmo *o, const double *rho0, const double *ux0, const double *uy
         for (int x = 0; x < o->nx; x++) {
             const int c = y * o->nx + x, k = IX(o, x, y);
             double out[Q];
-            /* step 2: f^eq(0) */
+            /* f^eq(0), eq (Equilibrium) */
             hlbmo_feq_cell(o->rho[k], o->ux[k], o->uy[k], o->th[k], out);
             for (int i = 0; i < Q; i++) o->feq[i][k] = out[i];
-            /* step 3: a1(0) = a1^FD (or given) */
+            /* a1(0) = a1^FD of eq (a1FD), or the given one */
             if (a1opt) {
                 o->axx[k] = a1opt[c]; o->axy[k] = a1opt[n + c]; o->ayy[k] = a1opt[2 * n + c];
             } else {
@@ -586,7 +592,7 @@ int hlbmo_init(hlbmo *o, const double *rho0, const double *ux0, const double *uy
                 o->axx[k] = a[0][0]; o->axy[k] = a[0][1]; o->ayy[k] = a[1][1];
             }
         }
-    /* step 4: psi(0) */
+    /* psi(0), eq (Psialgo) */
     compute_psi(o, o->rho, o->ux, o->uy, o->th, o->psi);
     o->step = 0;
     return 0;
@@ -645,7 +651,7 @@ static int has_wall(const hlbmo *o)
     return 0;
 }
 
-/* Algorithm 1, step 5 for every interior cell: F_i = f^eq_i + (1 - 1/tau_bar)
+/* The regularised collision for every interior cell: F_i = f^eq_i + (1 - 1/tau_bar)
  * f1_i + psi_i / 2 (eq streamalgo), the post-collision populations of level n. */
 static void collide(hlbmo *o)
 {
@@ -672,7 +678,7 @@ static void collide(hlbmo *o)
     }
 }
 
-/* Entropy right-hand side of eq (sequaalgo) at level n (Algorithm 1, step 7):
+/* Entropy right-hand side of eq (sequaalgo), every term at level n:
  * -u . grad s (MUSCL, Van Albada) + div(lambda grad theta) / (rho theta)
  * + Phi / (rho theta). */
 static double entropy_rhs(const hlbmo *o, int x, int y)
@@ -720,7 +726,7 @@ static void swap_ptr(double **a, double **b) { double *t = *a; *a = *b; *b = t; 
 int hlbmo_step(hlbmo *o, long nsteps)
 {
     for (long it = 0; it < nsteps; it++) {
-        /* step 5: collide with [f^eq, a1, psi]^(n) ... */
+        /* collide with [f^eq, a1, psi]^(n), eq (streamalgo) ... */
         collide(o);
         /* ... and stream: fbar_i(x) = F_i(x - c_i) */
         ROWS_PARALLEL
@@ -729,7 +735,7 @@ int hlbmo_step(hlbmo *o, long nsteps)
                 const int k = IX(o, x, y);
                 for (int i = 0; i < Q; i++) o->fb[i][k] = o->F[i][IX(o, x - CX[i], y - CY[i])];
             }
-        /* step 6: rho, u at n+1, eqs (rhoalgo), (ualgo) */
+        /* rho, u at n+1, eqs (rhoalgo), (ualgo) */
         ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
@@ -742,14 +748,14 @@ int hlbmo_step(hlbmo *o, long nsteps)
                 }
                 o->rho1[k] = r; o->ux1[k] = mx / r; o->uy1[k] = my / r;
             }
-        /* step 7: s at n+1 from level-n rho, u, theta, a1 (explicit Euler, dt = 1) */
+        /* s at n+1 from level-n rho, u, theta, a1, eq (sequaalgo) (explicit Euler, dt = 1) */
         ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
                 const int k = IX(o, x, y);
                 o->s1[k] = o->s[k] + entropy_rhs(o, x, y);
             }
-        /* step 8: theta at n+1 */
+        /* theta at n+1, eq (Entropie expression) */
         ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
@@ -757,9 +763,9 @@ int hlbmo_step(hlbmo *o, long nsteps)
                 o->th1[k] = theta_of(o, o->rho1[k], o->s1[k]);
             }
         fill_level(o, o->rho1, o->ux1, o->uy1, o->th1, o->s1);
-        /* step 9: psi at n+1 */
+        /* psi at n+1, eq (Psialgo) */
         compute_psi(o, o->rho1, o->ux1, o->uy1, o->th1, o->psi1);
-        /* step 10: f^eq at n+1 */
+        /* f^eq at n+1, eq (Equilibrium) */
         ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
@@ -768,7 +774,7 @@ int hlbmo_step(hlbmo *o, long nsteps)
                 hlbmo_feq_cell(o->rho1[k], o->ux1[k], o->uy1[k], o->th1[k], out);
                 for (int i = 0; i < Q; i++) o->feq1[i][k] = out[i];
             }
-        /* step 11: a1 at n+1 = sigma a1^PR + (1 - sigma) a1^FD, eq (a1sigalgo) */
+        /* a1 at n+1 = sigma a1^PR + (1 - sigma) a1^FD, eq (a1sigalgo) */
         ROWS_PARALLEL
         for (int y = 0; y < o->ny; y++)
             for (int x = 0; x < o->nx; x++) {
@@ -825,7 +831,7 @@ void hlbmo_get_feq(const hlbmo *o, double *out9)
     for (int i = 0; i < Q; i++) copy_out(o, o->feq[i], out9 + (size_t)i * n);
 }
 
-/* Post-collision populations of the current level (step 5 without streaming). */
+/* Post-collision populations of the current level (eq streamalgo without streaming). */
 void hlbmo_get_post_collision(hlbmo *o, double *out9)
 {
     const int n = o->nx * o->ny;

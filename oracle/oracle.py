@@ -4,8 +4,10 @@ TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this module.  The product library
 (``paper_2002_03644_gb300``) never imports it.
 
-The oracle restates Algorithm 1 of Renard et al. (arXiv 2002.03644) in plain
-C with FP64 arithmetic; this module only marshals numpy arrays through ctypes.
+The oracle restates the equations of the time step of Renard et al. (arXiv
+2002.03644) -- collision and streaming, moments, the entropy update, the
+closure correction, the equilibrium and a1 (Sec. 2-3) -- in plain C with FP64
+arithmetic; this module only marshals numpy arrays through ctypes.
 """
 from __future__ import annotations
 
@@ -145,7 +147,7 @@ def muscl_term(u, smm, sm, s0, sp, spp):
 # ---- whole-grid solver ---------------------------------------------------------
 
 class Oracle:
-    """FP64 CPU solver following Algorithm 1.  Arrays are row-major [ny][nx]."""
+    """FP64 CPU solver of the paper's time step (Sec. 3).  Arrays are row-major [ny][nx]."""
 
     def __init__(self, nx, ny, gamma=1.4, Pr=0.71, mu=1e-3, sigma=0.0,
                  bc=(BC_PERIODIC,) * 4, bc_state=None, phi_mode=0, ablation=0):

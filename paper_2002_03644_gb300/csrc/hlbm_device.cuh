@@ -18,16 +18,16 @@
 // row-marching form (the FP32 default on larger grids, the batched form's
 // marching shapes, and the moment-state form).
 //
-// One launch of fused_step_kernel performs Algorithm 1 steps 5-11 for a tile
+// One launch of fused_step_kernel performs one time step of Algorithm 1 for a tile
 // of TX x TY cells:
 //   phase 0: s(n) on the tile plus a 3-cell halo -> shared memory
 //   phase 1: rho, u, theta at level n on tile + 2 (local moments of F(n))
-//   phase 2: on tile + 1: the entropy update (step 7, MUSCL / Van Albada,
-//            Fourier, viscous heating), pull-streaming and moments (steps
-//            5-6), theta (step 8), closure defect Gamma (Sec. 3.2)
-//   phase 3: on the tile: E1 (upwind) and E2 (centred) -> psi (step 9),
-//            f^eq (step 10), a1 = sigma a1^PR + (1 - sigma) a1^FD with the
-//            recurrence (step 11), and the regularised collision of the next
+//   phase 2: on tile + 1: the entropy update (eq sequaalgo, MUSCL / Van Albada,
+//            Fourier, viscous heating), pull-streaming and moments (eqs
+//            rhoalgo, ualgo), theta (eq Entropie expression), closure defect Gamma (Sec. 3.2)
+//   phase 3: on the tile: E1 (upwind) and E2 (centred) -> psi (eq Psialgo),
+//            f^eq (eq Equilibrium), a1 = sigma a1^PR + (1 - sigma) a1^FD with the
+//            recurrence (eq a1sigalgo, Sec. 3.3), and the regularised collision of the next
 //            step, written as F(n+1), s(n+1), a1(n+1).
 // The populations are rebuilt from their nine raw moments with a 1-D x 1-D
 // inverse transform (the D2Q9 lattice is the tensor product of two D1Q3
@@ -389,7 +389,7 @@ __device__ __forceinline__ T gamma_defect(T rho, T ua, T th)
     return rho * ua * (T(1) - th - ua * ua);
 }
 
-// One tile of Algorithm 1, steps 5-11 (all threads of the CTA take part;
+// One tile of one time step of Algorithm 1 (all threads of the CTA take part;
 // the caller separates consecutive tiles with a barrier).
 template <typename T, typename S, int TX, int TY, int NT>
 __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ inF, const T *__restrict__ inA,
@@ -507,7 +507,7 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
                 axx = __ldg(inA + A_XX * P + o); axy = __ldg(inA + A_XY * P + o); ayy = __ldg(inA + A_YY * P + o);
             }
         }
-        // step 7: entropy update from level-n fields
+        // entropy update from level-n fields (eq sequaalgo)
         const int k2 = (ly + 1) * R2X + lx + 1;
         const T rho0 = mRho[k2], th0 = mTh[k2], ux0 = mUx[k2], uy0 = mUy[k2];
         const T dxux = T(0.5) * (mUx[k2 + 1] - mUx[k2 - 1]);
@@ -529,7 +529,7 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
             phi = cs.mu * (d1 * d1 + d2 * d2);
         }
         const T s1 = s0 - adv + fdiv(cs.lam * lap + phi, rt);
-        // steps 5-6: pull the post-collision populations (shared memory), moments
+        // pull the post-collision populations (shared memory), moments (eqs rhoalgo, ualgo)
         T f[9];
 #pragma unroll
         for (int i = 0; i < 9; i++) f[i] = sF[i * N2 + k2 - cxi(i) - cyi(i) * R2X];
@@ -537,7 +537,7 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
         moments(f, rho1, jx, jy);
         const T ir = fdiv(T(1), rho1);
         nRho[c] = rho1; nUx[c] = jx * ir; nUy[c] = jy * ir;
-        nTh[c] = cs.theta(rho1, s1);  // step 8
+        nTh[c] = cs.theta(rho1, s1);  // eq (Entropie expression)
         nS[c] = s1;
     }
     __syncthreads();
@@ -583,7 +583,7 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
         }
     }
 
-    // phase 3: steps 9-11 and the collision of the next step on the tile
+    // phase 3: psi, f^eq, a1 and the collision of the next step on the tile
     for (int c = threadIdx.x; c < TX * TY; c += NT) {
         const int ly = c / TX, lx = c - ly * TX;
         const int gx = x0 + lx, gy = y0 + ly;
@@ -782,7 +782,7 @@ __global__ void wall_ghost_kernel(const typename S::raw *__restrict__ inF, const
     wg[9 * stride + w] = (T)(kp.cv * (log((double)c.th) - kp.gm1 * log((double)c.rho)));
 }
 
-// ---- initialisation (Algorithm 1, steps 1-4) -----------------------------------
+// ---- initialisation (Sec. 3.5: f^eq, a1^FD and psi of the input state) --------
 // Entropy of an initial cell, s = c_v (ln theta - (gamma - 1) ln rho), in the
 // arithmetic type of the state.
 __device__ __forceinline__ double init_entropy(const KParams &kp, double rho, double th)

@@ -1,4 +1,4 @@
-// hlbm_march.cuh -- the fused step of Algorithm 1 (steps 5-11) as a
+// hlbm_march.cuh -- the fused time step of Algorithm 1 as a
 // row-marching kernel: each CTA owns a strip of columns and walks down a
 // segment of rows, so that only the x halo is loaded and computed twice
 // (a tiled kernel recomputes a halo in both directions).
@@ -7,10 +7,12 @@
 //   load:    F(n) of row r+2 and s(n) of row r+3 (prefetched into registers
 //            one iteration earlier), the level-n rho, u, theta of row r+2
 //            (local moments of F(n), theta from s(n) of the same cell)
-//   phase 2: level n+1 of row r+1: the entropy update (step 7),
-//            pull-streaming and moments (steps 5-6), theta (step 8), and
+//   phase 2: level n+1 of row r+1: the entropy update (eq sequaalgo),
+//            pull-streaming and moments (eqs streamalgo, rhoalgo, ualgo),
+//            theta (eq Entropie expression), and
 //            the second moments of the pulled populations when sigma > 0
-//   phase 3: row r: E1, E2, a1 and the regularised collision (steps 9-11),
+//   phase 3: row r: E1, E2, a1 and the regularised collision (eqs Psialgo,
+//            Equilibrium, a1sigalgo, streamalgo),
 //            written as F(n+1), s(n+1), a1(n+1).
 // Rows live in shared-memory rings; a segment starts four rows early to
 // fill them.  The arithmetic of every cell is that of the tiled kernel,
@@ -87,7 +89,8 @@ struct CellN1 {
     T rho, ux, uy, th, s, mxx, myy, mxy;
 };
 
-// Steps 5-8 for one cell (the arithmetic of phase 2 of the tiled kernel).
+// Pull, moments, entropy and theta of level n+1 for one cell (the arithmetic
+// of phase 2 of the tiled kernel).
 // W/E/S/N = x-1, x+1, y-1, y+1; g[] the pulled populations.
 template <typename T, bool SIG, bool PHI0>
 __device__ __forceinline__ CellN1<T> level_np1(const Consts<T> &cs, T rho0, T ux0, T uy0, T th0, T uxW, T uxE,
@@ -130,7 +133,7 @@ __device__ __forceinline__ CellN1<T> level_np1(const Consts<T> &cs, T rho0, T ux
     return o;
 }
 
-// Steps 9-11 and the next collision for one cell (phase 3 of the tiled
+// psi, f^eq, a1 and the next collision for one cell (phase 3 of the tiled
 // kernel) from its level-(n+1) values and those of its four neighbours.
 template <typename T, bool SIG>
 __device__ __forceinline__ void collide_cell(const Consts<T> &cs, bool cen, const CellN1<T> &c, T rW, T uxW, T uyW,
@@ -1036,7 +1039,7 @@ march_moment_kernel(const float *__restrict__ in, float *__restrict__ out, const
     moment_segment<NT, SIG, PHI0, PER>(in, out, kp, blockIdx.x * MomGeom<NT>::W, ys, ye, smem_raw);
 }
 
-// Moment state from FP64 caller fields (Algorithm 1, steps 1-4): rho, u, s
+// Moment state from FP64 caller fields (the initialisation of Sec. 3.5): rho, u, s
 // and a1 (given, or a1^FD of the initial fields as in init_kernel), computed
 // in FP32 from the fields rounded to FP32, as init_kernel does for FP32.
 __global__ void init_moments_kernel(const double *__restrict__ rho, const double *__restrict__ ux,

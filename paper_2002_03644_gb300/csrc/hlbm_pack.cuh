@@ -145,7 +145,7 @@ struct CellN1x2 {
     f2 rho, ux, uy, th, s, mxx, myy, mxy;
 };
 
-// Steps 5-8 for two cells (level_np1).
+// Pull, moments, entropy and theta of level n+1 for two cells (level_np1).
 template <bool SIG, bool PHI0>
 __device__ __forceinline__ CellN1x2 level_np1_2(const Consts<float> &cs, f2 rho0, f2 ux0, f2 uy0, f2 th0, f2 uxW,
                                                f2 uxE, f2 uxS, f2 uxN, f2 uyW, f2 uyE, f2 uyS, f2 uyN, f2 thW,

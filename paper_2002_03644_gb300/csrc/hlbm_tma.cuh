@@ -288,7 +288,7 @@ fused_step_tma_kernel(const __grid_constant__ TmaMaps maps, const float *__restr
             __syncthreads();
         }
 
-        // phase 3: steps 9-11 and the collision on the tile
+        // phase 3: psi, f^eq, a1 and the collision on the tile
         for (int c = threadIdx.x; c < TX * TY; c += NT) {
             const int ly = c / TX, lx = c - ly * TX;
             const int gx = x0 + lx, gy = y0 + ly;

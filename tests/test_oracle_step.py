@@ -138,7 +138,7 @@ def test_dirichlet_sides_holding_the_same_state_keep_a_uniform_flow():
 @pytest.mark.parametrize("sigma", [1.0, 0.7, 0.0])
 def test_single_cell_collision_decays_geometrically(sigma):
     """On a 1x1 periodic grid every neighbour is the cell itself: gradients,
-    psi and a1^FD vanish, rho, u, theta and s stay fixed, and step 11 gives
+    psi and a1^FD vanish, rho, u, theta and s stay fixed, and eq (a1sigalgo) gives
     a1^(n+1) = sigma (1 - 1/tau_bar) a1^(n) exactly (eq. streamalgo with the
     orthogonality of the Hermite basis)."""
     rho, ux, uy, th, mu = 1.2, 0.3, -0.2, 0.4, 0.05
@@ -176,7 +176,7 @@ def test_mass_and_momentum_conserved_on_periodic_grid():
 @pytest.mark.parametrize("u", [0.31, -0.27])
 def test_entropy_advection_exact_for_linear_entropy(u):
     """With mu = 0 (no conduction, no heating) and a uniform velocity, the
-    entropy right-hand side of step 7 equals -u ds/dx exactly when s is
+    entropy right-hand side of eq (sequaalgo) equals -u ds/dx exactly when s is
     linear in x (the limited slopes reproduce linear data)."""
     nx, ny, k = 16, 3, 0.01
     rho = np.full((ny, nx), 1.0)
@@ -194,7 +194,7 @@ def test_entropy_advection_exact_for_linear_entropy(u):
 @pytest.mark.parametrize("cx,cy", [(0.0, 0.0), (3e-5, 0.0), (1e-5, -2e-5)])
 def test_entropy_conduction_term_of_a_quadratic_temperature(cx, cy):
     """Gas at rest (no advection; no heating, since grad u = 0 and a1 = 0):
-    the entropy right-hand side of step 7 is the conduction term
+    the entropy right-hand side of eq (sequaalgo) is the conduction term
     lambda lap(theta) / (rho theta) alone.  The 5-point Laplacian of a
     quadratic theta is exactly 2 (cx + cy), so a linear theta gives zero and
     a quadratic one lambda 2 (cx + cy) / (rho theta) at every interior cell,
