@@ -103,6 +103,56 @@ def backward(params, cache, y, target):
     return grads, dx_total
 
 
+# ---- the same network with BF16 storage -----------------------------------
+# The configuration trains the network "in BF16 with FP32 accumulation":
+# inputs, weights, hidden activations and the back-propagated gradients that
+# enter the tensor-core products are held in BF16 (8 significant bits);
+# every sum is exact here (FP64) instead of FP32.  What remains between this
+# and the GPU is FP32 accumulation order and the rare BF16 rounding that an
+# FP32 sum puts on the other side of a rounding boundary.
+
+def bf16_round(a):
+    """Round to the nearest BF16 value (8 significant bits), ties to even:
+    a = m 2^e with 0.5 <= |m| < 1, and m 2^8 is rounded to an integer."""
+    m, e = np.frexp(np.asarray(a, dtype=np.float64))
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def forward_bf16(params, x):
+    """forward() with BF16 storage: the input, the weights and every hidden
+    activation rounded to BF16; biases, sums and the residual stay exact (the
+    residual adds the unrounded input)."""
+    pb = [(bf16_round(W), b) for W, b in params]
+    h = bf16_round(x)
+    acts, pre = [h], []
+    L = len(pb)
+    for l, (W, b) in enumerate(pb):
+        z = conv3x3_periodic(h, W, b)
+        pre.append(z)
+        if l < L - 1:
+            h = bf16_round(gelu(z))
+        acts.append(h)
+    return x + pre[-1], (acts, pre, pb)
+
+
+def backward_bf16(cache, y, target):
+    """backward() with BF16 storage: each layer's pre-activation gradient dz
+    enters the weight-gradient and input-gradient products rounded to BF16,
+    with the layer's BF16 weights and activations; the bias gradient sums
+    the unrounded dz."""
+    acts, pre, pb = cache
+    L = len(pb)
+    dz = 2.0 * (y - target) / y.size
+    grads = [None] * L
+    for l in range(L - 1, -1, -1):
+        dzb = bf16_round(dz)
+        dx, dW, _ = conv3x3_periodic_backward(acts[l], pb[l][0], dzb)
+        grads[l] = (dW, dz.sum(axis=(0, 2, 3)))
+        if l > 0:
+            dz = dx * gelu_grad(pre[l - 1])
+    return grads
+
+
 def adam_update(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam step (Kingma & Ba 2015) on arrays, returning new (p, m, v)."""
     m = beta1 * m + (1.0 - beta1) * g

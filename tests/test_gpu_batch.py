@@ -1,8 +1,8 @@
 """Batched form: many FP32 cases of uneven size and parameters advanced by one
 persistent launch per step (replayed from a CUDA graph).  Each case is
-compared with the same case stepped alone by the single-case kernel of the
-same work shape: tile shape 0 of the tiled kernel must agree bitwise; the
-other shapes (kinds 1-4) and the row-marching kernel with the same segment
+compared with the FP64 oracle at the FP32 parity bound, and with the same
+case stepped alone by the single-case kernel of the same work shape: tile
+shape 0 of the tiled kernel must agree bitwise; the other shapes (kinds 1-4) and the row-marching kernel with the same segment
 height (kinds 5-10) run the same per-tile or per-segment source, but inlined
 into a different kernel the compiler may fuse a different set of
 multiply-adds, so they must agree to 1e-5 of each field's scale (ten times
@@ -82,6 +82,37 @@ def test_batch_equals_separate_runs_bitwise(hl, monkeypatch, kind):
                 assert close(g, m, k, c.gamma), (c.name, c.nx, k)
     for v in b.cases:
         assert v.step_count == 37
+    b.close()
+
+
+@pytest.mark.parametrize("kind", [0, 6, 10, None], ids=["tile0", "march32", "march128", "autotuned"])
+def test_batch_matches_the_fp64_oracle(hl, monkeypatch, kind):
+    """Every case of a batch (vortices of uneven size, Mach and gamma, and a
+    Sod tube) after 37 steps against the FP64 oracle run on that case alone:
+    all six fields within the FP32 parity bound (1e-4 of the field scales of
+    the single-case parity tests), and a1 at its own scale within the
+    single-case FP32 bound for 37 steps (a1_bound).  The work shapes
+    include a tiled shape, two row-marching shapes and the autotuner's
+    choice."""
+    from oracle.oracle import Oracle
+    from test_gpu_parity import TOL, a1_bound, compare
+    cases = make_cases()
+    spec = [dict(nx=c.nx, ny=c.ny, precision=1, **c.params()) for c in cases]
+    if kind is None:
+        monkeypatch.delenv("HLBM_BATCH_TILE", raising=False)
+    else:
+        monkeypatch.setenv("HLBM_BATCH_TILE", str(kind))
+    b = hl.Batch(spec)
+    for view, c in zip(b.cases, cases):
+        view.init(*c.fields())
+    if kind is None:
+        b.autotune()
+    b.step(37)
+    for view, c in zip(b.cases, cases):
+        o = Oracle(c.nx, c.ny, **c.params())
+        o.init(*c.fields())
+        o.step(37)
+        compare(view.macros(), o.macros(), c.gamma, TOL[1], a1_own=a1_bound(1, c.sigma, 37))
     b.close()
 
 

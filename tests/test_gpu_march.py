@@ -12,7 +12,7 @@ import pytest
 
 from oracle.oracle import Oracle
 from paper_2002_03644_gb300 import inputs
-from test_gpu_parity import BCS, TOL, _env, compare, run_pair
+from test_gpu_parity import BCS, TOL, _env, a1_bound, compare, run_pair
 from test_gpu_precision import BOUND, errors
 
 pytestmark = pytest.mark.gpu
@@ -41,7 +41,7 @@ def test_march_variants(hl, precision, variant, bc):
                                 sigma=0.5, bc=bc, bc_state=BS)
     with _env(HLBM_MARCH=variant):
         _, _, got, ref = run_pair(hl, case, precision, 9)
-    compare(got, ref, case.gamma, TOL[precision])
+    compare(got, ref, case.gamma, TOL[precision], a1_own=a1_bound(precision, case.sigma, 9))
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -52,7 +52,7 @@ def test_march_boundaries(hl, precision, variant, bc):
                                 sigma=0.5, bc=bc, bc_state=BS)
     with _env(HLBM_MARCH=variant, HLBM_MARCH_ROWS=5):
         _, _, got, ref = run_pair(hl, case, precision, 20)
-    compare(got, ref, case.gamma, TOL[precision])
+    compare(got, ref, case.gamma, TOL[precision], a1_own=a1_bound(precision, case.sigma, 20))
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -64,7 +64,7 @@ def test_march_segments(hl, precision, variant, rows, nx, ny, sigma):
     case = inputs.random_smooth(nx, ny, seed=100 + nx, amp=0.05, mu=2e-3, sigma=sigma)
     with _env(HLBM_MARCH=variant, HLBM_MARCH_ROWS=rows):
         _, _, got, ref = run_pair(hl, case, precision, 12)
-    compare(got, ref, case.gamma, TOL[precision])
+    compare(got, ref, case.gamma, TOL[precision], a1_own=a1_bound(precision, sigma, 12))
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -76,7 +76,7 @@ def test_march_phi_fd_and_ablations(hl, precision):
         for variant in (0, 3):
             with _env(HLBM_MARCH=variant):
                 _, _, got, ref = run_pair(hl, case, precision, 10)
-            compare(got, ref, case.gamma, TOL[precision])
+            compare(got, ref, case.gamma, TOL[precision], a1_own=a1_bound(precision, case.sigma, 10))
 
 
 def test_march_16bit_forms_within_their_bounds(hl):

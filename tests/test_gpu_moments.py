@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2002_03644_gb300 import inputs
-from test_gpu_parity import BCS, TOL, _env, compare, run_pair
+from test_gpu_parity import BCS, TOL, _env, a1_bound, compare, run_pair
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +35,7 @@ def hl():
 def test_moments_periodic_random_fields(hl, nx, ny, sigma):
     case = inputs.random_smooth(nx, ny, seed=100 + nx, amp=0.05, mu=2e-3, sigma=sigma)
     _, _, got, ref = run_pair(hl, case, MOM, 12)
-    compare(got, ref, case.gamma, TOL[1])
+    compare(got, ref, case.gamma, TOL[1], a1_own=a1_bound(1, sigma, 12))
 
 
 @pytest.mark.parametrize("bc", BCS)
@@ -45,7 +45,7 @@ def test_moments_boundaries(hl, bc, sigma):
                                 sigma=sigma, bc=bc, bc_state=BS)
     with _env(HLBM_MARCH_ROWS=5):
         _, _, got, ref = run_pair(hl, case, MOM, 20)
-    compare(got, ref, case.gamma, TOL[1])
+    compare(got, ref, case.gamma, TOL[1], a1_own=a1_bound(1, sigma, 20))
 
 
 @pytest.mark.parametrize("rows", [1, 3, 100000])
@@ -55,7 +55,7 @@ def test_moments_segments(hl, rows, bc):
                                 sigma=0.3, bc=bc, bc_state=BS)
     with _env(HLBM_MARCH_ROWS=rows):
         _, _, got, ref = run_pair(hl, case, MOM, 12)
-    compare(got, ref, case.gamma, TOL[1])
+    compare(got, ref, case.gamma, TOL[1], a1_own=a1_bound(1, case.sigma, 12))
 
 
 def test_moments_phi_fd_ablations_and_given_a1(hl):
@@ -64,7 +64,7 @@ def test_moments_phi_fd_ablations_and_given_a1(hl):
         case.phi_mode = phi_mode
         case.ablation = ablation
         _, _, got, ref = run_pair(hl, case, MOM, 10)
-        compare(got, ref, case.gamma, TOL[1])
+        compare(got, ref, case.gamma, TOL[1], a1_own=a1_bound(1, case.sigma, 10))
     case = inputs.random_smooth(30, 26, seed=4, amp=0.04, mu=3e-3, sigma=0.4)
     a1 = np.random.default_rng(3).normal(size=(3, case.ny, case.nx)) * 1e-4
     _, _, got, ref = run_pair(hl, case, MOM, 6, a1=a1)
@@ -74,7 +74,7 @@ def test_moments_phi_fd_ablations_and_given_a1(hl):
 def test_moments_vortex_and_sod(hl):
     case = inputs.vortex(n=256, R=8.0)
     _, _, got, ref = run_pair(hl, case, MOM, 40)
-    compare(got, ref, case.gamma, TOL[1])
+    compare(got, ref, case.gamma, TOL[1], a1_own=a1_bound(1, case.sigma, 40))
     # a shock: L2 over the fields (rounding differences grow at the discontinuities)
     case = inputs.sod(C0=3.875, mu=3e-6, sigma=0.0)
     _, _, got, ref = run_pair(hl, case, MOM, 100)

@@ -1,13 +1,22 @@
 """The learned surrogate's CUDA kernels against the FP64 reference
 (oracle/surrogate_oracle.py), and what training buys.
 
-Tolerance: the GPU multiplies BF16 operands (8-bit mantissa, relative
-rounding 2^-9) and accumulates in FP32, and it also rounds every layer's
+Tolerance: the GPU multiplies BF16 operands (8 significant bits, unit
+roundoff 2^-8) and accumulates in FP32, and it also rounds every layer's
 output to BF16.  For sums of a few hundred products with random signs
 this leaves a relative error of order 1e-3 to 1e-2 in outputs and
 gradients.  So outputs and gradients are compared norm-wise at 3e-2, and
-gradients must also point the same way (cosine > 0.999).  Adam's update is
-plain FP32 and is compared at 1e-5."""
+gradients must also point the same way (cosine > 0.999).
+
+Element by element, on the configured network (4 -> 64 x 5 -> 4, the
+64 -> 64 layers on the tcgen05 kernels): every element of the output
+increment y - x and of every layer's weight and bias gradient is compared,
+as max |GPU - reference| over that tensor's max |reference|:
+  - against the BF16-storage reference (the same roundings, exact sums):
+    1e-2.  What remains is FP32 summation order and the BF16 roundings that
+    it flips (measured at most 3.8e-3);
+  - against the exact FP64 network: 3e-2 (measured at most 9.8e-3).
+Adam's update is plain FP32 and is compared at 1e-5."""
 import math
 
 import numpy as np
@@ -83,6 +92,50 @@ def test_forward_and_gradients_match_reference(env, widths, shape):
     sur.close()
 
 
+CONFIGURED = (4, 64, 64, 64, 64, 64, 4)
+
+
+@pytest.mark.parametrize("shape", [(2, 6, 256), (1, 12, 20)], ids=["6x256", "12x20"])
+def test_configured_network_element_by_element(env, shape):
+    """The configured surrogate on an image as wide as its 256^2 grid (the
+    tensor-core path) and on a small one (the mma.sync path): the output and
+    every gradient, element by element, against the BF16-storage reference
+    and against the exact FP64 network."""
+    torch, hlbm, surrogate = env
+    B, H, W = shape
+    widths = CONFIGURED
+    sur = surrogate.Surrogate(widths, H, W, batch_max=B, seed=3)
+    params = unpack(widths, sur.params())
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(B, H, W, widths[0])).astype(np.float32)
+    t = (x + 0.1 * rng.normal(size=x.shape)).astype(np.float32)
+    y = sur.forward(torch.from_numpy(x).cuda()).cpu().numpy().transpose(0, 3, 1, 2).astype(np.float64)
+    hlbm.hlbm_sur_backward(sur.s, torch.from_numpy(t).cuda())
+    g = sur.grads().astype(np.float64)
+    sur.synchronize()
+    sur.close()
+    xo = x.transpose(0, 3, 1, 2).astype(np.float64)
+    to = t.transpose(0, 3, 1, 2).astype(np.float64)
+    y_exact, cache = S.forward(params, xo)
+    g_exact, _ = S.backward(params, cache, y_exact, to)
+    y_b16, cache_b = S.forward_bf16(params, xo)
+    g_b16 = S.backward_bf16(cache_b, y_b16, to)
+
+    def elementwise(a, ref):
+        return float(np.abs(a - ref).max() / np.abs(ref).max())
+
+    for ref_y, ref_g, bound in ((y_b16, g_b16, 1e-2), (y_exact, g_exact, 3e-2)):
+        errs = {"y - x": elementwise(y - xo, ref_y - xo)}
+        o = 0
+        for l, (dw, db) in enumerate(ref_g):
+            errs[f"dW{l}"] = elementwise(g[o:o + dw.size].reshape(dw.shape), dw)
+            o += dw.size
+            errs[f"db{l}"] = elementwise(g[o:o + db.size], db)
+            o += db.size
+        bad = {k: v for k, v in errs.items() if not v <= bound}
+        assert not bad, (bound, bad)
+
+
 def test_adam_matches_reference(env):
     torch, hlbm, surrogate = env
     widths = (4, 16, 4)
@@ -126,6 +179,42 @@ def test_training_beats_persistence_and_hybrid_rollout(env):
     state, log = surrogate.hybrid_rollout(sur, norm, case, calls=8, K=K, judge_every=4, tol=1e-9)
     assert len(log) == 2 and all(back for _, _, back in log)  # tol so small that the HLBM always takes over
     assert np.isfinite(state).all()
+
+    # a realistic tolerance on the device-resident rollout: eight held-out
+    # initial states, the judge on every second call.  A first pass accepts
+    # every finite error and records the judged errors of the first judged
+    # call; with the tolerance at their median, the second pass (identical up
+    # to that call) accepts the states at or below it and falls back on the
+    # others, which continue from exactly the HLBM's result over the whole
+    # window (two calls of K steps from the initial state).
+    dnorm = surrogate.DeviceNormaliser(torch.from_numpy(X[:60]).float().cuda())
+    cases = [inputs.random_fourier(n=n, seed=2000 + b, mu=2e-3) for b in range(8)]
+    x0 = torch.stack([torch.from_numpy(np.stack(c.fields(), axis=-1)) for c in cases]).float().cuda()
+    judge = surrogate.FieldJudge(n, cases[0].params())
+    sur8 = surrogate.Surrogate((4, 32, 32, 4), n, n, batch_max=8, seed=0)
+    sur8.set_params(sur.params())
+    _, log0 = surrogate.hybrid_rollout_device(sur8, dnorm, judge, x0.clone(), calls=2, K=K, judge_every=2)
+    errs = np.array([e for _, _, e, _ in log0])
+    assert len(errs) == 8 and np.isfinite(errs).all() and not any(b for *_, b in log0)
+    tol = float(np.median(errs))
+    # the states just before the judged call, for the fallback check
+    first = dnorm.inv(sur8.predict(dnorm.fwd(x0).contiguous()))
+    state, log1 = surrogate.hybrid_rollout_device(sur8, dnorm, judge, x0.clone(), calls=2, K=K, judge_every=2,
+                                                  tol=tol)
+    backs = np.array([b for *_, b in log1])
+    assert np.allclose([e for _, _, e, _ in log1], errs, rtol=0, atol=1e-6)
+    assert np.array_equal(backs, errs > tol)
+    assert 0 < backs.sum() < 8, (errs, tol)
+    ref = torch.empty_like(x0[0])
+    for b in np.flatnonzero(backs):
+        judge.advance(x0[b], 2 * K, ref)
+        assert torch.equal(state[b], ref), b
+    for b in np.flatnonzero(~backs):
+        judge.advance(first[b], K, ref)  # the judge's own run, for the accepted ones
+        err = float((dnorm.fwd(state[b]) - dnorm.fwd(ref)).abs().max())
+        assert err == pytest.approx(errs[b], abs=1e-6) and err <= tol
+    judge.close()
+    sur8.close()
     sur.close()
 
 

@@ -106,10 +106,12 @@ def _table1(golden_dir):
 @pytest.mark.parametrize("row", range(6))
 def test_shear_wave_viscosity_matches_table1(row, golden_dir):
     """Sec. 4.1: nu measured from the fitted decay of max(u_x) reproduces
-    the printed relative errors of the present model within 15 %."""
+    the printed relative errors of the present model within 11 % (measured:
+    10.1 % at nu = 0.1 m^2/s, Ma 0.5, and 0.3 % to 3.3 % on the other five
+    rows)."""
     nu_phys, Ma, eps_paper = _table1(golden_dir)[row]
     eps = _shear_eps(nu_phys, Ma)
-    assert abs(eps - eps_paper) <= 0.15 * eps_paper, (nu_phys, Ma, eps, eps_paper)
+    assert abs(eps - eps_paper) <= 0.11 * eps_paper, (nu_phys, Ma, eps, eps_paper)
 
 
 def _original_rows(golden_dir):

@@ -85,3 +85,55 @@ def test_adam_first_step_moves_by_lr_times_sign():
     p1, m, v = S.adam_update(p, g, np.zeros(3), np.zeros(3), 1, lr=1e-2)
     # bias-corrected first step: m_hat / sqrt(v_hat) = sign(g) (eps aside)
     assert np.allclose(p1, p - 1e-2 * np.sign(g), atol=1e-7)
+
+
+# ---- the BF16-storage form ------------------------------------------------
+
+def _bf16_bits(x32):
+    """Float32 -> nearest BF16 (ties to even) by the usual bit-level route:
+    add 0x7FFF plus the lowest kept bit, then clear the low 16 bits."""
+    u = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_round_matches_bit_level_float32_rounding():
+    r = np.random.default_rng(21)
+    x = (r.normal(size=20000) * 10.0 ** r.uniform(-6, 6, size=20000)).astype(np.float32)
+    assert np.array_equal(S.bf16_round(x.astype(np.float64)), _bf16_bits(x))
+
+
+def test_bf16_round_keeps_bf16_values_and_ties_to_even():
+    k = np.arange(128, 256)
+    exact = np.concatenate([k * 2.0 ** -7, -k * 2.0 ** 3])
+    assert np.array_equal(S.bf16_round(exact), exact)
+    # midpoints between neighbours 1 + j 2^-7 and 1 + (j + 1) 2^-7 go to even j
+    assert S.bf16_round(1.0 + 2.0 ** -8) == 1.0
+    assert S.bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    x = np.random.default_rng(2).normal(size=1000)
+    # unit roundoff of 8 significant bits: 2^-8
+    assert np.max(np.abs(S.bf16_round(x) - x) / np.abs(x)) <= 2.0 ** -8
+
+
+def test_bf16_network_without_rounding_to_do_is_the_exact_network():
+    """With one layer (no hidden activation to round), BF16 inputs and BF16
+    weights the BF16 form is the exact network bitwise; with hidden layers it
+    stays within BF16 rounding of it."""
+    r = np.random.default_rng(8)
+    W = S.bf16_round(r.normal(size=(3, 3, 3, 3)) * 0.3)
+    b = r.normal(size=3)
+    x = S.bf16_round(r.normal(size=(2, 3, 5, 7)))
+    y, _ = S.forward([(W, b)], x)
+    yb, _ = S.forward_bf16([(W, b)], x)
+    assert np.array_equal(y, yb)
+    params = _net((4, 8, 8, 4), seed=3)
+    x = r.normal(size=(2, 4, 6, 8))
+    t = r.normal(size=x.shape)
+    y, cache = S.forward(params, x)
+    yb, cb = S.forward_bf16(params, x)
+    assert np.linalg.norm(yb - y) <= 2.0 ** -6 * np.linalg.norm(y - x)
+    g, _ = S.backward(params, cache, y, t)
+    gb = S.backward_bf16(cb, yb, t)
+    for (dw, db), (dwb, dbb) in zip(g, gb):
+        assert np.linalg.norm(dwb - dw) <= 2.0 ** -5 * np.linalg.norm(dw)
+        assert np.linalg.norm(dbb - db) <= 2.0 ** -5 * np.linalg.norm(db)
