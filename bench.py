@@ -9,10 +9,18 @@ kernel).  The state (2 x 54.5 MB) fits in L2, so L2 is flushed between timed
 steps (a write of one buffer and a read of another, each larger than L2) and
 each step is timed alone with CUDA events on the library's stream.
 
-Prints one JSON line.  --impl reference times the FP64 CPU oracle on the host
-cores on a bounded sample of the same workload.  Under torchrun every rank
-runs an independent replica on its own GPU (the method has no exchange step
-in this single-GPU build); value is the sum over ranks.
+Prints one JSON line.  Beside the headline step it carries, on one GPU, the
+end-to-end figure through the C ABI with host buffers (per step, and
+amortised over 100 steps per call), the FP64 oracle on the host cores as the
+CPU baseline, and two sub-objects for the forms grown from the step:
+`batched` (the 64-case vortex sweep advanced together against the same
+cases one after another, with both compared to the FP64 oracle) and
+`surrogate` (the K = 16 learned surrogate trained in the run, one call
+against 16 solver steps, and a hybrid rollout judged by the solver at a
+sweep of tolerances).  --impl reference times the FP64 CPU oracle on the
+host cores on the same workload.  Under torchrun every rank runs an
+independent replica on its own GPU (the method has no exchange step in this
+single-GPU build); value is the sum over ranks.
 """
 from __future__ import annotations
 
@@ -49,12 +57,23 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--surrogate", action="store_true",
-                    help="train the K=16 conv surrogate on HLBM rollouts and compare it with the HLBM step")
+                    help="only the surrogate leg: train the K=16 conv surrogate on HLBM rollouts and compare "
+                         "it with the HLBM step")
     ap.add_argument("--sur-samples", type=int, default=2000)
-    ap.add_argument("--sur-epochs", type=int, default=20)
+    ap.add_argument("--sur-epochs", type=int, default=30)
+    ap.add_argument("--sur-noise", type=float, default=0.1,
+                    help="standard deviation of the Gaussian noise added to the normalised training inputs")
+    ap.add_argument("--sur-pushforward", type=float, default=0.0,
+                    help="fraction of training inputs replaced by the network's own prediction from the previous "
+                         "snapshot (second half of the epochs)")
+    ap.add_argument("--sur-tol", type=float, default=1.0,
+                    help="judged-error tolerance of the hybrid rollout (max-abs, normalised fields)")
     ap.add_argument("--batched", action="store_true",
-                    help="the 64-case batched vortex sweep (one persistent launch per step) "
-                         "against the same cases run one after another")
+                    help="only the batched leg: the 64-case batched vortex sweep (one persistent launch per "
+                         "step) against the same cases run one after another")
+    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--no-batched", action="store_true", help="leave the batched leg out of the default line")
+    ap.add_argument("--no-surrogate", action="store_true", help="leave the surrogate leg out of the default line")
     return ap.parse_args()
 
 
@@ -277,22 +296,19 @@ def run_reference(args):
     case = workload(args.n)
     from oracle.oracle import Oracle, max_threads
     threads = max_threads()
-    rows = min(16 * threads, case.ny)  # 16 rows per thread
-    sl = slice(case.ny // 2 - rows // 2, case.ny // 2 - rows // 2 + rows)
-    f = [np.ascontiguousarray(a[sl]) for a in case.fields()]
-    o = Oracle(case.nx, rows, **case.params())
+    o = Oracle(case.nx, case.ny, **case.params())
     o.set_threads(threads)
-    o.init(*f)
+    o.init(*case.fields())
     for _ in range(args.warmup):
         o.step(1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         o.step(1)
     dt = time.perf_counter() - t0
-    cells = case.nx * rows
+    cells = case.nx * case.ny
     v = cells * args.steps / dt / 1e6
-    sample = (f"{rows}-row periodic strip ({case.nx}x{rows}) through the vortex centre, one time step per bench step, "
-              f"rows split over {threads} threads")
+    sample = (f"the full {case.nx}x{case.ny} workload, one time step per bench step, rows of each per-cell pass "
+              f"split over {threads} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
@@ -332,6 +348,8 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     s = hlbm.Solver(case.nx, case.ny, stream=stream.cuda_stream, precision=prec, **case.params())
     s.init(*case.fields())
+    # the FP64 pipe's rate, for the FP64 form's roofline (outside the timed region)
+    fp64_fma_rate = hlbm.hlbm_selftest_fp64_rate(stream=stream.cuda_stream) if args.precision == "fp64" else None
 
     flush_w = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     flush_r = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
@@ -340,6 +358,9 @@ def run_ours(args):
         flush_w.zero_()
         flush_r.sum()
 
+    # clocks are sampled from the first warm-up step to the end of the last
+    # GPU leg (the timed steps alone are shorter than the sampling period)
+    clk = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         flush()
         s.step(1)
@@ -347,13 +368,12 @@ def run_ours(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier(ws)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for a, b in ev:
-            flush()
-            a.record(stream)
-            s.step(1)
-            b.record(stream)
-        torch.cuda.synchronize()
+    for a, b in ev:
+        flush()
+        a.record(stream)
+        s.step(1)
+        b.record(stream)
+    torch.cuda.synchronize()
     barrier(ws)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     own_s = sum(step_ms) / 1e3
@@ -373,23 +393,40 @@ def run_ours(args):
     if d[7] != 0:
         raise RuntimeError("non-finite state after the timed steps")
 
-    # end to end through the C ABI with pinned host buffers: init from host,
-    # e2e_inner steps, read rho, u, theta back to host
+    # end to end through the C ABI with pinned host buffers: every e2e step
+    # initialises the state from the host fields, advances it by one time
+    # step and reads rho, u, theta back to the host (so the copies are per
+    # step); the same with 100 time steps per call is reported beside it
     pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case.fields()]
     outs = [torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
-    e2e_iters = 3
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_iters):
-        hlbm.hlbm_init_fields(s.h, *pin, n=cells)
-        s.step(args.e2e_inner)
-        hlbm.hlbm_get_macros(s.h, rho=outs[0], ux=outs[1], uy=outs[2], theta=outs[3], n=cells)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": job_throughput(cells * args.e2e_inner * e2e_iters, e2e_s, ws) / 1e6, "unit": UNIT,
-           "h2d_bytes_per_step": 4 * 8 * cells, "d2h_bytes_per_step": 4 * 8 * cells,
-           "steps_per_call": args.e2e_inner,
-           "note": "one e2e step = hlbm_init_fields(host) + hlbm_step(e2e_inner) + hlbm_get_macros(host)"}
+
+    def e2e_leg(inner, iters):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            hlbm.hlbm_init_fields(s.h, *pin, n=cells)
+            s.step(inner)
+            hlbm.hlbm_get_macros(s.h, rho=outs[0], ux=outs[1], uy=outs[2], theta=outs[3], n=cells)
+        return job_throughput(cells * inner * iters, time.perf_counter() - t0, ws) / 1e6
+
+    e2e_leg(1, 2)
+    copy_bytes = 4 * 8 * cells
+    e2e = {"value": e2e_leg(1, max(args.steps, 3)), "unit": UNIT, "h2d_bytes_per_step": copy_bytes,
+           "d2h_bytes_per_step": copy_bytes, "steps_per_call": 1,
+           "note": "one e2e step = hlbm_init_fields(pinned host rho, u_x, u_y, theta) + hlbm_step(1) + "
+                   "hlbm_get_macros(pinned host rho, u_x, u_y, theta)",
+           "amortised": {"value": e2e_leg(args.e2e_inner, 3), "unit": UNIT, "steps_per_call": args.e2e_inner,
+                         "h2d_bytes_per_step": copy_bytes / args.e2e_inner,
+                         "d2h_bytes_per_step": copy_bytes / args.e2e_inner}}
     s.close()
+    del flush_w, flush_r
+
+    batched = surr = None
+    if ws == 1 and not args.no_batched:
+        batched = batched_leg(args, stream, cpu=not args.no_cpu_baseline)
+    if ws == 1 and not args.no_surrogate:
+        surr = surrogate_leg(args, stream)
+    clk.__exit__(None, None, None)
 
     if rank != 0:
         if ws > 1:
@@ -412,14 +449,16 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": bpc * cells}
     else:
         # FP64 is bound by GB300's FP64 pipe: FP64 operations (add, mul, 2 per
-        # fma) executed per cell-update, counted by ncu, against the nominal
-        # FP64 rate (no measured FP64 peak is available)
+        # fma) executed per cell-update, counted by ncu, against this GPU's
+        # FP64 rate measured in the same run by the library's FMA-chain probe
         fpc = profiled_fp64_flops(args.n)
         tf = None if fpc is None else fpc * cells / mean_launch_s / 1e12
-        roof = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": None if tf is None else tf / FP64_NOMINAL_TFLOPS,
+        peak = 2.0 * fp64_fma_rate / 1e12
+        roof = {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                "frac": None if tf is None else tf / peak,
                 "traffic": profiled_traffic(args.precision, args.n),
-                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s; no measured FP64 peak)",
+                "peak_source": "measured in this run: hlbm_selftest_fp64_rate, FP64 FMA chains on every SM "
+                               f"(nominal {FP64_NOMINAL_TFLOPS} TFLOP/s)",
                 "fp64_flops_per_cell": fpc, "hbm_gbs_achieved": achieved,
                 "kernel": kernel_name(args.precision, cells, case.sigma, case.phi_mode),
                 "algorithmic_bytes_per_launch": bpc * cells}
@@ -447,6 +486,10 @@ def run_ours(args):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
         "gpu_launches": args.steps,
     }
+    if batched is not None:
+        line["batched"] = batched
+    if surr is not None:
+        line["surrogate"] = surr
     print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -454,27 +497,37 @@ def run_ours(args):
     return 0
 
 
-def run_batched(args):
-    """64 vortex cases of uneven size (128^2 .. 1024^2), Mach and gamma,
-    advanced together: autotuned work shape, CUDA-graph replay.  Against the
-    same cases stepped one after another with the default single-case
-    kernel; the field difference between the two is measured."""
+def field_errors(got, ref, gamma):
+    """max |got - ref| per field over the parity tests' field scales (rho:
+    max rho; u: max |u| + max sound speed; theta: max theta; a1: max p), and
+    a1 at its own scale (max |a1_ref|)."""
+    c = np.sqrt(gamma * np.abs(ref["theta"]) / 3.0).max()
+    um = np.sqrt(ref["ux"] ** 2 + ref["uy"] ** 2).max()
+    sc = {"rho": np.abs(ref["rho"]).max(), "ux": um + c, "uy": um + c, "theta": np.abs(ref["theta"]).max(),
+          "s": np.abs(ref["s"]).max(), "a1": (ref["rho"] * ref["theta"] / 3.0).max()}
+    e = {k: float(np.abs(got[k] - ref[k]).max() / sc[k]) for k in sc}
+    e["a1_own"] = float(np.abs(got["a1"] - ref["a1"]).max() / max(np.abs(ref["a1"]).max(), 1e-300))
+    return e
+
+
+def batched_leg(args, stream, cpu=True, ncmp=4):
+    """The 64-case vortex sweep (128^2 .. 1024^2, Mach 0.1-1.5, three gammas)
+    advanced together (autotuned work shape, CUDA-graph replay), against the
+    same cases stepped one after another by the default single-case kernel.
+    With cpu, the FP64 oracle runs the `ncmp` smallest cases over the same
+    steps on the host cores (timed: the leg's CPU baseline) and both GPU
+    forms are compared with it field by field."""
     import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__ as g
-    g.build()
     from paper_2002_03644_gb300 import hlbm, inputs
     cases = inputs.batch_sweep()
-    steps = args.steps
+    steps, warm = args.batched_steps, max(args.warmup, 3)
     cells = sum(c.nx * c.ny for c in cases)
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
     spec = [dict(nx=c.nx, ny=c.ny, precision=hlbm.HLBM_FP32, **c.params()) for c in cases]
     b = hlbm.Batch(spec, stream=stream.cuda_stream)
     for v, c in zip(b.cases, cases):
         v.init(*c.fields())
     tile = b.autotune()
-    b.step(args.warmup)
+    b.step(warm)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -483,18 +536,17 @@ def run_batched(args):
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1) / 1e3
     bad = sum(int(v.diagnostics()[7]) for v in b.cases)
+    order = sorted(range(len(cases)), key=lambda i: (cases[i].nx * cases[i].ny, i))
+    cmp_idx = order[:ncmp]
+    final_b = {i: b.cases[i].macros() for i in cmp_idx}
     fields = ("rho", "ux", "uy", "theta")
-    final_b = [{k: m[k].astype(np.float32) for k in fields} for m in (v.macros() for v in b.cases)]
+    all_b = [{k: m[k].astype(np.float32) for k in fields} for m in (v.macros() for v in b.cases)]
     b.close()
-    # the same cases, one handle at a time on the same stream, each with the
-    # library's default single-case kernel; the field difference is measured
-    # (max |batch - separate| over max |field|, all cases and fields)
-    t_sep = 0.0
-    err = 0.0
-    for c, fb in zip(cases, final_b):
+    t_sep, err_sep, final_s = 0.0, 0.0, {}
+    for i, (c, fb) in enumerate(zip(cases, all_b)):
         s = hlbm.Solver(c.nx, c.ny, stream=stream.cuda_stream, precision=hlbm.HLBM_FP32, **c.params())
         s.init(*c.fields())
-        s.step(args.warmup)
+        s.step(warm)
         torch.cuda.synchronize()
         e0.record(stream)
         s.step(steps)
@@ -502,44 +554,76 @@ def run_batched(args):
         torch.cuda.synchronize()
         t_sep += e0.elapsed_time(e1) / 1e3
         m = s.macros()
+        if i in cmp_idx:
+            final_s[i] = m
         for k in fields:
-            err = max(err, float(np.abs(m[k] - fb[k]).max() / max(np.abs(m[k]).max(), 1e-30)))
+            err_sep = max(err_sep, float(np.abs(m[k] - fb[k]).max() / max(np.abs(m[k]).max(), 1e-30)))
         s.close()
     v_batch = cells * steps / t_batch / 1e6
     v_sep = cells * steps / t_sep / 1e6
-    line = {"metric": "MLUPS (batched 64-case vortex sweep)", "value": v_batch, "unit": UNIT, "n_gpus": 1,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": t_batch / steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "64 vortex cases, N from {128,256,512,1024}, Ma U[0.1,1.5], gamma from "
-                                   "{1.4,1.3,1.67}, CFL 0.7, seed 2002", "cells": cells,
-                       "sizes": sorted({c.nx for c in cases}), "autotuned_tile_index": tile},
-            "separate_runs_mlups": v_sep, "speedup_vs_separate": v_batch / v_sep,
-            "field_error_vs_separate": err,
-            "field_error_note": "max |batch - separate| / max |field| over rho, u_x, u_y, theta of all cases after the "
-                                "run, separate runs on the default single-case kernel (float32 read-back); zero when "
-                                "both use the same kernel",
-            "nonfinite_cells": bad}
-    print(json.dumps(line))
-    return 0
+    out = {"metric": "MLUPS (batched 64-case vortex sweep)", "value": v_batch, "unit": UNIT,
+           "steps": steps, "warmup": warm, "ms_per_step": t_batch / steps * 1e3,
+           "workload": "64 vortex cases, N from {128,256,512,1024}, Ma U[0.1,1.5], gamma from {1.4,1.3,1.67}, "
+                       "CFL 0.7, seed 2002, FP32", "cells": cells, "autotuned_tile_index": tile,
+           "separate_runs_mlups": v_sep, "speedup_vs_separate": v_batch / v_sep,
+           "batch_vs_separate_max_rel": err_sep, "nonfinite_cells": bad,
+           "l2": "state (29.9 M cells, 3.1 GB) larger than L2"}
+    if cpu:
+        from oracle.oracle import Oracle, max_threads
+        threads = max_threads()
+        errs_b, errs_s, work, t_cpu = [], [], 0, 0.0
+        for i in cmp_idx:
+            c = cases[i]
+            o = Oracle(c.nx, c.ny, **c.params())
+            o.set_threads(threads)
+            o.init(*c.fields())
+            t0 = time.perf_counter()
+            o.step(warm + steps)
+            t_cpu += time.perf_counter() - t0
+            work += c.nx * c.ny * (warm + steps)
+            ref = o.macros()
+            errs_b.append(field_errors(final_b[i], ref, c.gamma))
+            errs_s.append(field_errors(final_s[i], ref, c.gamma))
+
+        def worst(es):
+            return {k: max(e[k] for e in es) for k in es[0]}
+        out["field_error_vs_oracle"] = {
+            "batched": worst(errs_b), "separate": worst(errs_s), "bound": 1e-4,
+            "cases": [cases[i].name for i in cmp_idx], "steps": warm + steps,
+            "note": "max |GPU - FP64 oracle| over the parity tests' field scales after the leg's steps; a1_own: "
+                    "a1 over max |a1_oracle|"}
+        out["cpu_baseline"] = {"value": work / t_cpu / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"FP64 oracle on the {ncmp} smallest cases of the sweep, "
+                                         f"{warm + steps} time steps each ({t_cpu:.1f} s)"}
+    return out
 
 
-def run_surrogate(args):
-    """Learned K = 16 surrogate: 6 periodic 3x3 conv layers (4 -> 64 x 5 -> 4,
-    GELU), BF16 operands with FP32 accumulation, trained by the library's own
-    kernels on HLBM snapshot pairs of 256^2 random-Fourier fields (8 lowest
-    modes, amplitude 0.05, Mach 0.3-1.2).  Reports training throughput, the
-    held-out error, and the time of one surrogate call against 16 HLBM
-    steps on the same grid."""
+def run_batched(args):
+    """The batched leg alone, as its own JSON line."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__ as g
     g.build()
-    from paper_2002_03644_gb300 import hlbm, inputs, surrogate
-    n, K, batch = 256, 16, 16
-    # one dedicated stream for the solver, the surrogate and the events
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    out = batched_leg(args, stream, cpu=not args.no_cpu_baseline)
+    out.update(n_gpus=1, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic")
+    print(json.dumps(out))
+    return 0
+
+
+def surrogate_leg(args, stream):
+    """Learned K = 16 surrogate: 6 periodic 3x3 conv layers (4 -> 64 x 5 -> 4,
+    GELU), BF16 operands with FP32 accumulation, trained by the library's own
+    kernels on HLBM snapshot pairs of 256^2 random-Fourier fields (8 lowest
+    modes, amplitude 0.05, Mach 0.3-1.2).  Reports training throughput, the
+    held-out error, the time of one surrogate call against 16 HLBM steps on
+    the same grid, and a hybrid rollout of held-out initial states (the HLBM
+    judging every 8th call, falling back above the tolerance) against the
+    plain FP32 HLBM over the same steps."""
+    import torch
+    from paper_2002_03644_gb300 import hlbm, inputs, surrogate
+    n, K, batch, judge_every, calls = 256, 16, 16, 8, 16
     sh = stream.cuda_stream
     t0 = time.perf_counter()
     X, Y = surrogate.make_dataset_device(args.sur_samples, n=n, K=K, pairs_per_run=4, seed=2002, stream=sh)
@@ -551,23 +635,23 @@ def run_surrogate(args):
     del X, Y
     widths = (4, 64, 64, 64, 64, 64, 4)
     sur = surrogate.Surrogate(widths, n, n, batch_max=batch, seed=0, stream=sh)
-    # FLOPs per sample of one forward pass (multiply-add = 2)
     fwd_flops = sum(2 * 9 * a * b * n * n for a, b in zip(widths[:-1], widths[1:]))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = sur.fit(Xn[:ntrain], Yn[:ntrain], epochs=args.sur_epochs, batch=batch, lr=1e-3)
+    hist = sur.fit(Xn[:ntrain], Yn[:ntrain], epochs=args.sur_epochs, batch=batch, lr=2e-3, lr_final=5e-5,
+                   noise=args.sur_noise, pushforward=args.sur_pushforward, pairs_per_run=4)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     samples = args.sur_epochs * ntrain
-    # held-out error (normalised fields) of the surrogate and of y = x
     errs, errs_id, mse, mse_id = [], [], [], []
     for b0 in range(ntrain, Xn.shape[0] - batch + 1, batch):
         pred = sur.predict(Xn[b0:b0 + batch].contiguous())
         d, d0 = pred - Yn[b0:b0 + batch], Xn[b0:b0 + batch] - Yn[b0:b0 + batch]
         errs.append(float(d.abs().max())); errs_id.append(float(d0.abs().max()))
         mse.append(float((d * d).mean())); mse_id.append(float((d0 * d0).mean()))
-    # inference time per sample (batch of 16) vs 16 HLBM steps per sample
-    x = Xn[:batch].contiguous()
+    del Xn, Yn
+    # one call per sample (batch of 16) against 16 FP32 HLBM steps per sample
+    x = torch.from_numpy(np.random.default_rng(1).normal(size=(batch, n, n, 4)).astype(np.float32)).cuda()
     y = torch.empty_like(x)
     for _ in range(3):
         sur.predict(x, y)
@@ -581,33 +665,97 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     sur.synchronize()  # raises if a tensor-core kernel reported a timeout
     t_sur = e0.elapsed_time(e1) / 1e3 / (reps * batch)
-    case = inputs.random_fourier(n=n, seed=1)
-    s = hlbm.Solver(n, n, stream=sh, precision=hlbm.HLBM_FP32, **case.params())
-    s.init(*case.fields())
+    held = [inputs.random_fourier(n=n, seed=10 ** 6 + k) for k in range(batch)]
+    s = hlbm.Solver(n, n, stream=sh, precision=hlbm.HLBM_FP32, **held[0].params())
+    s.init(*held[0].fields())
     s.step(K)
     s.synchronize()
-    t0 = time.perf_counter()
-    reps_h = 50
-    s.step(K * reps_h)
-    s.synchronize()
-    t_hlbm = (time.perf_counter() - t0) / reps_h
+    e0.record(stream)
+    s.step(K * 50)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_hlbm = e0.elapsed_time(e1) / 1e3 / 50
     s.close()
+    # hybrid rollout of 16 held-out states over calls * K steps, end to end
+    # through the library's API (device buffers), against the plain FP32 HLBM
+    x0 = torch.stack([torch.from_numpy(np.stack(c.fields(), axis=-1)) for c in held]).float().cuda()
+    judge = surrogate.FieldJudge(n, held[0].params(), stream=sh)
+    surrogate.hybrid_rollout_device(sur, norm, judge, x0.clone(), calls=judge_every, K=K,
+                                    judge_every=judge_every, tol=args.sur_tol)  # warm-up
+    plain = torch.empty_like(x0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for bi in range(batch):
+        judge.advance(x0[bi], calls * K, plain[bi])
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+
+    def hybrid(tol):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, lg = surrogate.hybrid_rollout_device(sur, norm, judge, x0.clone(), calls=calls, K=K,
+                                                 judge_every=judge_every, tol=tol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        d = norm.fwd(st) - norm.fwd(plain)
+        return st, lg, dt, d
+
+    st_h, log, t_hyb, dn = hybrid(args.sur_tol)
+    sweep = []
+    for tol in (0.5, 1.0, 2.0, 4.0, 8.0, None):
+        _, lg, dt, d = hybrid(tol)
+        sweep.append({"tolerance": tol, "accepted": sum(1 for *_, b in lg if not b), "judged": len(lg),
+                      "final_error_vs_plain_hlbm_max": float(d.abs().max()),
+                      "final_error_vs_plain_hlbm_rms": float(d.pow(2).mean().sqrt()),
+                      "speedup_vs_plain_hlbm": t_plain / dt})
+    judge.close()
     sur.close()
-    line = {"metric": "surrogate K=16 call vs 16 HLBM steps (256^2)", "value": t_hlbm / t_sur, "unit": "x",
-            "higher_is_better": True, "n_gpus": 1, "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
-            "config": {"workload": "256^2 periodic random-Fourier fields (8 lowest modes, amplitude 0.05, Mach "
-                                   "0.3-1.2), K = 16, net 4-64x5-4 3x3 periodic conv, GELU",
-                       "samples": int(Xn.shape[0]), "train": ntrain, "epochs": args.sur_epochs, "batch": batch},
-            "surrogate_s_per_sample": t_sur, "hlbm_s_per_16_steps": t_hlbm,
-            "train_samples_per_s": samples / t_train,
-            "train_tflops": 3 * fwd_flops * samples / t_train / 1e12,
-            "data_generation_s": t_data, "loss_first_last": [hist[0], hist[-1]],
-            "heldout_mse_normalised": float(np.mean(mse)) if mse else None,
-            "heldout_mse_identity": float(np.mean(mse_id)) if mse_id else None,
-            "heldout_maxabs_err_normalised": max(errs) if errs else None,
-            "heldout_maxabs_err_identity": max(errs_id) if errs_id else None,
-            "field_error_bound_note": "errors in units of the per-channel standard deviation of the inputs"}
-    print(json.dumps(line))
+    jerr = [e for _, _, e, _ in log if math.isfinite(e)]
+    return {
+        "metric": "surrogate K=16 call vs 16 HLBM steps (256^2)", "value": t_hlbm / t_sur, "unit": "x",
+        "dtype": "bf16 operands, f32 accumulate",
+        "workload": "256^2 periodic random-Fourier fields (8 lowest modes, amplitude 0.05, Mach 0.3-1.2), K = 16, "
+                    "net 4-64x5-4 3x3 periodic conv, GELU",
+        "samples": int(args.sur_samples), "train": ntrain, "epochs": args.sur_epochs, "batch": batch,
+        "input_noise": args.sur_noise, "pushforward": args.sur_pushforward,
+        "surrogate_s_per_sample": t_sur, "hlbm_s_per_16_steps": t_hlbm,
+        "train_samples_per_s": samples / t_train, "train_tflops": 3 * fwd_flops * samples / t_train / 1e12,
+        "data_generation_s": t_data, "loss_first_last": [hist[0], hist[-1]],
+        "heldout_mse_normalised": float(np.mean(mse)) if mse else None,
+        "heldout_mse_identity": float(np.mean(mse_id)) if mse_id else None,
+        "heldout_maxabs_err_normalised": max(errs) if errs else None,
+        "heldout_maxabs_err_identity": max(errs_id) if errs_id else None,
+        "hybrid_rollout": {
+            "samples": batch, "calls": calls, "steps": calls * K, "judge_every": judge_every,
+            "tolerance": args.sur_tol, "judged": len(log), "accepted": sum(1 for *_, b in log if not b),
+            "judged_nonfinite": len(log) - len(jerr),
+            "judged_error_mean": float(np.mean(jerr)) if jerr else None,
+            "judged_error_median": float(np.median(jerr)) if jerr else None,
+            "judged_error_max": float(np.max(jerr)) if jerr else None,
+            "final_error_vs_plain_hlbm_max": float(dn.abs().max()),
+            "final_error_vs_plain_hlbm_rms": float(dn.pow(2).mean().sqrt()),
+            "seconds": t_hyb, "plain_hlbm_seconds": t_plain, "speedup_vs_plain_hlbm": t_plain / t_hyb,
+            "tolerance_sweep": sweep,
+            "note": "both legs through the library's API with device buffers: per sample, the plain leg "
+                    "initialises the FP32 solver, advances calls*K steps and reads the fields back; the hybrid "
+                    "runs the surrogate on all samples per call and the judge (the same solver, K steps) every "
+                    "judge_every-th call; a rejected sample is re-run by the solver over its whole window. "
+                    "Errors: max-abs of the normalised fields (judged: one call against the judge; final: the "
+                    "hybrid's state after all calls against the plain HLBM's)"},
+        "field_error_bound_note": "errors in units of the per-channel standard deviation of the training inputs"}
+
+
+def run_surrogate(args):
+    """The surrogate leg alone, as its own JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = surrogate_leg(args, stream)
+    out.update(n_gpus=1, higher_is_better=True, data="synthetic")
+    print(json.dumps(out))
     return 0
 
 

@@ -244,19 +244,19 @@ def random_smooth(nx, ny, seed=7, amp=0.05, modes=4, rho0=1.0, theta0=0.2, u0=(0
     """Sum of seeded random Fourier modes (the lowest `modes` wavenumbers per
     axis) on rho, u_x, u_y and theta around a mean state.  Periodic in both
     directions by construction."""
-    X, Y = _grid(nx, ny)
     out = []
     r = uniform01(seed, 4 * modes * modes * 3).reshape(4, modes, modes, 3)
+    # sum over (kx, ky) of a cos(2 pi (kx x / nx + ky y / ny) + ph) at the cell
+    # centres, evaluated as Re(E_y C E_x) with C[ky, kx] = a exp(i ph)
+    k = np.arange(modes)
+    ex = np.exp(2j * math.pi * np.outer(k, np.arange(nx) + 0.5) / nx)  # [kx, x]
+    ey = np.exp(2j * math.pi * np.outer(np.arange(ny) + 0.5, k) / ny)  # [y, ky]
+    KX, KY = np.meshgrid(k, k, indexing="ij")
     for f in range(4):
-        acc = np.zeros((ny, nx))
-        for kx in range(modes):
-            for ky in range(modes):
-                if kx == 0 and ky == 0:
-                    continue
-                a = (2.0 * r[f, kx, ky, 0] - 1.0) / (1.0 + kx * kx + ky * ky)
-                ph = 2.0 * math.pi * r[f, kx, ky, 1]
-                acc += a * np.cos(2.0 * math.pi * (kx * X / nx + ky * Y / ny) + ph)
-        out.append(amp * acc)
+        a = (2.0 * r[f, :, :, 0] - 1.0) / (1.0 + KX * KX + KY * KY)  # [kx, ky]
+        a[0, 0] = 0.0
+        c = (a * np.exp(2j * math.pi * r[f, :, :, 1])).T  # [ky, kx]
+        out.append(amp * np.real(ey @ c @ ex))
     rho = rho0 * (1.0 + out[0])
     ux = u0[0] + out[1]
     uy = u0[1] + out[2]

@@ -197,19 +197,45 @@ class Surrogate:
         hlbm.hlbm_sur_adam(self.s, lr)
         return loss
 
-    def fit(self, X, Y, epochs=10, batch=8, lr=1e-3, seed=0, log=None):
-        """X, Y: CUDA float32 [N, H, W, C] (normalised).  Returns the mean
-        loss of every epoch."""
+    def fit(self, X, Y, epochs=10, batch=8, lr=1e-3, seed=0, log=None, lr_final=None, noise=0.0,
+            pushforward=0.0, pairs_per_run=None):
+        """X, Y: CUDA float32 [N, H, W, C] (normalised).  The learning rate
+        goes from `lr` to `lr_final` (default: stays at lr) along a cosine
+        over the epochs.  With noise > 0 every input batch gets seeded
+        Gaussian noise of that standard deviation (the target stays the
+        solver's result), so that the network learns to advance states that
+        carry its own earlier errors, as in a rollout.  With pushforward > 0
+        (and X, Y holding runs of `pairs_per_run` consecutive pairs, X[i] =
+        Y[i - 1] inside a run), in the second half of the epochs that
+        fraction of the samples that have a predecessor take as input the
+        network's own prediction from the predecessor instead of the solver's
+        state, with the solver's next state as the target: the network is
+        trained on the states its rollouts reach.  Returns the mean loss of
+        every epoch."""
         import torch
         rng = np.random.default_rng(seed)
+        gen = torch.Generator(device=X.device)
+        gen.manual_seed(int(seed) + 1)
         hist = []
         N = X.shape[0]
         for ep in range(epochs):
             order = rng.permutation(N)
             tot, cnt = 0.0, 0
+            lr_ep = lr
+            if lr_final is not None and epochs > 1:
+                lr_ep = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * ep / (epochs - 1)))
             for b0 in range(0, N - batch + 1, batch):
-                idx = torch.as_tensor(order[b0:b0 + batch], device=X.device)
-                tot += self.train_step(X[idx].contiguous(), Y[idx].contiguous(), lr)
+                sel = order[b0:b0 + batch]
+                idx = torch.as_tensor(sel, device=X.device)
+                xb = X[idx].contiguous()
+                if pushforward > 0.0 and pairs_per_run and 2 * ep >= epochs:
+                    pick = np.flatnonzero((sel % pairs_per_run != 0) & (rng.random(len(sel)) < pushforward))
+                    if pick.size:
+                        prev = torch.as_tensor(sel[pick] - 1, device=X.device)
+                        xb[torch.as_tensor(pick, device=X.device)] = self.predict(X[prev].contiguous())
+                if noise > 0.0:
+                    xb = xb + noise * torch.randn(xb.shape, device=X.device, generator=gen)
+                tot += self.train_step(xb, Y[idx].contiguous(), lr_ep)
                 cnt += 1
             self.synchronize()
             hist.append(tot / max(cnt, 1))
@@ -243,6 +269,69 @@ def hybrid_rollout(sur, norm, case, calls, K=16, judge_every=8, tol=None, stream
             state = ref if back else y
         else:
             state = y
+    return state, log
+
+
+class FieldJudge:
+    """The HLBM as the surrogate's judge: one FP32 solver handle (the cases
+    of a rollout share their parameters) that advances a device state
+    [H, W, 4] (rho, u_x, u_y, theta, float32) by K time steps, with device
+    buffers only (no host copies)."""
+
+    def __init__(self, n, params, stream=None):
+        import torch
+        self.n = n
+        self.solver = hlbm.Solver(n, n, stream=stream, precision=hlbm.HLBM_FP32, **params)
+        self.f64 = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(4)]
+
+    def advance(self, state, K, out):
+        """out[...] = the state K steps after `state` (both [H, W, 4] float32
+        CUDA tensors); a1 starts from its finite-difference form, the
+        initialisation of Sec. 3.5."""
+        for q in range(4):
+            self.f64[q].copy_(state[..., q])
+        self.solver.init(*self.f64)
+        self.solver.step(K)
+        n2 = self.n * self.n
+        hlbm.hlbm_get_macros(self.solver.h, rho=self.f64[0], ux=self.f64[1], uy=self.f64[2],
+                             theta=self.f64[3], n=n2)
+        for q in range(4):
+            out[..., q] = self.f64[q]
+        return out
+
+    def close(self):
+        self.solver.close()
+
+
+def hybrid_rollout_device(sur, norm, judge, state, calls, K=16, judge_every=8, tol=None):
+    """Advance a batch of states [B, H, W, 4] (float32, CUDA, physical
+    fields) by calls * K time steps with the surrogate, the HLBM judging every
+    `judge_every`-th call.  The judge re-runs that call's K steps from the
+    same states; the judged error of a state is the max-abs difference of the
+    normalised fields.  A state whose error is finite and within `tol` (any
+    finite error when tol is None) continues from the surrogate's result.
+    Any other state -- drifted, or broken by the unjudged calls before it --
+    is advanced again by the HLBM over the whole window since the previous
+    judged call, from its state there (the fallback), so that no rejected
+    window carries on.  `norm` is a DeviceNormaliser.  Returns (state, log)
+    with log entries (call, sample, error, fell_back)."""
+    import torch
+    B = state.shape[0]
+    log = []
+    ckpt, ckpt_call = state.clone(), 0
+    ref = torch.empty_like(state[0])
+    for k in range(calls):
+        prev = state
+        state = norm.inv(sur.predict(norm.fwd(state).contiguous()))
+        if (k + 1) % judge_every == 0:
+            for b in range(B):
+                judge.advance(prev[b], K, ref)
+                err = float((norm.fwd(state[b]) - norm.fwd(ref)).abs().max())
+                ok = math.isfinite(err) and (tol is None or err <= tol)
+                if not ok:
+                    judge.advance(ckpt[b], (k + 1 - ckpt_call) * K, state[b])
+                log.append((k, b, err, not ok))
+            ckpt, ckpt_call = state.clone(), k + 1
     return state, log
 
 
