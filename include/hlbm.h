@@ -324,6 +324,35 @@ int hlbm_diagnostics_noalloc(const void *state, int precision, int nx, int ny, i
  * involved, and the device stays usable whatever the outcome. */
 int hlbm_selftest_wait(void *stream, long long budget_cycles, int arrive);
 
+/* ---- index checks of the debug build ---------------------------------------
+ * A debugging aid, not a method of the paper.  The library built with
+ * HLBM_DEBUG (libhlbm_debug.so, see paper_2002_03644_gb300/build.py) checks
+ * in the marching, moment-state and tiled step kernels the cell of every
+ * global load and store against the grid (the partner column of 2-element
+ * accesses too) and the ring slots of the marching kernel against the ring
+ * depths.  A failed check skips its access (a load reads zero) and the first
+ * one is recorded; no kernel traps.  This call waits for the whole device,
+ * then reads and clears the record: *site = 0 when every check passed, else
+ * the site (1-3 marching loads of F, s, a1; 4 marching store; 5 ring slot; 6
+ * phase-2 pair; 10-12 tiled loads of s, F and tiled store; 21, 22 moment
+ * loads; 24 moment store) with two values of the failed check in *a, *b (row
+ * and column, or the value and its bound).  Any pointer may be NULL.  The
+ * release build returns HLBM_ERR_UNSUPPORTED. */
+int hlbm_debug_check(long long *site, long long *a, long long *b);
+
+/* ---- FP64 rate probe -------------------------------------------------------
+ * Measurement support, not a method of the paper: the FP64 form of the step
+ * is bound by the GPU's FP64 pipe, so its roofline needs that pipe's rate.
+ * Runs 8 independent FP64 fused multiply-add chains of `iters` steps in
+ * every thread of 8 CTAs of 256 threads per SM (after a warm-up launch of an
+ * eighth of the length), timed with CUDA events on `stream` (a
+ * cudaStream_t; NULL for the legacy default stream), and writes the rate in
+ * fused multiply-adds per second (2 flops each) to *fma_per_s.  The call
+ * waits for its work.  HLBM_ERR_ARG for iters outside 1 .. 2^24 or a NULL
+ * out pointer; HLBM_ERR_CUDA on a CUDA error.  It allocates no device
+ * memory and changes no device setting. */
+int hlbm_selftest_fp64_rate(void *stream, int iters, double *fma_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "hlbm.h"
 #include "hlbm_device.cuh"
@@ -160,6 +161,16 @@ static int env_choice(const char *name, int dflt, int lo, int hi)
     const int v = atoi(e);
     return (v >= lo && v < hi) ? v : dflt;
 }
+
+// A named NVTX range over one entry point's host work (what it enqueues and
+// any wait), visible in a profiler's timeline; without a tool attached a
+// range costs a function call.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 
 template <int TX, int TY, int NT>
@@ -633,9 +644,12 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         hlbm_destroy(h);
         return HLBM_ERR_NOMEM;
     }
-    // pad columns stay zero (never read as cells)
-    if (cudaMemsetAsync(h->state[0], 0, bytes, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->state[1], 0, bytes, h->stream) != cudaSuccess) {
+    // Every byte 0xFF: a NaN in each storage type (FP64, FP32, FP16, BF16).
+    // The pad columns of each row (pitch > nx) keep it for good -- no kernel
+    // writes them -- so a kernel that used a value it should never read
+    // would carry a NaN into the fields, where every parity test sees it.
+    if (cudaMemsetAsync(h->state[0], 0xFF, bytes, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->state[1], 0xFF, bytes, h->stream) != cudaSuccess) {
         hlbm_destroy(h);
         return HLBM_ERR_CUDA;
     }
@@ -711,6 +725,7 @@ static int run_diagnostics(hlbm_handle *h, double out[8])
 int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const double *uy, const double *theta,
                      const double *a1, int mem_kind)
 {
+    NvtxRange nvtx_range("hlbm_init_fields");
     if (!h) return HLBM_ERR_ARG;
     if (!rho || !ux || !uy || !theta) return fail(h, HLBM_ERR_ARG, "rho, ux, uy and theta are required");
     if (mem_kind != HLBM_MEM_HOST && mem_kind != HLBM_MEM_DEVICE) return fail(h, HLBM_ERR_ARG, "mem_kind");
@@ -774,8 +789,27 @@ int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const 
     return HLBM_OK;
 }
 
+int hlbm_debug_check(long long *site, long long *a, long long *b)
+{
+#ifdef HLBM_DEBUG
+    unsigned long long v = 0;
+    const unsigned long long zero = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpyFromSymbol(&v, dbg_first, sizeof(v)) != cudaSuccess ||
+        cudaMemcpyToSymbol(dbg_first, &zero, sizeof(zero)) != cudaSuccess)
+        return HLBM_ERR_CUDA;
+    if (site) *site = v ? (long long)((v >> 56) & 0x7F) : 0;
+    if (a) *a = (long long)((v >> 28) & 0xFFFFFFF);
+    if (b) *b = (long long)(v & 0xFFFFFFF);
+    return HLBM_OK;
+#else
+    (void)site; (void)a; (void)b;
+    return HLBM_ERR_UNSUPPORTED;
+#endif
+}
+
 int hlbm_step(hlbm_handle *h, int64_t n)
 {
+    NvtxRange nvtx_range("hlbm_step");
     if (!h) return HLBM_ERR_ARG;
     if (!h->initialized) return fail(h, HLBM_ERR_STATE, "hlbm_step before hlbm_init_fields");
     if (n < 0) return fail(h, HLBM_ERR_ARG, "n < 0");
@@ -801,6 +835,7 @@ int hlbm_step(hlbm_handle *h, int64_t n)
 static int extract(hlbm_handle *h, double *rho, double *ux, double *uy, double *theta, double *s, double *a1,
                    double *F, int mem_kind)
 {
+    NvtxRange nvtx_range("hlbm_get_fields");
     if (!h) return HLBM_ERR_ARG;
     if (!h->initialized) return fail(h, HLBM_ERR_STATE, "no state yet");
     if (mem_kind != HLBM_MEM_HOST && mem_kind != HLBM_MEM_DEVICE) return fail(h, HLBM_ERR_ARG, "mem_kind");
@@ -861,6 +896,7 @@ int hlbm_get_populations(hlbm_handle *h, double *F, int mem_kind)
 
 int hlbm_diagnostics(hlbm_handle *h, double out[8])
 {
+    NvtxRange nvtx_range("hlbm_diagnostics");
     if (!h || !out) return HLBM_ERR_ARG;
     if (!h->initialized) return fail(h, HLBM_ERR_STATE, "no state yet");
     CK(cudaSetDevice(h->device), "cudaSetDevice");
@@ -884,6 +920,7 @@ int hlbm_state_bytes(const hlbm_handle *h, size_t *bytes)
 
 int hlbm_get_state(hlbm_handle *h, void *buf, size_t bytes)
 {
+    NvtxRange nvtx_range("hlbm_get_state");
     if (!h || !buf) return HLBM_ERR_ARG;
     if (!h->initialized) return fail(h, HLBM_ERR_STATE, "no state yet");
     size_t need = 0;
@@ -906,6 +943,7 @@ int hlbm_get_state(hlbm_handle *h, void *buf, size_t bytes)
 
 int hlbm_set_state(hlbm_handle *h, const void *buf, size_t bytes)
 {
+    NvtxRange nvtx_range("hlbm_set_state");
     if (!h || !buf) return HLBM_ERR_ARG;
     size_t need = 0;
     hlbm_state_bytes(h, &need);
@@ -1226,6 +1264,7 @@ int hlbm_batch_case(hlbm_batch *b, int index, hlbm_handle **h)
 
 int hlbm_batch_step(hlbm_batch *b, int64_t n)
 {
+    NvtxRange nvtx_range("hlbm_batch_step");
     if (!b || n < 0) return HLBM_ERR_ARG;
     if (cudaSetDevice(b->device) != cudaSuccess) return HLBM_ERR_CUDA;
     return batch_advance(b, n);
@@ -1244,6 +1283,7 @@ int hlbm_batch_tile(const hlbm_batch *b, int *index, int *tx, int *ty, int *thre
 
 int hlbm_batch_autotune(hlbm_batch *b, int *tile)
 {
+    NvtxRange nvtx_range("hlbm_batch_autotune");
     if (!b) return HLBM_ERR_ARG;
     if (cudaSetDevice(b->device) != cudaSuccess) return HLBM_ERR_CUDA;
     if (batch_parity(b) < 0) return HLBM_ERR_STATE;

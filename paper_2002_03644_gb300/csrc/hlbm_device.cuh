@@ -61,6 +61,42 @@
 
 namespace hlbm {
 
+// ---- index checks of the debug build (HLBM_DEBUG) --------------------------------
+// Built with -DHLBM_DEBUG, the marching and tiled kernels check the cell of
+// every global access against the grid (and the vector accesses' partner
+// column) and their ring slots against the ring depths.  The first failing
+// check records (site, first value, second value) in dbg_first and the
+// access is skipped (a load gives zero); no kernel traps.  hlbm_debug_check
+// reads and clears the record.  In the release build every check is the
+// constant true and costs nothing.
+#ifdef HLBM_DEBUG
+static __device__ unsigned long long dbg_first;  // 0: no failed check
+__device__ __noinline__ void dbg_record(int site, long long a, long long b)
+{
+    const unsigned long long v = ((unsigned long long)(site & 0xFF) << 56) |
+                                 ((unsigned long long)(a & 0xFFFFFFF) << 28) | (unsigned long long)(b & 0xFFFFFFF);
+    atomicCAS(&dbg_first, 0ull, v | (1ull << 63));
+}
+// (row, col) inside the grid, and col + width - 1 too
+__device__ __forceinline__ bool dbg_cell(int row, int col, int width, int nx, int ny, int site)
+{
+    if (row >= 0 && row < ny && col >= 0 && col + width - 1 < nx) return true;
+    dbg_record(site, row, col);
+    return false;
+}
+__device__ __forceinline__ bool dbg_range(long long v, long long n, int site)
+{
+    if (v >= 0 && v < n) return true;
+    dbg_record(site, v, n);
+    return false;
+}
+#define HLBM_CELL_OK(row, col, width, kp, site) ::hlbm::dbg_cell((row), (col), (width), (kp).nx, (kp).ny, (site))
+#define HLBM_RANGE_OK(v, n, site) ::hlbm::dbg_range((v), (n), (site))
+#else
+#define HLBM_CELL_OK(row, col, width, kp, site) true
+#define HLBM_RANGE_OK(v, n, site) true
+#endif
+
 constexpr int NPLANE = 13;
 constexpr int P_S = 9, P_AXX = 10, P_AXY = 11, P_AYY = 12;
 enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_DIRICHLET = 2, BC_WALL = 3 };
@@ -417,7 +453,7 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
         const int ly = c / R3X, lx = c - ly * R3X;
         const int gx = x0 - 3 + lx, gy = y0 - 3 + ly;
         const int o = interior ? gy * pitch + gx : locate_w(gx, gy, kp, pitch);
-        sS[c] = o >= 0 ? __ldg(inA + A_S * P + o)
+        sS[c] = o >= 0 ? (HLBM_CELL_OK(o / pitch, o % pitch, 1, kp, 10) ? __ldg(inA + A_S * P + o) : T(0))
                        : (o > -kWallCode ? side.s_(-o - 1) : wall_val<T>(kp, -o - kWallCode, 9));
     }
     {
@@ -434,8 +470,9 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
                 const int o = interior ? gy * pitch + gx : locate_w(gx, gy, kp, pitch);
                 oc[it] = o;
                 if (o >= 0) {
+                    const bool ok = HLBM_CELL_OK(o / pitch, o % pitch, 1, kp, 11);
 #pragma unroll
-                    for (int i = 0; i < 9; i++) f[it][i] = S::get(inF[i * P + o], i, kp);
+                    for (int i = 0; i < 9; i++) f[it][i] = ok ? S::get(inF[i * P + o], i, kp) : T(0);
                 } else if (o > -kWallCode) {
 #pragma unroll
                     for (int i = 0; i < 9; i++) f[it][i] = side.F(-o - 1, i);
@@ -634,6 +671,7 @@ __device__ __forceinline__ void step_tile(const typename S::raw *__restrict__ in
         T f[9];
         build_populations(rho, ux, uy, th, axx, axy, ayy, ex, ey, omega, f);
         const int o = gy * pitch + gx;
+        if (!HLBM_CELL_OK(gy, gx, 1, kp, 12)) continue;
 #pragma unroll
         for (int i = 0; i < 9; i++) outF[i * P + o] = S::put(f[i], i, kp);
         outA[A_S * P + o] = nS[k];

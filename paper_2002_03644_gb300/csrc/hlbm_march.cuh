@@ -257,30 +257,37 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
     auto load_F = [&](int mr, T *fa, T *fb) {
         if (mr >= 0 && vecL) {
             const raw *src = inF + ((long long)mr * pitch + gxL);
+            const bool ok = HLBM_CELL_OK(mr, gxL, 2, kp, 1);
 #pragma unroll
             for (int i = 0; i < 9; i++) {
-                const raw2 v = *reinterpret_cast<const raw2 *>(src + i * P);
+                const raw2 v = ok ? *reinterpret_cast<const raw2 *>(src + i * P) : S::pack(S::put(T(0), i, kp), S::put(T(0), i, kp));
                 fa[i] = S::get(v.x, i, kp);
                 fb[i] = S::get(v.y, i, kp);
             }
         } else {
             const int oa = join_map(mr, mcLa, pitch), ob = join_map(mr, mcLb, pitch);
+            const bool oka = oa < 0 || HLBM_CELL_OK(oa / pitch, oa % pitch, 1, kp, 1);
+            const bool okb = ob < 0 || HLBM_CELL_OK(ob / pitch, ob % pitch, 1, kp, 1);
 #pragma unroll
             for (int i = 0; i < 9; i++) {
-                fa[i] = oa >= 0 ? S::get(inF[oa + i * P], i, kp) : side.F(-oa - 1, i);
-                fb[i] = ob >= 0 ? S::get(inF[ob + i * P], i, kp) : side.F(-ob - 1, i);
+                fa[i] = oa >= 0 ? (oka ? S::get(inF[oa + i * P], i, kp) : T(0)) : side.F(-oa - 1, i);
+                fb[i] = ob >= 0 ? (okb ? S::get(inF[ob + i * P], i, kp) : T(0)) : side.F(-ob - 1, i);
             }
         }
     };
     auto load_s = [&](int mr, T &sa, T &sb) {
         if (mr >= 0 && vecL) {
-            const V v = *reinterpret_cast<const V *>(inA + A_S * P + ((long long)mr * pitch + gxL));
+            const bool ok = HLBM_CELL_OK(mr, gxL, 2, kp, 2);
+            const V v = ok ? *reinterpret_cast<const V *>(inA + A_S * P + ((long long)mr * pitch + gxL))
+                           : Vec2<T>::make(T(0), T(0));
             sa = v.x;
             sb = v.y;
         } else {
             const int oa = join_map(mr, mcLa, pitch), ob = join_map(mr, mcLb, pitch);
-            sa = oa >= 0 ? inA[A_S * P + oa] : side.s_(-oa - 1);
-            sb = ob >= 0 ? inA[A_S * P + ob] : side.s_(-ob - 1);
+            const bool oka = oa < 0 || HLBM_CELL_OK(oa / pitch, oa % pitch, 1, kp, 2);
+            const bool okb = ob < 0 || HLBM_CELL_OK(ob / pitch, ob % pitch, 1, kp, 2);
+            sa = oa >= 0 ? (oka ? inA[A_S * P + oa] : T(0)) : side.s_(-oa - 1);
+            sb = ob >= 0 ? (okb ? inA[A_S * P + ob] : T(0)) : side.s_(-ob - 1);
         }
     };
     auto fetch = [&](int r) {
@@ -290,18 +297,21 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
             const int mr = mrow(r + 1);
             if (mr >= 0 && vec2) {
                 const T *src = inA + ((long long)mr * pitch + gx2);
+                const bool ok = HLBM_CELL_OK(mr, gx2, 2, kp, 3);
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
-                    const V v = *reinterpret_cast<const V *>(src + (A_XX + k) * P);
+                    const V v = ok ? *reinterpret_cast<const V *>(src + (A_XX + k) * P) : Vec2<T>::make(T(0), T(0));
                     pA[0][k] = v.x;
                     pA[1][k] = v.y;
                 }
             } else {
                 const int oa = join_map(mr, mc2a, pitch), ob = join_map(mr, mc2b, pitch);
+                const bool oka = oa >= 0 && HLBM_CELL_OK(oa / pitch, oa % pitch, 1, kp, 3);
+                const bool okb = ob >= 0 && HLBM_CELL_OK(ob / pitch, ob % pitch, 1, kp, 3);
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
-                    pA[0][k] = oa >= 0 ? inA[(A_XX + k) * P + oa] : T(0);
-                    pA[1][k] = ob >= 0 ? inA[(A_XX + k) * P + ob] : T(0);
+                    pA[0][k] = oka ? inA[(A_XX + k) * P + oa] : T(0);
+                    pA[1][k] = okb ? inA[(A_XX + k) * P + ob] : T(0);
                 }
             }
         }
@@ -328,6 +338,15 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
     for (int c = 0; c < 2; c++) cur[c] = nxt[c] = CellN1<T>{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
 
     for (int r = base; r < ye; r++) {
+#ifdef HLBM_DEBUG
+        // ring slots within their rings; the neighbour pairs of phases 2 and 3 inside the CTA
+        {
+            const int slots[14] = {fs0, fs1, fs2, bs1, bs2, ss0, ss1, ss2, ss3, ss4, ns0, ns1, ns2, 0};
+            const int depth[14] = {3, 3, 3, 2, 2, 5, 5, 5, 5, 5, 3, 3, 3, 1};
+            for (int k = 0; k < 14; k++) HLBM_RANGE_OK(slots[k], depth[k], 5);
+        }
+        if (do2) HLBM_RANGE_OK(t + 2, NT, 6);  // phase 2 reads pairs q - 1 .. q + 1, q = t + 1
+#endif
         {
             // ---- load phase: row r+2 of F(n) and the level-n macros, row r+3 of s(n)
             T fa[9], fb[9];
@@ -547,7 +566,9 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
             }
             }
             const long long o = (long long)r * pitch + gx2;
-            if (v3a && v3b) {
+            const bool okst = !v3a || HLBM_CELL_OK(r, gx2, v3b ? 2 : 1, kp, 4);  // checked where a store happens
+            if (!okst) {
+            } else if (v3a && v3b) {
                 raw *dF = outF + o;
 #pragma unroll
                 for (int i = 0; i < 9; i++)
@@ -737,7 +758,7 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
     // state with a1 = 0
     auto load_row = [&](int y) {
         const int mr = mrow(y);
-        if (mr >= 0 && vecL) {
+        if (mr >= 0 && vecL && HLBM_CELL_OK(mr, gxL, 2, kp, 21)) {
             const float *src = in + ((long long)mr * pitch + gxL);
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -753,7 +774,7 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const int o = join_map(mr, c ? mcLb : mcLa, pitch);
-                if (PER || o >= 0) {
+                if ((PER || o >= 0) && HLBM_CELL_OK(o / pitch, o % pitch, 1, kp, 21)) {
 #pragma unroll
                     for (int k = 0; k < 4; k++) pM[c][k] = in[k * P + o];
 #pragma unroll
@@ -770,7 +791,7 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
     auto load_a2 = [&](int y) {
         if (!PHI0 || !do2) return;
         const int mr = mrow(y);
-        if (mr >= 0 && vec2) {
+        if (mr >= 0 && vec2 && HLBM_CELL_OK(mr, gx2, 2, kp, 22)) {
             const float *src = in + ((long long)mr * pitch + gx2);
 #pragma unroll
             for (int k = 0; k < 3; k++) {
@@ -781,8 +802,9 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const int o = join_map(mr, c ? mc2b : mc2a, pitch);
+                const bool ok = (PER || o >= 0) && HLBM_CELL_OK(o / pitch, o % pitch, 1, kp, 22);
 #pragma unroll
-                for (int k = 0; k < 3; k++) pA2[c][k] = (PER || o >= 0) ? in[(MS_AXX + k) * P + o] : 0.0f;
+                for (int k = 0; k < 3; k++) pA2[c][k] = ok ? in[(MS_AXX + k) * P + o] : 0.0f;
             }
         }
     };
@@ -1008,7 +1030,8 @@ __device__ __forceinline__ void moment_segment(const float *__restrict__ in, flo
             }
             const long long o = (long long)r * pitch + gx2;
             float *d = out + o;
-            if (v3a && v3b) {
+            if (v3a && !HLBM_CELL_OK(r, gx2, v3b ? 2 : 1, kp, 24)) {
+            } else if (v3a && v3b) {
                 *reinterpret_cast<V *>(d + MS_RHO * P) = V{A.rho, B.rho};
                 *reinterpret_cast<V *>(d + MS_UX * P) = V{A.ux, B.ux};
                 *reinterpret_cast<V *>(d + MS_UY * P) = V{A.uy, B.uy};

@@ -20,6 +20,7 @@
 // atomics.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdlib>
@@ -1335,10 +1336,22 @@ static int sur_run(hlbm_sur *s, const float *x, float *y, int B, bool keep_z)
     return HLBM_OK;
 }
 
-int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B) { return sur_run(s, x, y, B, true); }
+int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B)
+{
+    nvtxRangePushA("hlbm_sur_forward");
+    const int rc = sur_run(s, x, y, B, true);
+    nvtxRangePop();
+    return rc;
+}
 
 // Inference only: the hidden layers' pre-activations are not stored.
-int hlbm_sur_predict(hlbm_sur *s, const float *x, float *y, int B) { return sur_run(s, x, y, B, false); }
+int hlbm_sur_predict(hlbm_sur *s, const float *x, float *y, int B)
+{
+    nvtxRangePushA("hlbm_sur_predict");
+    const int rc = sur_run(s, x, y, B, false);
+    nvtxRangePop();
+    return rc;
+}
 
 // After hlbm_sur_forward on the same batch: loss = mean((y - target)^2)
 // (target FP32 NHWC [B, H, W, C0] on the device) and the gradient of every

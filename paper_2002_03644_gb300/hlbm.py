@@ -29,7 +29,7 @@ ENTRY_POINTS = (
     "hlbm_create", "hlbm_init_fields", "hlbm_step", "hlbm_get_macros", "hlbm_get_populations",
     "hlbm_diagnostics", "hlbm_state_bytes", "hlbm_get_state", "hlbm_set_state", "hlbm_step_count",
     "hlbm_synchronize", "hlbm_destroy", "hlbm_strerror", "hlbm_last_error", "hlbm_abi_version",
-    "hlbm_diagnostics_noalloc", "hlbm_selftest_wait",
+    "hlbm_diagnostics_noalloc", "hlbm_selftest_wait", "hlbm_selftest_fp64_rate", "hlbm_debug_check",
     "hlbm_batch_create", "hlbm_batch_case", "hlbm_batch_step", "hlbm_batch_autotune", "hlbm_batch_tile",
     "hlbm_batch_destroy",
     "hlbm_sur_create", "hlbm_sur_param_count", "hlbm_sur_set_params", "hlbm_sur_get_params", "hlbm_sur_forward",
@@ -80,7 +80,10 @@ _PD = ctypes.c_void_p  # pointers are passed as raw addresses
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libhlbm.so, or the index-checking debug build libhlbm_debug.so when
+    the environment sets HLBM_LIBRARY=debug (build it with
+    build.build_library(debug=True))."""
+    return _build.LIB_DEBUG if os.environ.get("HLBM_LIBRARY") == "debug" else _build.LIB
 
 
 def _lib():
@@ -161,6 +164,10 @@ def _lib():
                                                  ctypes.c_double, _PD, _P]
         lib.hlbm_selftest_wait.restype = ctypes.c_int
         lib.hlbm_selftest_wait.argtypes = [_P, ctypes.c_longlong, ctypes.c_int]
+        lib.hlbm_selftest_fp64_rate.restype = ctypes.c_int
+        lib.hlbm_selftest_fp64_rate.argtypes = [_P, ctypes.c_int, _PD]
+        lib.hlbm_debug_check.restype = ctypes.c_int
+        lib.hlbm_debug_check.argtypes = [_P, _P, _P]
         _libh = lib
         return lib
 
@@ -322,6 +329,23 @@ def hlbm_selftest_wait(budget_cycles, arrive, stream=None):
     the status code (HLBM_ERR_TIMEOUT when the wait ran out, HLBM_OK when it
     completed) instead of raising."""
     return _lib().hlbm_selftest_wait(stream or None, int(budget_cycles), 1 if arrive else 0)
+
+
+def hlbm_selftest_fp64_rate(iters=1 << 15, stream=None):
+    """Measured FP64 fused multiply-adds per second of this GPU (eight
+    independent chains per thread, all SMs busy); 2 flops each."""
+    out = ctypes.c_double(0.0)
+    _check(_lib().hlbm_selftest_fp64_rate(stream or None, int(iters), ctypes.addressof(out)))
+    return out.value
+
+
+def hlbm_debug_check():
+    """(site, a, b) of the first failed index check since the last call (site
+    0: none), read and cleared; HlbmError(HLBM_ERR_UNSUPPORTED) from the
+    release build."""
+    v = [ctypes.c_longlong(0) for _ in range(3)]
+    _check(_lib().hlbm_debug_check(*[ctypes.addressof(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def hlbm_batch_create(params_list, stream=None):
