@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16pop", "bf16pop", "moments"])
     ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "quadrant"],
+                    help="vortex: the isentropic vortex (default); quadrant: the four-quadrant Riemann problem on its "
+                         "longest-running setting (FD Phi, sigma 0.1, C_0 10, mu 0.01; zero-gradient sides)")
     ap.add_argument("--e2e-inner", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -77,18 +80,24 @@ def parse():
     return ap.parse_args()
 
 
-def workload(n):
+def workload(n, kind="vortex"):
     from paper_2002_03644_gb300 import inputs
+    if kind == "quadrant":
+        case = inputs.four_quadrant(n=n, C0=10.0, mu=0.01, sigma=0.1)
+        case.phi_mode = 1
+        return case
     return inputs.vortex(n=n)
 
 
 def describe(case, precision):
-    return {
-        "workload": f"isentropic vortex {case.nx}x{case.ny} periodic, Ma 1.2, strength 0.2, radius 32, "
-                    f"gamma 1.4, Pr 0.71, sigma 0, mu 1.5e-6, +-1e-6 seeded rho noise",
-        "nx": case.nx, "ny": case.ny, "precision": precision,
-        "l2": "flushed between timed steps (state smaller than L2)",
-    }
+    if case.name == "four_quadrant":
+        text = (f"four-quadrant Riemann problem {case.nx}x{case.ny}, zero-gradient sides, C_0 10, mu 0.01, "
+                f"sigma 0.1, finite-difference Phi")
+    else:
+        text = (f"isentropic vortex {case.nx}x{case.ny} periodic, Ma 1.2, strength 0.2, radius 32, "
+                f"gamma 1.4, Pr 0.71, sigma 0, mu 1.5e-6, +-1e-6 seeded rho noise")
+    return {"workload": text, "nx": case.nx, "ny": case.ny, "precision": precision,
+            "l2": "flushed between timed steps" + (" (state smaller than L2)" if case.nx * case.ny <= 1 << 20 else "")}
 
 
 # ---- distributed plumbing ------------------------------------------------------------
@@ -293,7 +302,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    case = workload(args.n)
+    case = workload(args.n, args.workload)
     from oracle.oracle import Oracle, max_threads
     threads = max_threads()
     o = Oracle(case.nx, case.ny, **case.params())
@@ -339,7 +348,7 @@ def run_ours(args):
 
     prec = {"fp32": hlbm.HLBM_FP32, "fp64": hlbm.HLBM_FP64, "fp16pop": hlbm.HLBM_FP32_F16POP,
             "bf16pop": hlbm.HLBM_FP32_BF16POP, "moments": hlbm.HLBM_FP32_MOMENTS}[args.precision]
-    case = workload(args.n)
+    case = workload(args.n, args.workload)
     cells = case.nx * case.ny
     # a dedicated stream: torch's default stream has handle 0, which the C ABI
     # reads as "create your own stream"; events and flushes must share the
@@ -441,7 +450,7 @@ def run_ours(args):
     if args.precision != "fp64":
         peak = peaks["hbm_gbs"] if peaks else 6800.0
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(args.precision, args.n),
+                "frac": achieved / peak, "traffic": profiled_traffic(args.precision, args.n) if args.workload == "vortex" else None,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                 "kernel": kernel_name(args.precision, cells, case.sigma, case.phi_mode,
                                       all(b == 0 for b in case.bc) and case.ny >= 4
@@ -456,7 +465,7 @@ def run_ours(args):
         peak = 2.0 * fp64_fma_rate / 1e12
         roof = {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
                 "frac": None if tf is None else tf / peak,
-                "traffic": profiled_traffic(args.precision, args.n),
+                "traffic": profiled_traffic(args.precision, args.n) if args.workload == "vortex" else None,
                 "peak_source": "measured in this run: hlbm_selftest_fp64_rate, FP64 FMA chains on every SM "
                                f"(nominal {FP64_NOMINAL_TFLOPS} TFLOP/s)",
                 "fp64_flops_per_cell": fpc, "hbm_gbs_achieved": achieved,

@@ -143,6 +143,80 @@ def test_four_quadrant_full_size_first_step(hl):
     print("\nfour-quadrant 4096^2, one step, L-infinity: " + json.dumps(report))
 
 
+def _report(name, steps, report):
+    print(f"\nprecision errors {name} after {steps} steps:\n" + json.dumps(report, indent=1))
+    out = os.environ.get("HLBM_PRECISION_REPORT")
+    if out:
+        with open(out, "a") as f:
+            f.write(json.dumps({"case": name, "steps": steps, "errors": report}) + "\n")
+
+
+def test_precision_forms_four_quadrant_512_on_the_longest_running_setting(hl):
+    """The four-quadrant configuration's 512^2 error run, on the setting of
+    the paper's own knobs that runs longest before the scheme leaves its range
+    of stability (finite-difference Phi, sigma = 0.1, C_0 = 10, mu = 0.01: 670
+    of the 1536 steps to t = 0.3 in the oracle), over its first 100 steps.
+    The problem is chaotic under round-off: the oracle fed one quadrant's
+    density larger by one part in 2^50 departs from itself by L2 about 2e-4
+    of the density scale.  FP32 and the moment state are held to 3x that
+    measured sensitivity, the 16-bit forms to their L2 bounds, field by
+    field; all are reported."""
+    from oracle.oracle import max_threads
+    n, steps = 512, 100
+    case = inputs.four_quadrant(n=n, C0=10.0, mu=0.01, sigma=0.1)
+    case.phi_mode = 1
+
+    def oracle(rho):
+        o = Oracle(case.nx, case.ny, **case.params())
+        o.set_threads(max_threads())
+        o.init(rho, case.ux, case.uy, case.theta)
+        o.step(steps)
+        return o.macros()
+    ref = oracle(case.rho)
+    r2 = case.rho.copy()
+    r2[n // 2:, n // 2:] *= 1.0 + 2.0 ** -50
+    sens = errors(oracle(r2), ref, case.gamma)
+    report = {"oracle_2^-50": sens}
+    for prec, name in ((1, "fp32"), (4, "moments"), (2, "fp16pop"), (3, "bf16pop")):
+        s = hl.Solver(case.nx, case.ny, precision=prec, **case.params())
+        s.init(*case.fields())
+        s.step(steps)
+        got = s.macros()
+        s.close()
+        e = errors(got, ref, case.gamma)
+        report[name] = e
+        for k in ("rho", "ux", "uy", "theta", "s"):
+            assert np.isfinite(got[k]).all()
+            bound = 3.0 * sens[k]["l2"] if prec in (1, 4) else BOUND[prec]
+            assert e[k]["l2"] <= bound, (name, k, e[k], sens[k])
+    _report("quadrant512", steps, report)
+
+
+def test_16bit_error_follows_the_departure_from_the_reference(hl):
+    """Why FP16 storage misses 1e-4 on the configured vortex: it stores
+    F_i - f_ref_i with 11 significant bits and one reference equilibrium per
+    case, so its error follows the size of that difference, i.e. the flow's
+    departure from the mean state.  On the 256^2 vortex (R = 8, 200 steps)
+    halving and quartering the vortex strength shrinks the FP16 error of rho
+    by more than 2x in all, to within 1e-4 at a quarter of the strength."""
+    rep = {}
+    for beta in (0.2, 0.1, 0.05):
+        case = inputs.vortex(n=256, R=8.0, beta=beta)
+        ora = Oracle(case.nx, case.ny, **case.params())
+        ora.init(*case.fields())
+        ora.step(200)
+        ref = ora.macros()
+        s = hl.Solver(case.nx, case.ny, precision=2, **case.params())
+        s.init(*case.fields())
+        s.step(200)
+        rep[beta] = errors(s.macros(), ref, case.gamma)
+        s.close()
+    e = [rep[b]["rho"]["linf"] for b in (0.2, 0.1, 0.05)]
+    assert e[0] > e[1] > e[2] and e[0] > 2.0 * e[2], e
+    assert e[2] <= 1e-4, e
+    _report("vortex256_fp16_by_strength", 200, {f"beta={b}": rep[b] for b in rep})
+
+
 @pytest.mark.parametrize("prec", [2, 3])
 def test_16bit_checkpoint_keeps_the_reference(hl, prec):
     case = inputs.vortex(n=96, R=6.0)
