@@ -370,72 +370,74 @@ def run_ours(args):
     # clocks are sampled from the first warm-up step to the end of the last
     # GPU leg (the timed steps alone are shorter than the sampling period)
     clk = ClockSampler(local).__enter__()
-    for _ in range(args.warmup):
-        flush()
-        s.step(1)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier(ws)
-    torch.cuda.synchronize()
-    for a, b in ev:
-        flush()
-        a.record(stream)
-        s.step(1)
-        b.record(stream)
-    torch.cuda.synchronize()
-    barrier(ws)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    own_s = sum(step_ms) / 1e3
-    value = job_throughput(cells * args.steps, own_s, ws) / 1e6
-    ms_per_step = max_over_ranks(own_s, ws) / args.steps * 1e3
-
-    # back-to-back steps (L2 warm), reported for context only
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    s.step(args.steps)
-    b.record(stream)
-    torch.cuda.synchronize()
-    b2b = cells * args.steps / (a.elapsed_time(b) / 1e3) / 1e6
-
-    d = s.diagnostics()
-    if d[7] != 0:
-        raise RuntimeError("non-finite state after the timed steps")
-
-    # end to end through the C ABI with pinned host buffers: every e2e step
-    # initialises the state from the host fields, advances it by one time
-    # step and reads rho, u, theta back to the host (so the copies are per
-    # step); the same with 100 time steps per call is reported beside it
-    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case.fields()]
-    outs = [torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
-
-    def e2e_leg(inner, iters):
+    try:
+        for _ in range(args.warmup):
+            flush()
+            s.step(1)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(iters):
-            hlbm.hlbm_init_fields(s.h, *pin, n=cells)
-            s.step(inner)
-            hlbm.hlbm_get_macros(s.h, rho=outs[0], ux=outs[1], uy=outs[2], theta=outs[3], n=cells)
-        return job_throughput(cells * inner * iters, time.perf_counter() - t0, ws) / 1e6
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier(ws)
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush()
+            a.record(stream)
+            s.step(1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        own_s = sum(step_ms) / 1e3
+        value = job_throughput(cells * args.steps, own_s, ws) / 1e6
+        ms_per_step = max_over_ranks(own_s, ws) / args.steps * 1e3
 
-    e2e_leg(1, 2)
-    copy_bytes = 4 * 8 * cells
-    e2e = {"value": e2e_leg(1, max(args.steps, 3)), "unit": UNIT, "h2d_bytes_per_step": copy_bytes,
-           "d2h_bytes_per_step": copy_bytes, "steps_per_call": 1,
-           "note": "one e2e step = hlbm_init_fields(pinned host rho, u_x, u_y, theta) + hlbm_step(1) + "
-                   "hlbm_get_macros(pinned host rho, u_x, u_y, theta)",
-           "amortised": {"value": e2e_leg(args.e2e_inner, 3), "unit": UNIT, "steps_per_call": args.e2e_inner,
-                         "h2d_bytes_per_step": copy_bytes / args.e2e_inner,
-                         "d2h_bytes_per_step": copy_bytes / args.e2e_inner}}
-    s.close()
-    del flush_w, flush_r
+        # back-to-back steps (L2 warm), reported for context only
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.step(args.steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        b2b = cells * args.steps / (a.elapsed_time(b) / 1e3) / 1e6
 
-    batched = surr = None
-    if ws == 1 and not args.no_batched:
-        batched = batched_leg(args, stream, cpu=not args.no_cpu_baseline)
-    if ws == 1 and not args.no_surrogate:
-        surr = surrogate_leg(args, stream)
-    clk.__exit__(None, None, None)
+        d = s.diagnostics()
+        if d[7] != 0:
+            raise RuntimeError("non-finite state after the timed steps")
+
+        # end to end through the C ABI with pinned host buffers: every e2e step
+        # initialises the state from the host fields, advances it by one time
+        # step and reads rho, u, theta back to the host (so the copies are per
+        # step); the same with 100 time steps per call is reported beside it
+        pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in case.fields()]
+        outs = [torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+
+        def e2e_leg(inner, iters):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(iters):
+                hlbm.hlbm_init_fields(s.h, *pin, n=cells)
+                s.step(inner)
+                hlbm.hlbm_get_macros(s.h, rho=outs[0], ux=outs[1], uy=outs[2], theta=outs[3], n=cells)
+            return job_throughput(cells * inner * iters, time.perf_counter() - t0, ws) / 1e6
+
+        e2e_leg(1, 2)
+        copy_bytes = 4 * 8 * cells
+        e2e = {"value": e2e_leg(1, max(args.steps, 3)), "unit": UNIT, "h2d_bytes_per_step": copy_bytes,
+               "d2h_bytes_per_step": copy_bytes, "steps_per_call": 1,
+               "note": "one e2e step = hlbm_init_fields(pinned host rho, u_x, u_y, theta) + hlbm_step(1) + "
+                       "hlbm_get_macros(pinned host rho, u_x, u_y, theta)",
+               "amortised": {"value": e2e_leg(args.e2e_inner, 3), "unit": UNIT, "steps_per_call": args.e2e_inner,
+                             "h2d_bytes_per_step": copy_bytes / args.e2e_inner,
+                             "d2h_bytes_per_step": copy_bytes / args.e2e_inner}}
+        s.close()
+        del flush_w, flush_r
+
+        batched = surr = None
+        if ws == 1 and not args.no_batched:
+            batched = batched_leg(args, stream, cpu=not args.no_cpu_baseline)
+        if ws == 1 and not args.no_surrogate:
+            surr = surrogate_leg(args, stream)
+    finally:
+        clk.__exit__(None, None, None)
 
     if rank != 0:
         if ws > 1:

@@ -20,6 +20,10 @@
  *  - mem_kind says where caller arrays live: HLBM_MEM_HOST (pageable or
  *    pinned host memory) or HLBM_MEM_DEVICE (device memory on the handle's
  *    GPU).  Caller buffers are borrowed for the duration of the call only.
+ *    Page-locked host arrays (pinned or registered) are read and written in
+ *    place by the kernels over the host link; pageable ones go through a
+ *    device staging buffer and a copy.  Both give the same values; the
+ *    environment variable HLBM_ZERO_COPY=0 stages every host array.
  *  - The library allocates and owns all of its device state; nothing is
  *    allocated by hlbm_step.
  *  - Work is enqueued on the stream given to hlbm_create.  hlbm_step returns

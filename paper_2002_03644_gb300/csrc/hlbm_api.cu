@@ -722,6 +722,22 @@ static int run_diagnostics(hlbm_handle *h, double out[8])
     return check_timeout(h);
 }
 
+// The device address of a host buffer that kernels may read and write in
+// place -- page-locked (pinned or registered) host memory, which this GPU
+// reaches over its host link -- or nullptr for pageable memory, which goes
+// through the staging buffer and a copy.  HLBM_ZERO_COPY=0 sends every host
+// buffer through the staging buffer.
+static double *host_view(const void *p)
+{
+    if (!p || env_choice("HLBM_ZERO_COPY", 1, 0, 2) == 0) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? static_cast<double *>(at.devicePointer) : nullptr;
+}
+
 int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const double *uy, const double *theta,
                      const double *a1, int mem_kind)
 {
@@ -734,13 +750,15 @@ int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const 
     const double *src[5] = {rho, ux, uy, theta, a1};
     const double *dev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     if (mem_kind == HLBM_MEM_HOST) {
-        for (int k = 0; k < 4; k++) {
-            CK(cudaMemcpyAsync(h->staging + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "init copy");
+        // pinned fields are read in place by the kernels; pageable ones are
+        // copied to the staging buffer first
+        for (int k = 0; k < 5; k++) {
+            if (!src[k]) continue;
+            if ((dev[k] = host_view(src[k]))) continue;
+            const size_t cnt = (k == 4 ? 3 : 1) * n;
+            CK(cudaMemcpyAsync(h->staging + k * n, src[k], cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+               "init copy");
             dev[k] = h->staging + k * n;
-        }
-        if (a1) {
-            CK(cudaMemcpyAsync(h->staging + 4 * n, a1, 3 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "init copy a1");
-            dev[4] = h->staging + 4 * n;
         }
     } else {
         for (int k = 0; k < 5; k++) dev[k] = src[k];
@@ -843,15 +861,18 @@ static int extract(hlbm_handle *h, double *rho, double *ux, double *uy, double *
     const size_t n = (size_t)h->p.nx * h->p.ny;
     double *dst[7] = {rho, ux, uy, theta, s, a1, F};
     double *dev[7];
+    bool copy_back[7] = {false, false, false, false, false, false, false};
     if (mem_kind == HLBM_MEM_HOST) {
-        // staging holds 9 planes: fields use planes 0..7 (a1 = 3), F uses all 9
-        if (F) {
-            for (int k = 0; k < 6; k++) dev[k] = nullptr;
-            dev[6] = h->staging;
-        } else {
-            const size_t off[6] = {0, 1, 2, 3, 4, 5};
-            for (int k = 0; k < 6; k++) dev[k] = dst[k] ? h->staging + off[k] * n : nullptr;
-            dev[6] = nullptr;
+        // pinned destinations are written in place by the kernel; pageable
+        // ones go through the staging buffer (9 planes: fields use planes
+        // 0..7 (a1 = 3), F uses all 9) and a copy
+        const size_t off[7] = {0, 1, 2, 3, 4, 5, 0};
+        for (int k = 0; k < 7; k++) {
+            dev[k] = nullptr;
+            if (!dst[k] || (F && k < 6)) continue;  // populations are read alone
+            if ((dev[k] = host_view(dst[k]))) continue;
+            dev[k] = h->staging + off[k] * n;
+            copy_back[k] = true;
         }
     } else {
         for (int k = 0; k < 7; k++) dev[k] = dst[k];
@@ -871,12 +892,10 @@ static int extract(hlbm_handle *h, double *rho, double *ux, double *uy, double *
                                                                         dev[2], dev[3], dev[4], dev[5], dev[6], h->kp);
            return cudaGetLastError();
        }), "macros_kernel");
-    if (mem_kind == HLBM_MEM_HOST) {
-        for (int k = 0; k < 7; k++) {
-            if (!dst[k] || !dev[k]) continue;
-            const size_t cnt = (k == 5 ? 3 : (k == 6 ? 9 : 1)) * n;
-            CK(cudaMemcpyAsync(dst[k], dev[k], cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "get copy");
-        }
+    for (int k = 0; k < 7; k++) {
+        if (!copy_back[k]) continue;
+        const size_t cnt = (k == 5 ? 3 : (k == 6 ? 9 : 1)) * n;
+        CK(cudaMemcpyAsync(dst[k], dev[k], cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "get copy");
     }
     CK(cudaStreamSynchronize(h->stream), "get sync");
     return check_timeout(h);
