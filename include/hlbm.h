@@ -135,7 +135,13 @@ typedef struct hlbm_handle hlbm_handle;
 /* Create a solver on the current CUDA device.  stream is a cudaStream_t (or
  * NULL: the library creates and owns a non-blocking stream).  Allocates the
  * ping-pong state (13 planes per copy: 9 post-collision populations, s and
- * a1_xx, a1_xy, a1_yy) and FP64 staging buffers.  *out is NULL on failure. */
+ * a1_xx, a1_xy, a1_yy; rows padded to a multiple of 32 elements, the pad
+ * columns filled with NaN and never written) and FP64 staging buffers.  The
+ * parameters are checked before any CUDA call: HLBM_ERR_ARG for grids
+ * outside 1 .. 2^28 cells or values outside the ranges above (a periodic
+ * side without a periodic partner included), HLBM_ERR_UNSUPPORTED for an
+ * unknown precision or side kind and for walls with the moment state;
+ * HLBM_ERR_NOMEM when the allocation fails.  *out is NULL on failure. */
 int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out);
 
 /* Input and initialisation (Sec. 3.5): from [rho, u, theta]^(0)
