@@ -42,6 +42,19 @@ sys.path.insert(0, ROOT)
 
 # 9 populations + s + 3 a1 read and written once per cell-update
 BYTES_PER_CELL = {"fp32": 104, "fp64": 208, "fp16pop": 68, "bf16pop": 68, "moments": 56}
+# the FP64 marching kernel also reads and writes each cell's level rho, u_x,
+# u_y, theta (4 FP64 planes kept so that no step recomputes them)
+FP64_MARCH_BYTES_PER_CELL = 272
+
+
+def bytes_per_cell(precision, cells):
+    """Bytes one cell-update reads and writes in the fused-step kernel the
+    library launches (kernel choice as in kernel_name)."""
+    if precision == "fp64":
+        march = int(os.environ.get("HLBM_MARCH", "-1" if cells <= 768 * 768 else "0"))
+        if 0 <= march < 4:
+            return FP64_MARCH_BYTES_PER_CELL
+    return BYTES_PER_CELL[precision]
 METRIC, UNIT = "MLUPS", "MLUPS"
 
 
@@ -446,7 +459,7 @@ def run_ours(args):
         return 0
 
     peaks = measured_peaks()
-    bpc = BYTES_PER_CELL[args.precision]
+    bpc = bytes_per_cell(args.precision, cells)
     mean_launch_s = statistics.mean(step_ms) / 1e3
     achieved = bpc * cells / mean_launch_s / 1e9
     if args.precision != "fp64":

@@ -136,7 +136,11 @@ typedef struct hlbm_handle hlbm_handle;
  * NULL: the library creates and owns a non-blocking stream).  Allocates the
  * ping-pong state (13 planes per copy: 9 post-collision populations, s and
  * a1_xx, a1_xy, a1_yy; rows padded to a multiple of 32 elements, the pad
- * columns filled with NaN and never written) and FP64 staging buffers.  The
+ * columns filled with NaN and never written) and FP64 staging buffers.  In
+ * HLBM_FP64 on the row-marching kernel (grids above 768^2 without wall
+ * sides) each copy has 4 more planes, each cell's rho, u_x, u_y, theta of
+ * the level it holds (derived state: hlbm_init_fields computes them, each
+ * step stores them for the next, checkpoints carry them).  The
  * parameters are checked before any CUDA call: HLBM_ERR_ARG for grids
  * outside 1 .. 2^28 cells or values outside the ranges above (a periodic
  * side without a periodic partner included), HLBM_ERR_UNSUPPORTED for an
@@ -183,8 +187,15 @@ int hlbm_get_populations(hlbm_handle *h, double *F, int mem_kind);
 int hlbm_diagnostics(hlbm_handle *h, double out[8]);
 
 /* Checkpoint: the size of the state blob, and a byte-exact copy of the state
- * and step counter into / from host memory.  set_state checks sizes,
- * precision and a header; it returns HLBM_ERR_STATE on any mismatch. */
+ * and step counter into / from host memory: a header, then the state's
+ * planes (13 for the population forms, 7 for HLBM_FP32_MOMENTS, 17 for
+ * HLBM_FP64 on the row-marching kernel: the 13 and the 4 planes of level-n
+ * rho, u_x, u_y, theta).  A run resumed from a blob continues bitwise as the
+ * run that wrote it.  set_state checks sizes, precision and a header; it
+ * returns HLBM_ERR_STATE on any mismatch.  In FP64 it takes a blob of 13
+ * or 17 planes whatever kernel the handle runs: a 13-plane blob set on a
+ * marching handle has its 4 planes derived from F and s (the first step
+ * then agrees with the run that wrote it to rounding). */
 int hlbm_state_bytes(const hlbm_handle *h, size_t *bytes);
 int hlbm_get_state(hlbm_handle *h, void *buf, size_t bytes);
 int hlbm_set_state(hlbm_handle *h, const void *buf, size_t bytes);
@@ -290,8 +301,8 @@ void hlbm_sur_destroy(hlbm_sur *s);
  * Same results, in the same order, as hlbm_diagnostics, for a state that
  * the caller holds: `state` points to device memory with 13 planes of
  * [ny][pitch] elements (FP64 or FP32 per `precision`: 9 post-collision
- * populations, s, a1_xx, a1_xy, a1_yy), the layout hlbm_get_state copies
- * after its header.  gamma is the heat capacity ratio of the case.  out is
+ * populations, s, a1_xx, a1_xy, a1_yy), the layout of the first 13 planes
+ * that hlbm_get_state copies after its header.  gamma is the heat capacity ratio of the case.  out is
  * a host array of 8 doubles.
  *
  * `stream` must be an explicit cudaStream_t, best one created with

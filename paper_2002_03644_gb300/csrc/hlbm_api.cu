@@ -71,6 +71,7 @@ struct hlbm_handle {
     bool moments = false;       // HLBM_FP32_MOMENTS: 7 FP32 planes, moment-state kernel
     bool walls = false;         // a wall side: tiled kernel plus wall_ghost_kernel each step
     bool periodic = false;      // all four sides periodic and ny >= 4 (specialised marching kernels)
+    bool mcache = false;        // FP64 marching: level-n rho, u, theta planes behind the state (A_RHO .. A_TH)
     void *wall_g = nullptr;     // wall ghost rows (KParams::wall_g)
     int march_nseg = 1;         // row segments per strip
     int *d_err = nullptr;       // device-side timeout flag of the TMA kernel
@@ -111,10 +112,30 @@ static T *aux_planes(const hlbm_handle *h, int idx)
     return reinterpret_cast<T *>(static_cast<char *>(h->state[idx]) + 9 * h->plane * sizeof(typename S::raw));
 }
 
-// Bytes of one state copy.
+// Bytes of one state copy (what a checkpoint holds).
 static size_t payload_bytes(const hlbm_handle *h)
 {
     return h->moments ? h->plane * MS_NPLANE * sizeof(float) : h->plane * (9 * h->fsize + 4 * h->asize);
+}
+
+// Bytes allocated per state copy: the payload, then the FP64 marching
+// form's cache planes.
+static size_t alloc_bytes(const hlbm_handle *h)
+{
+    return payload_bytes(h) + (h->mcache ? h->plane * A_NCACHE * sizeof(double) : 0);
+}
+
+// FP64 marching form: derive the cache planes of state copy cur from its
+// F(n) and s(n), after init or a checkpoint set the state.
+static cudaError_t fill_cache(hlbm_handle *h)
+{
+    if (!h->mcache) return cudaSuccess;
+    const int blk = 256;
+    const long long n = (long long)h->p.nx * h->p.ny;
+    const int grid = (int)std::min<long long>((n + blk - 1) / blk, 65535);
+    cache_macros_kernel<<<grid, blk, 0, h->stream>>>(pop_planes<double, FullStore<double>>(h, h->cur),
+                                                     aux_planes<double, FullStore<double>>(h, h->cur), h->kp);
+    return cudaGetLastError();
 }
 
 // Call fn(Types<T, S>{}) for the handle's precision.
@@ -633,7 +654,12 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
     h->fsize = (params->precision == HLBM_FP32_F16POP || params->precision == HLBM_FP32_BF16POP) ? 2 : h->asize;
     h->pitch = (params->nx + 31) / 32 * 32;
     h->plane = (size_t)h->pitch * params->ny;
-    const size_t bytes = payload_bytes(h);
+    // FP64 without wall sides may take the marching kernel (decided below);
+    // its cache planes are allocated up front and dropped from use if not
+    bool wall_side = false;
+    for (int k = 0; k < 4; k++) wall_side = wall_side || params->bc[k] == HLBM_BC_WALL;
+    h->mcache = params->precision == HLBM_FP64 && !wall_side;
+    const size_t bytes = alloc_bytes(h);
     const size_t ncell = (size_t)params->nx * params->ny;
     if (cudaMalloc(&h->state[0], bytes) != cudaSuccess || cudaMalloc(&h->state[1], bytes) != cudaSuccess ||
         cudaMalloc(&h->staging, 9 * ncell * sizeof(double)) != cudaSuccess ||
@@ -698,6 +724,7 @@ int hlbm_create(const hlbm_params *params, void *stream, hlbm_handle **out)
         hlbm_destroy(h);
         return HLBM_ERR_CUDA;
     }
+    h->mcache = h->mcache && h->march_variant >= 0;
     *out = h;
     return HLBM_OK;
 }
@@ -793,6 +820,7 @@ int hlbm_init_fields(hlbm_handle *h, const double *rho, const double *ux, const 
            return cudaGetLastError();
        }), "init_kernel");
     h->cur = 0;
+    CK(fill_cache(h), "cache_macros_kernel");
     h->step = 0;
     h->initialized = true;
     CK(cudaStreamSynchronize(h->stream), "init sync");
@@ -933,7 +961,7 @@ int hlbm_synchronize(hlbm_handle *h)
 int hlbm_state_bytes(const hlbm_handle *h, size_t *bytes)
 {
     if (!h || !bytes) return HLBM_ERR_ARG;
-    *bytes = sizeof(StateHeader) + payload_bytes(h);
+    *bytes = sizeof(StateHeader) + alloc_bytes(h);
     return HLBM_OK;
 }
 
@@ -949,7 +977,8 @@ int hlbm_get_state(hlbm_handle *h, void *buf, size_t bytes)
     StateHeader hd;
     memset(&hd, 0, sizeof(hd));
     hd.magic = STATE_MAGIC; hd.abi = HLBM_ABI_VERSION; hd.precision = h->p.precision;
-    hd.nx = h->p.nx; hd.ny = h->p.ny; hd.pitch = h->pitch; hd.nplane = h->moments ? MS_NPLANE : NPLANE;
+    hd.nx = h->p.nx; hd.ny = h->p.ny; hd.pitch = h->pitch;
+    hd.nplane = h->moments ? MS_NPLANE : NPLANE + (h->mcache ? A_NCACHE : 0);
     hd.step = h->step;
     hd.payload_bytes = (int64_t)(need - sizeof(StateHeader));
     for (int i = 0; i < 9; i++) hd.ref[i] = h->kp.f_ref[i];
@@ -964,21 +993,41 @@ int hlbm_set_state(hlbm_handle *h, const void *buf, size_t bytes)
 {
     NvtxRange nvtx_range("hlbm_set_state");
     if (!h || !buf) return HLBM_ERR_ARG;
-    size_t need = 0;
-    hlbm_state_bytes(h, &need);
-    if (bytes != need) return fail(h, HLBM_ERR_STATE, "state size mismatch");
+    if (bytes < sizeof(StateHeader)) return fail(h, HLBM_ERR_STATE, "state size mismatch");
     StateHeader hd;
     memcpy(&hd, buf, sizeof(hd));
+    // The population forms accept 13 planes, and in FP64 also 17 (the 13
+    // and the marching form's cache planes, which hlbm_get_state of such a
+    // handle writes): the cache is copied when both sides have it, derived
+    // from F(n) and s(n) when only the handle has it, and skipped when only
+    // the blob has it.
+    const size_t base = payload_bytes(h);
+    const size_t cache = h->plane * A_NCACHE * sizeof(double);
+    bool ok_planes;
+    size_t blob_payload;
+    if (h->moments) {
+        ok_planes = hd.nplane == MS_NPLANE;
+        blob_payload = base;
+    } else if (hd.nplane == NPLANE + A_NCACHE) {
+        ok_planes = h->p.precision == HLBM_FP64;
+        blob_payload = base + cache;
+    } else {
+        ok_planes = hd.nplane == NPLANE;
+        blob_payload = base;
+    }
     if (hd.magic != STATE_MAGIC || hd.abi != HLBM_ABI_VERSION || hd.precision != h->p.precision || hd.nx != h->p.nx ||
-        hd.ny != h->p.ny || hd.pitch != h->pitch || hd.nplane != (h->moments ? MS_NPLANE : NPLANE) || hd.step < 0 ||
-        hd.payload_bytes != (int64_t)(need - sizeof(StateHeader)))
+        hd.ny != h->p.ny || hd.pitch != h->pitch || !ok_planes || hd.step < 0 ||
+        hd.payload_bytes != (int64_t)blob_payload)
         return fail(h, HLBM_ERR_STATE, "state header mismatch");
+    if (bytes != sizeof(hd) + blob_payload) return fail(h, HLBM_ERR_STATE, "state size mismatch");
+    const bool copy_cache = h->mcache && blob_payload > base;
     CK(cudaSetDevice(h->device), "cudaSetDevice");
-    CK(cudaMemcpyAsync(h->state[0], static_cast<const char *>(buf) + sizeof(hd), (size_t)hd.payload_bytes,
+    CK(cudaMemcpyAsync(h->state[0], static_cast<const char *>(buf) + sizeof(hd), copy_cache ? base + cache : base,
                        cudaMemcpyHostToDevice, h->stream), "state copy");
-    CK(cudaStreamSynchronize(h->stream), "state sync");
     for (int i = 0; i < 9; i++) h->kp.f_ref[i] = hd.ref[i];
     h->cur = 0;
+    if (!copy_cache) CK(fill_cache(h), "cache_macros_kernel");
+    CK(cudaStreamSynchronize(h->stream), "state sync");
     h->step = hd.step;
     h->initialized = true;
     return HLBM_OK;

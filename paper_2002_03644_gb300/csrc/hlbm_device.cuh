@@ -167,6 +167,12 @@ struct BF16Store {
 };
 // auxiliary plane indices
 constexpr int A_S = 0, A_XX = 1, A_XY = 2, A_YY = 3;
+// FP64 row-marching form only: four more planes behind the auxiliary ones
+// hold each cell's level-n rho, u_x, u_y, theta.  They are derived state, so
+// a checkpoint leaves them out: the step that ends a level stores the values
+// its phase 2 computed, and the next step's load phase reads them instead of
+// taking the moments of F(n) and recovering theta again.
+constexpr int A_RHO = 4, A_UX = 5, A_UY = 6, A_TH = 7, A_NCACHE = 4;
 
 // Dirichlet constants in the kernel's precision.
 template <typename T> struct Side;

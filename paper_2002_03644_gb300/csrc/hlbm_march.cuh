@@ -370,14 +370,16 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
             gC[(fs2 * 3 + 2) * NT + t] = Vec2<T>::make(fa[6], fb[6]);
             const int mr = mrow(r + 2);
             T m[2][4];
-            auto macros = [&](const T *f, T sv, int o, T *mm) {
+            // FP64: the level-n rho, u, theta of a cell are the level-(n+1)
+            // values that phase 2 of the previous step computed (the
+            // collision conserves rho and rho u, eqs. rhoalgo, ualgo), kept in
+            // the cache planes A_RHO .. A_TH; a Dirichlet position holds the
+            // side's state
+            auto cached = [&](int o, T *mm) {
                 if (o >= 0) {
-                    T jx, jy;
-                    moments(f, mm[0], jx, jy);
-                    const T ir = fdiv(T(1), mm[0]);
-                    mm[1] = jx * ir;
-                    mm[2] = jy * ir;
-                    mm[3] = cs.theta(mm[0], sv);
+                    const bool ok = HLBM_CELL_OK(o / pitch, o % pitch, 1, kp, 1);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) mm[k] = ok ? inA[(A_RHO + k) * P + o] : T(0);
                 } else {
                     const int sd = -o - 1;
                     mm[0] = side.rho(sd); mm[1] = side.ux(sd); mm[2] = side.uy(sd); mm[3] = side.th(sd);
@@ -398,8 +400,8 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
                 if (!PER && oa < 0) { const int sd = -oa - 1; m[0][0] = side.rho(sd); m[0][1] = side.ux(sd); m[0][2] = side.uy(sd); m[0][3] = side.th(sd); }
                 if (!PER && ob < 0) { const int sd = -ob - 1; m[1][0] = side.rho(sd); m[1][1] = side.ux(sd); m[1][2] = side.uy(sd); m[1][3] = side.th(sd); }
             } else {
-                macros(fa, sPa, join_map(mr, mcLa, pitch), m[0]);
-                macros(fb, sPb, join_map(mr, mcLb, pitch), m[1]);
+                cached(join_map(mr, mcLa, pitch), m[0]);
+                cached(join_map(mr, mcLb, pitch), m[1]);
             }
 #pragma unroll
             for (int k = 0; k < 4; k++) rM[(fs2 * 4 + k) * NT + t] = Vec2<T>::make(m[0][k], m[1][k]);
@@ -577,6 +579,13 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
                 *reinterpret_cast<V *>(dA + A_S * P) = Vec2<T>::make(A.s, B.s);
 #pragma unroll
                 for (int k = 0; k < 3; k++) *reinterpret_cast<V *>(dA + (A_XX + k) * P) = Vec2<T>::make(aa[k], ab[k]);
+                if constexpr (std::is_same<T, double>::value) {
+                    // the cache planes: this row's level n+1, the next step's level n
+                    *reinterpret_cast<V *>(dA + A_RHO * P) = Vec2<T>::make(A.rho, B.rho);
+                    *reinterpret_cast<V *>(dA + A_UX * P) = Vec2<T>::make(A.ux, B.ux);
+                    *reinterpret_cast<V *>(dA + A_UY * P) = Vec2<T>::make(A.uy, B.uy);
+                    *reinterpret_cast<V *>(dA + A_TH * P) = Vec2<T>::make(A.th, B.th);
+                }
             } else if (v3a) {
                 raw *dF = outF + o;
 #pragma unroll
@@ -585,6 +594,9 @@ __device__ __forceinline__ void march_pair_segment(const typename S::raw *__rest
                 dA[A_S * P] = A.s;
 #pragma unroll
                 for (int k = 0; k < 3; k++) dA[(A_XX + k) * P] = aa[k];
+                if constexpr (std::is_same<T, double>::value) {
+                    dA[A_RHO * P] = A.rho; dA[A_UX * P] = A.ux; dA[A_UY * P] = A.uy; dA[A_TH * P] = A.th;
+                }
             }
         }
         // next row: the values computed in phase 2 become the cells' own
@@ -611,6 +623,32 @@ march_pair_kernel(const typename S::raw *__restrict__ inF, const T *__restrict__
     const int ys = seg_start(blockIdx.y, nseg, kp.ny), ye = seg_start(blockIdx.y + 1, nseg, kp.ny);
     march_pair_segment<T, S, NT, SIG, PHI0, PER>(inF, inA, outF, outA, kp, blockIdx.x * PairGeom<T, NT>::W, ys, ye,
                                                  smem_raw);
+}
+
+// FP64 row-marching form: the cache planes of a state whose level-n values
+// no step has stored yet (after init or a checkpoint is set).  Per cell,
+// rho and u are the moments of F(n) (eqs. rhoalgo, ualgo) and theta follows
+// from rho and s(n) (eq. Entropie expression): the arithmetic the load phase
+// would do.  One thread per cell of the interior; pad columns stay as they are.
+__global__ void cache_macros_kernel(const double *__restrict__ F, double *__restrict__ A, const KParams kp)
+{
+    const long long n = (long long)kp.nx * kp.ny;
+    const long long P = kp.plane;
+    Consts<double> cs;
+    cs.load(kp);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(i / kp.nx), x = (int)(i % kp.nx);
+        const long long o = (long long)y * kp.pitch + x;
+        double f[9], rho, jx, jy;
+#pragma unroll
+        for (int k = 0; k < 9; k++) f[k] = F[o + k * P];
+        moments(f, rho, jx, jy);
+        const double ir = fdiv(1.0, rho);
+        A[A_RHO * P + o] = rho;
+        A[A_UX * P + o] = jx * ir;
+        A[A_UY * P + o] = jy * ir;
+        A[A_TH * P + o] = cs.theta(rho, A[A_S * P + o]);
+    }
 }
 
 // ---- many cases in one persistent launch (FP32) ---------------------------------

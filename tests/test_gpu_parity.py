@@ -401,6 +401,48 @@ def test_checkpoint_roundtrip_is_bitwise(hl, precision):
     assert e.value.code == hl.HLBM_ERR_STATE
 
 
+def test_fp64_marching_checkpoint_carries_the_level_macros(hl):
+    """The FP64 marching form keeps each cell's level-n rho, u, theta in 4
+    planes behind the state; its blob has 17 planes and resumes bitwise.  A
+    13-plane blob (from the tiled kernel) set on a marching handle has them
+    derived from F and s; a 17-plane blob set on a tiled handle gives its
+    first 13 planes."""
+    case = inputs.random_smooth(70, 44, seed=5, amp=0.05, mu=2e-3, sigma=0.4)
+    with _env(HLBM_MARCH=0, HLBM_MARCH_ROWS=7):
+        a = hl.Solver(case.nx, case.ny, precision=0, **case.params())
+        b = hl.Solver(case.nx, case.ny, precision=0, **case.params())
+        c = hl.Solver(case.nx, case.ny, precision=0, **case.params())
+    with _env(HLBM_MARCH=-1):
+        t = hl.Solver(case.nx, case.ny, precision=0, **case.params())
+    a.init(*case.fields())
+    a.step(10)
+    blob = a.state()
+    F10 = a.populations()
+    a.step(10)
+    b.set_state(blob)
+    b.step(10)
+    assert np.array_equal(a.populations(), b.populations())
+    ma, mb = a.macros(), b.macros()
+    for k in ma:
+        assert np.array_equal(ma[k], mb[k]), k
+    # 17-plane blob on the tiled kernel: the first 13 planes
+    t.set_state(blob)
+    assert np.array_equal(t.populations(), F10)
+    # 13-plane blob on the marching kernel: the cache derived from F and s;
+    # both runs then follow the same scheme to rounding
+    t.step(10)
+    tb = t.state()
+    assert len(tb) < len(blob)
+    c.set_state(tb)
+    c.step(10)
+    t.step(10)
+    mc, mt = c.macros(), t.macros()
+    for k in mc:
+        assert np.max(np.abs(mc[k] - mt[k])) <= 1e-12 * np.max(np.abs(mt[k])) + 1e-15, k
+    for s_ in (a, b, c, t):
+        s_.close()
+
+
 def test_error_paths(hl):
     case = inputs.random_smooth(16, 16, seed=1)
     s = hl.Solver(16, 16, precision=1, **case.params())
