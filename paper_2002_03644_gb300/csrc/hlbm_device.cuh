@@ -9,9 +9,10 @@
 //   9     entropy s (eq. Entropie expression)
 //   10-12 a1_xx, a1_xy, a1_yy (eq. a1sigalgo)
 // pitch is nx rounded up to 32 elements so that every row starts on a
-// 128-byte boundary.  rho and u of a level are never stored: they are the
-// moments of F (collision invariants, eqs. rhoalgo, ualgo); theta follows
-// from s and rho.
+// 128-byte boundary.  rho and u of a level are the moments of F (collision
+// invariants, eqs. rhoalgo, ualgo) and theta follows from s and rho; only the
+// FP64 row-marching form also stores them, in four planes behind these
+// (A_RHO .. A_TH), so that no step recomputes them.
 //
 // This file holds the tiled form of the step (FP64, and FP32 grids of up to
 // 768^2 cells) with the scalar cell arithmetic; hlbm_march.cuh holds the
