@@ -258,17 +258,18 @@ def kernel_name(precision, cells, sigma=0.0, phi_mode=0, periodic=False):
 FP64_NOMINAL_TFLOPS = 1.25
 
 
-def profiled_fp64_flops(n):
-    """FP64 operations per cell-update of the FP64 fused kernel from the
-    committed ncu count, if it was taken on the current kernel source."""
+def profiled_fp64_counts(n):
+    """FP64 operations (add, mul, 2 per fma) and FP64 instructions per
+    cell-update of the FP64 fused kernel from the committed ncu count, if it
+    was taken on the current kernel source; (None, None) otherwise."""
     path = os.path.join(ROOT, "profiles", "fused_step_vortex_traffic.json")
     try:
         e = json.load(open(path)).get(f"fp64_{n}")
     except Exception:
-        return None
+        return None, None
     if not e or e.get("kernel_source_hash") != kernel_source_hash():
-        return None
-    return e.get("fp64_flops_per_cell")
+        return None, None
+    return e.get("fp64_flops_per_cell"), e.get("fp64_instructions_per_cell")
 
 
 def profiled_traffic(precision, n):
@@ -474,16 +475,20 @@ def run_ours(args):
     else:
         # FP64 is bound by GB300's FP64 pipe: FP64 operations (add, mul, 2 per
         # fma) executed per cell-update, counted by ncu, against this GPU's
-        # FP64 rate measured in the same run by the library's FMA-chain probe
-        fpc = profiled_fp64_flops(args.n)
+        # FP64 rate measured in the same run by the library's FMA-chain probe.
+        # An add or a multiply occupies the pipe like an FMA but counts one
+        # flop, so the FP64 instruction rate against the probe's FMA rate
+        # (pipe_instruction_frac) is the tighter measure.
+        fpc, ipc = profiled_fp64_counts(args.n)
         tf = None if fpc is None else fpc * cells / mean_launch_s / 1e12
         peak = 2.0 * fp64_fma_rate / 1e12
         roof = {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
                 "frac": None if tf is None else tf / peak,
+                "pipe_instruction_frac": None if ipc is None else ipc * cells / mean_launch_s / fp64_fma_rate,
                 "traffic": profiled_traffic(args.precision, args.n) if args.workload == "vortex" else None,
                 "peak_source": "measured in this run: hlbm_selftest_fp64_rate, FP64 FMA chains on every SM "
                                f"(nominal {FP64_NOMINAL_TFLOPS} TFLOP/s)",
-                "fp64_flops_per_cell": fpc, "hbm_gbs_achieved": achieved,
+                "fp64_flops_per_cell": fpc, "fp64_instructions_per_cell": ipc, "hbm_gbs_achieved": achieved,
                 "kernel": kernel_name(args.precision, cells, case.sigma, case.phi_mode),
                 "algorithmic_bytes_per_launch": bpc * cells}
 
