@@ -59,11 +59,12 @@ def _shear(hl, nu_phys, Ma, precision, ablation=0, span=30000, every=250):
 
 @pytest.mark.parametrize("row", range(6))
 def test_gpu_shear_wave_matches_table1(hl, golden_dir, row):
-    """FP64: the viscosity error of Table 1 within 15 %."""
+    """FP64: the viscosity error of Table 1 within 11 %, the bound the
+    oracle's own pin holds (its worst row is 10.1 % off)."""
     nu_phys, Ma, eps_paper = map(float, _rows(golden_dir, "shear_wave_table1.txt")[row])
     eps, _ = _shear(hl, nu_phys, Ma, 0)
     assert eps is not None
-    assert abs(eps - eps_paper) <= 0.15 * eps_paper, (eps, eps_paper)
+    assert abs(eps - eps_paper) <= 0.11 * eps_paper, (eps, eps_paper)
 
 
 @pytest.mark.parametrize("row", range(6))
