@@ -3,9 +3,10 @@ kernels check the cell of every global access and the marching kernel's
 ring slots; a failed check is recorded and the access skipped, never
 trapped.  Run in a child process (a process loads one build of the
 library): every step kernel family -- the marching kernel on an all-periodic
-grid and with every boundary kind, the tiled kernel, the moment state and a
-batch -- runs clean (no failed check) and still meets the FP32 parity bound
-against the oracle.  The release build answers HLBM_ERR_UNSUPPORTED."""
+grid and with every boundary kind (FP32, FP16 storage, and FP64 with its
+cache planes of the level macros), the tiled kernel, the moment state and a
+batch -- runs clean (no failed check) and still meets its parity bound
+against the oracle (FP64 1e-10, FP32 1e-4).  The release build answers HLBM_ERR_UNSUPPORTED."""
 import json
 import os
 import subprocess
@@ -30,7 +31,9 @@ runs = [("march periodic", dict(HLBM_MARCH=0), 1, (0, 0, 0, 0)),
         ("tiled boundaries", dict(HLBM_MARCH=-1), 1, (1, 1, 2, 2)),
         ("moments periodic", dict(), 4, (0, 0, 0, 0)),
         ("moments boundaries", dict(HLBM_MARCH_ROWS=3), 4, (2, 1, 1, 1)),
-        ("fp16 march", dict(HLBM_MARCH=0), 2, (0, 0, 0, 0))]
+        ("fp16 march", dict(HLBM_MARCH=0), 2, (0, 0, 0, 0)),
+        ("fp64 march boundaries", dict(HLBM_MARCH=0, HLBM_MARCH_ROWS=5), 0, (1, 2, 2, 1)),
+        ("fp64 march periodic", dict(HLBM_MARCH=0), 0, (0, 0, 0, 0))]
 for name, env, prec, bc in runs:
     case = inputs.random_smooth(101, 67, seed=3, amp=0.04, u0=(0.06, 0.01), theta0=0.2, mu=3e-3, sigma=0.5,
                                 bc=bc, bc_state=bs)
@@ -38,7 +41,7 @@ for name, env, prec, bc in runs:
         _, _, got, ref = run_pair(hlbm, case, prec, 9)
     site = hlbm.hlbm_debug_check()
     if prec != 2:
-        compare(got, ref, case.gamma, TOL[1])
+        compare(got, ref, case.gamma, TOL[prec if prec in (0, 1) else 1])
     out["checks"].append([name, list(site)])
 cases = [inputs.vortex(n=n, R=n / 12.0) for n in (48, 96)] + [inputs.sod(nx=160, ny=4, C0=3.875, mu=3e-6, sigma=0.0)]
 b = hlbm.Batch([dict(nx=c.nx, ny=c.ny, precision=1, **c.params()) for c in cases])
