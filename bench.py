@@ -85,8 +85,8 @@ def parse():
     ap.add_argument("--sur-tol", type=float, default=1.0,
                     help="judged-error tolerance of the hybrid rollout (max-abs, normalised fields)")
     ap.add_argument("--batched", action="store_true",
-                    help="only the batched leg: the 64-case batched vortex sweep (one persistent launch per "
-                         "step) against the same cases run one after another")
+                    help="only the batched leg: the 64-case batched vortex sweep (one launch per step over all "
+                         "cases, replayed from CUDA graphs) against the same cases run one after another")
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--no-batched", action="store_true", help="leave the batched leg out of the default line")
     ap.add_argument("--no-surrogate", action="store_true", help="leave the surrogate leg out of the default line")
