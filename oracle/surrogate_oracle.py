@@ -88,9 +88,16 @@ def loss(y, target):
 
 def backward(params, cache, y, target):
     """Gradients of loss(y, target) with respect to every (W, b) and x."""
+    return backward_dy(params, cache, 2.0 * (y - target) / y.size)
+
+
+def backward_dy(params, cache, dy):
+    """Chain rule through y = x + net(x) from a given dL/dy: the gradients
+    with respect to every (W, b) and dL/dx (the residual path included).
+    Chaining two calls, y1 = f(x) and y2 = f(y1), the dL/dx of the second
+    call is the upstream gradient of the first."""
     acts, pre = cache
     L = len(params)
-    dy = 2.0 * (y - target) / y.size
     dh = dy.copy()
     grads = [None] * L
     for l in range(L - 1, -1, -1):

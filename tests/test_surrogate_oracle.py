@@ -79,6 +79,47 @@ def test_backward_matches_finite_differences(widths):
         assert abs(dx[idx] - fd) < 1e-7 * max(1.0, abs(fd))
 
 
+def test_two_call_chain_rule_matches_finite_differences():
+    """Two calls chained, y1 = f(x), y2 = f(y1), with the loss of both:
+    L = loss(y2, t2) + loss(y1, t1).  The gradient by backward_dy (the second
+    call's dL/dy1 added to the first call's own dL/dy1) against central
+    differences of L, for weights, biases and the input."""
+    widths = (3, 4, 3)
+    params = _net(widths, seed=7)
+    x = RNG.normal(size=(2, widths[0], 5, 6))
+    t1, t2 = RNG.normal(size=x.shape), RNG.normal(size=x.shape)
+
+    def L(ps, xx):
+        y1 = S.forward(ps, xx)[0]
+        return S.loss(S.forward(ps, y1)[0], t2) + S.loss(y1, t1)
+
+    y1, c1 = S.forward(params, x)
+    y2, c2 = S.forward(params, y1)
+    g2, dy1 = S.backward(params, c2, y2, t2)
+    g1, dx = S.backward_dy(params, c1, dy1 + 2.0 * (y1 - t1) / y1.size)
+    grads = [(a[0] + b[0], a[1] + b[1]) for a, b in zip(g1, g2)]
+    h = 1e-6
+    for l, (W, b) in enumerate(params):
+        for idx in [(0, 0, 0, 0), (widths[l + 1] - 1, widths[l] - 1, 2, 1)]:
+            Wp, Wm = W.copy(), W.copy()
+            Wp[idx] += h; Wm[idx] -= h
+            pp = list(params); pp[l] = (Wp, b)
+            pm = list(params); pm[l] = (Wm, b)
+            fd = (L(pp, x) - L(pm, x)) / (2 * h)
+            assert abs(grads[l][0][idx] - fd) < 1e-7 * max(1.0, abs(fd)), (l, idx)
+        bp, bm = b.copy(), b.copy()
+        bp[-1] += h; bm[-1] -= h
+        pp = list(params); pp[l] = (W, bp)
+        pm = list(params); pm[l] = (W, bm)
+        fd = (L(pp, x) - L(pm, x)) / (2 * h)
+        assert abs(grads[l][1][-1] - fd) < 1e-7 * max(1.0, abs(fd))
+    for idx in [(0, 0, 0, 0), (1, widths[0] - 1, 4, 5)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h; xm[idx] -= h
+        fd = (L(params, xp) - L(params, xm)) / (2 * h)
+        assert abs(dx[idx] - fd) < 1e-7 * max(1.0, abs(fd))
+
+
 def test_adam_first_step_moves_by_lr_times_sign():
     p = np.array([1.0, -2.0, 3.0])
     g = np.array([0.5, -4.0, 1e-3])
