@@ -82,6 +82,11 @@ def parse():
     ap.add_argument("--sur-pushforward", type=float, default=0.0,
                     help="fraction of training inputs replaced by the network's own prediction from the previous "
                          "snapshot (second half of the epochs)")
+    ap.add_argument("--sur-rollout", type=int, default=1,
+                    help="calls chained through the network per training sample from --sur-rollout-from on "
+                         "(1: one call; k > 1: the loss of k calls, back-propagated through the chain)")
+    ap.add_argument("--sur-rollout-from", type=float, default=0.5,
+                    help="fraction of the epochs after which the chained training starts")
     ap.add_argument("--sur-tol", type=float, default=1.0,
                     help="judged-error tolerance of the hybrid rollout (max-abs, normalised fields)")
     ap.add_argument("--batched", action="store_true",
@@ -673,10 +678,11 @@ def surrogate_leg(args, stream):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     hist = sur.fit(Xn[:ntrain], Yn[:ntrain], epochs=args.sur_epochs, batch=batch, lr=2e-3, lr_final=5e-5,
-                   noise=args.sur_noise, pushforward=args.sur_pushforward, pairs_per_run=4)
+                   noise=args.sur_noise, pushforward=args.sur_pushforward, pairs_per_run=4,
+                   rollout=args.sur_rollout, rollout_from=args.sur_rollout_from)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    samples = args.sur_epochs * ntrain
+    samples = sur.fit_calls  # one forward and one backward pass of one sample each
     errs, errs_id, mse, mse_id = [], [], [], []
     for b0 in range(ntrain, Xn.shape[0] - batch + 1, batch):
         pred = sur.predict(Xn[b0:b0 + batch].contiguous())
@@ -752,6 +758,7 @@ def surrogate_leg(args, stream):
                     "net 4-64x5-4 3x3 periodic conv, GELU",
         "samples": int(args.sur_samples), "train": ntrain, "epochs": args.sur_epochs, "batch": batch,
         "input_noise": args.sur_noise, "pushforward": args.sur_pushforward,
+        "rollout_training": {"calls": args.sur_rollout, "from_epoch_fraction": args.sur_rollout_from},
         "surrogate_s_per_sample": t_sur, "hlbm_s_per_16_steps": t_hlbm,
         "train_samples_per_s": samples / t_train, "train_tflops": 3 * fwd_flops * samples / t_train / 1e12,
         "data_generation_s": t_data, "loss_first_last": [hist[0], hist[-1]],

@@ -280,6 +280,18 @@ int hlbm_sur_forward(hlbm_sur *s, const float *x, float *y, int B);
 int hlbm_sur_predict(hlbm_sur *s, const float *x, float *y, int B);
 /* after hlbm_sur_forward: gradients of mean((y - target)^2); *loss if non-NULL */
 int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss);
+/* The backward pass for a rollout through the network (y1 = f(x),
+ * y2 = f(y1), ...), after hlbm_sur_forward: dL/dy = 2 (y - target) / n + dy,
+ * where n = B H W C and dy ([B, H, W, C] like y, device memory) is the
+ * upstream gradient from later calls, or NULL.  With accumulate != 0 the
+ * parameter gradients are added to those already held (from a backward
+ * pass of another call) instead of replacing them; hlbm_sur_adam then steps
+ * on the sum.  dx (device, [B, H, W, C], or NULL) receives dL/dx, the
+ * residual's identity included: the dy of the call that produced x.
+ * target is required; *loss (if non-NULL) is its mean squared error alone.
+ * HLBM_ERR_ARG as hlbm_sur_backward. */
+int hlbm_sur_backward_ex(hlbm_sur *s, const float *target, const float *dy, int accumulate, float *dx,
+                         double *loss);
 int hlbm_sur_adam(hlbm_sur *s, float lr, float beta1, float beta2, float eps);
 /* Wait for the surrogate's stream.  HLBM_ERR_TIMEOUT if a wait of a
  * tensor-core kernel on its own MMAs gave up (after about a second; the

@@ -529,6 +529,29 @@ __global__ void pack_input_kernel(const float *__restrict__ x, int c_real, int c
 }
 
 // FP32 [n] -> BF16 [n]
+// dz_last[p][c] += dy[p][c] for c < c_real: an upstream gradient (from a
+// later call of a rollout through the network) added to dL/dy.
+__global__ void add_upstream_kernel(float *__restrict__ dz_last, int cpad_last, const float *__restrict__ dy,
+                                    int c_real, int npix)
+{
+    const long long n = (long long)npix * c_real;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dz_last[(i / c_real) * cpad_last + i % c_real] += dy[i];
+}
+
+// dx[p][c] = g[p][c] for c < c_real, from a padded [npix][cpad] gradient;
+// with add != 0, dx[p][c] += g[p][c].  The input gradient of y = x + net(x)
+// is dL/dy (the identity) plus the network's part.
+__global__ void gather_grad_kernel(const float *__restrict__ g, int cpad, int c_real, int npix, int add,
+                                   float *__restrict__ dx)
+{
+    const long long n = (long long)npix * c_real;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = g[(i / c_real) * cpad + i % c_real];
+        dx[i] = add ? dx[i] + v : v;
+    }
+}
+
 __global__ void to_bf16_kernel(const float *__restrict__ x, long long n, __nv_bfloat16 *__restrict__ out)
 {
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
@@ -1356,20 +1379,33 @@ int hlbm_sur_predict(hlbm_sur *s, const float *x, float *y, int B)
 // After hlbm_sur_forward on the same batch: loss = mean((y - target)^2)
 // (target FP32 NHWC [B, H, W, C0] on the device) and the gradient of every
 // parameter into the gradient buffer.
-int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss_out)
+// The backward pass after hlbm_sur_forward: dL/dy = 2 (y - target) / n (+
+// dy); parameter gradients replace the stored ones, or are added to them
+// with accumulate; dx (if non-NULL) receives dL/dx.
+static int sur_backward(hlbm_sur *s, const float *target, const float *dy, int accumulate, float *dx,
+                        double *loss_out)
 {
     if (!s || !target || s->last_batch < 1) return HLBM_ERR_ARG;
     const int B = s->last_batch, npix = B * s->H * s->W;
     const int L = s->L;
     float *dzf[2] = {s->dz, s->dz2};
     int cur = 0;
-    if (cudaMemsetAsync(s->g, 0, s->nparam * 4, s->stream) != cudaSuccess ||
+    if ((!accumulate && cudaMemsetAsync(s->g, 0, s->nparam * 4, s->stream) != cudaSuccess) ||
         cudaMemsetAsync(s->loss, 0, sizeof(double), s->stream) != cudaSuccess ||
         cudaMemsetAsync(dzf[cur], 0, (size_t)npix * s->cpad_out[L - 1] * 4, s->stream) != cudaSuccess)
         return HLBM_ERR_CUDA;
     residual_loss_kernel<<<1024, 256, 0, s->stream>>>(s->xin, s->z[L - 1], s->cpad_out[L - 1], target, s->width[0],
                                                       npix, s->y, dzf[cur], s->loss);
     if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+    if (dy) {
+        add_upstream_kernel<<<1024, 256, 0, s->stream>>>(dzf[cur], s->cpad_out[L - 1], dy, s->width[0], npix);
+        if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+    }
+    if (dx) {
+        // the residual's identity: dL/dx starts as dL/dy
+        gather_grad_kernel<<<1024, 256, 0, s->stream>>>(dzf[cur], s->cpad_out[L - 1], s->width[0], npix, 0, dx);
+        if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+    }
     // BF16 copy of the top gradient for the tensor-core input-gradient pass
     to_bf16_kernel<<<1024, 256, 0, s->stream>>>(dzf[cur], (long long)npix * s->cpad_out[L - 1], s->gbuf[0]);
     if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
@@ -1379,7 +1415,18 @@ int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss_out)
         if (launch_wgrad(s->cpad_in[l], s->cpad_out[l], s->act[l], s->gbuf[gb], dzf[cur], s->width[l], s->width[l + 1],
                          npix, s->H, s->W, s->g + s->woff[l], s->g + s->boff[l], s->stream) != cudaSuccess)
             return HLBM_ERR_CUDA;
-        if (l == 0) break;
+        if (l == 0) {
+            if (dx) {
+                // the network's part of dL/dx: W_0^T * dz_0, the transposed
+                // convolution without GELU' (the input has no activation)
+                const ConvArgs a{s->gbuf[gb], s->Wd[0], nullptr, 0, s->gbuf[gb ^ 1], dzf[cur ^ 1], nullptr, npix,
+                                 s->H, s->W, 2, 1};
+                if (launch_conv(s->cpad_out[0], s->cpad_in[0], a, s->stream) != cudaSuccess) return HLBM_ERR_CUDA;
+                gather_grad_kernel<<<1024, 256, 0, s->stream>>>(dzf[cur ^ 1], s->cpad_in[0], s->width[0], npix, 1, dx);
+                if (cudaGetLastError() != cudaSuccess) return HLBM_ERR_CUDA;
+            }
+            break;
+        }
         // dz_{l-1} = (W_l^T * dz_l) . GELU'(z_{l-1}): the transposed
         // convolution on the tensor cores (dz read at p - offset(tap)),
         // GELU' in the epilogue, FP32 and BF16 results
@@ -1397,6 +1444,17 @@ int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss_out)
         *loss_out = l2 / ((double)npix * s->width[0]);
     }
     return HLBM_OK;
+}
+
+int hlbm_sur_backward(hlbm_sur *s, const float *target, double *loss_out)
+{
+    return sur_backward(s, target, nullptr, 0, nullptr, loss_out);
+}
+
+int hlbm_sur_backward_ex(hlbm_sur *s, const float *target, const float *dy, int accumulate, float *dx,
+                         double *loss_out)
+{
+    return sur_backward(s, target, dy, accumulate, dx, loss_out);
 }
 
 // One Adam step (Kingma & Ba 2015) on all parameters from the gradient

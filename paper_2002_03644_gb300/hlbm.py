@@ -34,7 +34,7 @@ ENTRY_POINTS = (
     "hlbm_batch_destroy",
     "hlbm_sur_create", "hlbm_sur_param_count", "hlbm_sur_set_params", "hlbm_sur_get_params", "hlbm_sur_forward",
     "hlbm_sur_predict",
-    "hlbm_sur_backward", "hlbm_sur_adam", "hlbm_sur_synchronize", "hlbm_sur_destroy",
+    "hlbm_sur_backward", "hlbm_sur_backward_ex", "hlbm_sur_adam", "hlbm_sur_synchronize", "hlbm_sur_destroy",
 )
 HLBM_NOALLOC_MAX_CELLS = 16777216
 
@@ -153,6 +153,8 @@ def _lib():
         lib.hlbm_sur_predict.argtypes = [_P, _PD, _PD, ctypes.c_int]
         lib.hlbm_sur_backward.restype = ctypes.c_int
         lib.hlbm_sur_backward.argtypes = [_P, _PD, ctypes.POINTER(ctypes.c_double)]
+        lib.hlbm_sur_backward_ex.restype = ctypes.c_int
+        lib.hlbm_sur_backward_ex.argtypes = [_P, _PD, _PD, ctypes.c_int, _PD, ctypes.POINTER(ctypes.c_double)]
         lib.hlbm_sur_adam.restype = ctypes.c_int
         lib.hlbm_sur_adam.argtypes = [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
         lib.hlbm_sur_synchronize.restype = ctypes.c_int
@@ -447,6 +449,21 @@ def hlbm_sur_predict(s, x, y, batch):
 def hlbm_sur_backward(s, target):
     loss = ctypes.c_double()
     _check(_lib().hlbm_sur_backward(s, target.data_ptr(), ctypes.byref(loss)))
+    return loss.value
+
+
+def hlbm_sur_backward_ex(s, target, dy=None, accumulate=False, dx=None):
+    """Backward pass for a rollout through the network: dL/dy = 2 (y -
+    target) / n + dy; parameter gradients added to the held ones when
+    accumulate; dL/dx written to dx.  Tensors: contiguous float32 on the
+    surrogate's device.  Returns the mean squared error against target."""
+    for t in (target, dy, dx):
+        if t is not None and not t.is_contiguous():
+            raise ValueError("hlbm_sur_backward_ex: tensors must be contiguous")
+    loss = ctypes.c_double()
+    _check(_lib().hlbm_sur_backward_ex(s, target.data_ptr(), None if dy is None else dy.data_ptr(),
+                                       int(bool(accumulate)), None if dx is None else dx.data_ptr(),
+                                       ctypes.byref(loss)))
     return loss.value
 
 

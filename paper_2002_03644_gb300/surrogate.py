@@ -197,8 +197,35 @@ class Surrogate:
         hlbm.hlbm_sur_adam(self.s, lr)
         return loss
 
+    def rollout_grads(self, x, targets):
+        """Gradients of the loss of a rollout through the network, y_1 =
+        f(x), y_j = f(y_(j-1)), L = sum_j mean((y_j - targets[j-1])^2), left
+        in the parameter gradients.  The inputs of the calls come from a
+        first pass without stored activations; the backward passes then run
+        from the last call to the first, each after a forward pass that
+        restores its activations, the dL/dx of a call being the upstream
+        gradient of the one before.  Returns the mean of the calls' losses."""
+        import torch
+        k = len(targets)
+        ins = [x]
+        for _ in range(k - 1):
+            ins.append(self.predict(ins[-1]))
+        g, total = None, 0.0
+        for j in range(k - 1, -1, -1):
+            hlbm.hlbm_sur_forward(self.s, ins[j], None, x.shape[0])
+            dx = torch.empty_like(x) if j > 0 else None
+            total += hlbm.hlbm_sur_backward_ex(self.s, targets[j], g, accumulate=j < k - 1, dx=dx)
+            g = dx
+        return total / k
+
+    def train_step_rollout(self, x, targets, lr):
+        """One Adam step on the loss of a rollout of len(targets) calls."""
+        loss = self.rollout_grads(x, targets)
+        hlbm.hlbm_sur_adam(self.s, lr)
+        return loss
+
     def fit(self, X, Y, epochs=10, batch=8, lr=1e-3, seed=0, log=None, lr_final=None, noise=0.0,
-            pushforward=0.0, pairs_per_run=None):
+            pushforward=0.0, pairs_per_run=None, rollout=1, rollout_from=0.5):
         """X, Y: CUDA float32 [N, H, W, C] (normalised).  The learning rate
         goes from `lr` to `lr_final` (default: stays at lr) along a cosine
         over the epochs.  With noise > 0 every input batch gets seeded
@@ -210,24 +237,42 @@ class Surrogate:
         fraction of the samples that have a predecessor take as input the
         network's own prediction from the predecessor instead of the solver's
         state, with the solver's next state as the target: the network is
-        trained on the states its rollouts reach.  Returns the mean loss of
-        every epoch."""
+        trained on the states its rollouts reach.  With rollout = k > 1 (and
+        runs of `pairs_per_run` pairs), from the epoch `rollout_from` x epochs
+        on, every step trains on the loss of k calls chained through the
+        network, from the samples whose run holds k - 1 more pairs (targets:
+        the solver's states 1 .. k calls later), back-propagated through
+        the chain.  Returns the mean loss of every epoch."""
         import torch
         rng = np.random.default_rng(seed)
         gen = torch.Generator(device=X.device)
         gen.manual_seed(int(seed) + 1)
         hist = []
         N = X.shape[0]
+        self.fit_calls = 0  # forward and backward passes of one sample each, summed
         for ep in range(epochs):
-            order = rng.permutation(N)
+            unroll = rollout > 1 and pairs_per_run and ep >= rollout_from * epochs
+            if unroll:
+                starts = np.flatnonzero(np.arange(N) % pairs_per_run <= pairs_per_run - rollout)
+                order = starts[rng.permutation(starts.size)]
+            else:
+                order = rng.permutation(N)
             tot, cnt = 0.0, 0
             lr_ep = lr
             if lr_final is not None and epochs > 1:
                 lr_ep = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * ep / (epochs - 1)))
-            for b0 in range(0, N - batch + 1, batch):
+            for b0 in range(0, order.size - batch + 1, batch):
                 sel = order[b0:b0 + batch]
                 idx = torch.as_tensor(sel, device=X.device)
                 xb = X[idx].contiguous()
+                if unroll:
+                    if noise > 0.0:
+                        xb = xb + noise * torch.randn(xb.shape, device=X.device, generator=gen)
+                    targets = [Y[idx + j].contiguous() for j in range(rollout)]
+                    tot += self.train_step_rollout(xb, targets, lr_ep)
+                    cnt += 1
+                    self.fit_calls += rollout * batch
+                    continue
                 if pushforward > 0.0 and pairs_per_run and 2 * ep >= epochs:
                     pick = np.flatnonzero((sel % pairs_per_run != 0) & (rng.random(len(sel)) < pushforward))
                     if pick.size:
@@ -237,6 +282,7 @@ class Surrogate:
                     xb = xb + noise * torch.randn(xb.shape, device=X.device, generator=gen)
                 tot += self.train_step(xb, Y[idx].contiguous(), lr_ep)
                 cnt += 1
+                self.fit_calls += batch
             self.synchronize()
             hist.append(tot / max(cnt, 1))
             if log:

@@ -16,6 +16,9 @@ as max |GPU - reference| over that tensor's max |reference|:
     1e-2.  What remains is FP32 summation order and the BF16 roundings that
     it flips (measured at most 3.8e-3);
   - against the exact FP64 network: 3e-2 (measured at most 9.8e-3).
+Calls chained through the network (the rollout training) are compared
+with the FP64 chain rule the same way: one call's input gradient at 1e-2,
+the summed gradients of a two-call loss at 3e-2.
 Adam's update is plain FP32 and is compared at 1e-5."""
 import math
 
@@ -134,6 +137,61 @@ def test_configured_network_element_by_element(env, shape):
             o += db.size
         bad = {k: v for k, v in errs.items() if not v <= bound}
         assert not bad, (bound, bad)
+
+
+@pytest.mark.parametrize("shape", [(2, 6, 256), (1, 12, 20)], ids=["6x256", "12x20"])
+def test_rollout_gradients_match_the_oracle_chain_rule(env, shape):
+    """Calls chained through the configured network (y1 = f(x), y2 = f(y1)),
+    against the exact FP64 chain rule (oracle backward_dy), element by
+    element as max |GPU - reference| over the tensor's max |reference|:
+      - one call's input gradient dL/dx from hlbm_sur_backward_ex, within
+        1e-2 (measured at most 7.3e-4: the residual's identity carries most
+        of it);
+      - the parameter gradients of loss(y2, t2) + loss(y1, t1) summed over
+        the two backward passes of Surrogate.rollout_grads (the second
+        call's dL/dy1 passed to the first as its upstream gradient), within
+        3e-2, the bound of one call (measured at most 9.2e-3), although the
+        second call starts from the GPU's own BF16-computed y1."""
+    torch, hlbm, surrogate = env
+    B, H, W = shape
+    widths = CONFIGURED
+    sur = surrogate.Surrogate(widths, H, W, batch_max=B, seed=3)
+    params = unpack(widths, sur.params())
+    rng = np.random.default_rng(9)
+    x = rng.normal(size=(B, H, W, widths[0])).astype(np.float32)
+    t1 = (x + 0.1 * rng.normal(size=x.shape)).astype(np.float32)
+    t2 = (t1 + 0.1 * rng.normal(size=x.shape)).astype(np.float32)
+    xg, t1g, t2g = (torch.from_numpy(a).cuda() for a in (x, t1, t2))
+    sur.forward(xg)
+    dxg = torch.empty_like(xg)
+    hlbm.hlbm_sur_backward_ex(sur.s, t1g, dx=dxg)
+    dx = dxg.cpu().numpy().transpose(0, 3, 1, 2).astype(np.float64)
+    sur.rollout_grads(xg, [t1g, t2g])
+    g = sur.grads().astype(np.float64)
+    sur.synchronize()
+    sur.close()
+    xo, t1o, t2o = (a.transpose(0, 3, 1, 2).astype(np.float64) for a in (x, t1, t2))
+    y1, c1 = S.forward(params, xo)
+    _, dx_ref = S.backward(params, c1, y1, t1o)
+    y2, c2 = S.forward(params, y1)
+    g2, dy1 = S.backward(params, c2, y2, t2o)
+    g1, _ = S.backward_dy(params, c1, dy1 + 2.0 * (y1 - t1o) / y1.size)
+
+    def elementwise(a, ref):
+        return float(np.abs(a - ref).max() / np.abs(ref).max())
+
+    errs = {"dx": elementwise(dx, dx_ref)}
+    o = 0
+    for l, ((dw1, db1), (dw2, db2)) in enumerate(zip(g1, g2)):
+        dw, db = dw1 + dw2, db1 + db2
+        errs[f"W{l}"] = elementwise(g[o:o + dw.size], dw.ravel())
+        o += dw.size
+        errs[f"b{l}"] = elementwise(g[o:o + db.size], db)
+        o += db.size
+    print("rollout gradient errors", shape, {k: f"{v:.2e}" for k, v in errs.items()})
+    assert errs.pop("dx") < 1e-2
+    for k, v in errs.items():
+        assert v < 3e-2, (k, v)
 
 
 def test_adam_matches_reference(env):
