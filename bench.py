@@ -82,10 +82,10 @@ def parse():
     ap.add_argument("--sur-pushforward", type=float, default=0.0,
                     help="fraction of training inputs replaced by the network's own prediction from the previous "
                          "snapshot (second half of the epochs)")
-    ap.add_argument("--sur-rollout", type=int, default=1,
+    ap.add_argument("--sur-rollout", type=int, default=2,
                     help="calls chained through the network per training sample from --sur-rollout-from on "
                          "(1: one call; k > 1: the loss of k calls, back-propagated through the chain)")
-    ap.add_argument("--sur-rollout-from", type=float, default=0.5,
+    ap.add_argument("--sur-rollout-from", type=float, default=0.8,
                     help="fraction of the epochs after which the chained training starts")
     ap.add_argument("--sur-tol", type=float, default=1.0,
                     help="judged-error tolerance of the hybrid rollout (max-abs, normalised fields)")
